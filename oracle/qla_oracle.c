@@ -1,0 +1,398 @@
+/*
+ * Plain FP64 CPU oracle for the 2D qubit lattice algorithm (QLA) of
+ * Soe et al., "Quantum Computing Framework for Transient Scattering of
+ * Electromagnetic Waves by Dielectric Structures" (arXiv 2604.21128).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  The product
+ * (the CUDA library) never links, loads or calls it, and the two share no
+ * code: no header, helper, table or constant generator.
+ *
+ * The oracle applies the paper's operators one at a time, literally, over
+ * full periodic arrays, in the order the paper writes them:
+ *   Q(t + dt) = V_y V_x U_y U_x Q(t)                         (Eq. 2e14)
+ * with U_x, U_y the 16-operator collide/stream products of Eq. 2e6 and
+ * Eq. 2e9 (applied rightmost first), collisions C_x (Eq. 2e3) and C_y
+ * (Eq. 2e8) with angles theta = delta / (4 n) (Eq. 2e4), streaming shifts of
+ * Eq. 2e5, and the potential operators V_x, V_y (Eqs. 2e11-2e13).
+ *
+ * Readings where the paper is garbled or silent (each also listed in the
+ * design notes):
+ *   - isotropic medium n_x = n_y = n_z = n (Sec. V-B), so
+ *     theta_0 = theta_1 = theta_2 = delta/(4n), beta_0 = beta_2, beta_1 = beta_3;
+ *   - streaming read literally: S^{+x} q(x) <- q(x + delta);
+ *   - d n / d x by the centred periodic difference (n[i+1]-n[i-1])/(2 delta);
+ *   - V: default "rotation" reading (rotation by beta/2 in the planes that
+ *     Eqs. 2d1-2d6 couple), or the printed shear with the q5 row sign taken
+ *     from the LCU sum (Eqs. 2f1-2f4) and the q3 row of Eq. 2e12 read as
+ *     sin(beta_3) q2 + cos(beta_3) q3, or no V at all (Eq. 2e10).
+ *
+ * State layout: six planes q[c][j*nx + i], c = 0..5, i = x index (fastest),
+ * j = y index; site (i, j) sits at (i*delta, j*delta); periodic in both axes.
+ * The amplitudes are the Dyson-mapped fields of Eq. 3b3:
+ *   (q0..q5) = (n E_x, n E_y, n E_z, B_x, B_y, B_z)   (c = 1).
+ *
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (see build.py).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdint.h>
+
+#include "qla_oracle.h"
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define SITE(i, j) ((size_t)(j) * (size_t)nx + (size_t)(i))
+
+/* ------------------------------------------------------------------ */
+/* Angles of the medium: Eq. 2e4 and Eq. 2e13                         */
+/* ------------------------------------------------------------------ */
+
+void orc_angles(int nx, int ny, double delta, const double *n,
+                double *theta, double *beta_x, double *beta_y)
+{
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        int jm = (j - 1 + ny) % ny, jp = (j + 1) % ny;
+        for (int i = 0; i < nx; ++i) {
+            int im = (i - 1 + nx) % nx, ip = (i + 1) % nx;
+            double nn = n[SITE(i, j)];
+            /* Eq. 2e4: theta = delta / (4 n) */
+            theta[SITE(i, j)] = delta / (4.0 * nn);
+            /* centred difference for the gradient of n (paper is silent) */
+            double dndx = (n[SITE(ip, j)] - n[SITE(im, j)]) / (2.0 * delta);
+            double dndy = (n[SITE(i, jp)] - n[SITE(i, jm)]) / (2.0 * delta);
+            /* Eq. 2e13: beta = (1/n^2) (dn/dx) delta^2 */
+            beta_x[SITE(i, j)] = dndx / (nn * nn) * delta * delta;
+            beta_y[SITE(i, j)] = dndy / (nn * nn) * delta * delta;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Collision operators                                                */
+/* ------------------------------------------------------------------ */
+
+/* Apply the 2x2 block [[m00, m01], [m10, m11]] of a 6x6 operator to the
+ * component pair (qa, qb) at every site, with the block entries built from
+ * cos/sin of the site's angle.  sa, sb select the sign pattern of the sine
+ * entries: m01 = sa * sin, m10 = sb * sin. */
+static void pair_rotate(int nx, int ny, double *qa, double *qb,
+                        const double *angle, double angle_scale,
+                        double sa, double sb)
+{
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            size_t k = SITE(i, j);
+            double a = angle[k] * angle_scale;
+            double c = cos(a), s = sin(a);
+            double x = qa[k], y = qb[k];
+            qa[k] = c * x + sa * s * y;
+            qb[k] = sb * s * x + c * y;
+        }
+    }
+}
+
+/* C_x of Eq. 2e3: rows q1 = cos q1 - sin q5, q5 = sin q1 + cos q5 (theta_1),
+ * and q2 = cos q2 - sin q4, q4 = sin q2 + cos q4 (theta_2).  The adjoint is
+ * the transpose (the sine signs swap). */
+void orc_collide_x(int nx, int ny, double *q, const double *theta, int dagger)
+{
+    size_t N = (size_t)nx * ny;
+    double sa = dagger ? +1.0 : -1.0, sb = -sa;
+    pair_rotate(nx, ny, q + 1 * N, q + 5 * N, theta, 1.0, sa, sb);
+    pair_rotate(nx, ny, q + 2 * N, q + 4 * N, theta, 1.0, sa, sb);
+}
+
+/* C_y of Eq. 2e8: rows q0 = cos q0 + sin q5, q5 = -sin q0 + cos q5
+ * (theta_0), and q2 = cos q2 + sin q3, q3 = -sin q2 + cos q3 (theta_2). */
+void orc_collide_y(int nx, int ny, double *q, const double *theta, int dagger)
+{
+    size_t N = (size_t)nx * ny;
+    double sa = dagger ? -1.0 : +1.0, sb = -sa;
+    pair_rotate(nx, ny, q + 0 * N, q + 5 * N, theta, 1.0, sa, sb);
+    pair_rotate(nx, ny, q + 2 * N, q + 3 * N, theta, 1.0, sa, sb);
+}
+
+/* ------------------------------------------------------------------ */
+/* Streaming operators: Eq. 2e5                                       */
+/* ------------------------------------------------------------------ */
+
+/* Shift one plane: new q(x, y) = old q(x + sign*delta, y) for axis 0, or
+ * old q(x, y + sign*delta) for axis 1, periodic. */
+static void shift_plane(int nx, int ny, double *p, int axis, int sign,
+                        double *tmp)
+{
+    size_t N = (size_t)nx * ny;
+    memcpy(tmp, p, N * sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            int si = i, sj = j;
+            if (axis == 0) si = ((i + sign) % nx + nx) % nx;
+            else           sj = ((j + sign) % ny + ny) % ny;
+            p[SITE(i, j)] = tmp[SITE(si, sj)];
+        }
+    }
+}
+
+/* S_{ab}^{sign, axis}: shift the components a and b, leave the others. */
+void orc_stream(int nx, int ny, double *q, int comp_a, int comp_b, int axis,
+                int sign, double *tmp)
+{
+    size_t N = (size_t)nx * ny;
+    shift_plane(nx, ny, q + (size_t)comp_a * N, axis, sign, tmp);
+    shift_plane(nx, ny, q + (size_t)comp_b * N, axis, sign, tmp);
+}
+
+/* ------------------------------------------------------------------ */
+/* Evolution operators U_x (Eq. 2e6) and U_y (Eq. 2e9)                */
+/* ------------------------------------------------------------------ */
+
+/* One factor of the product: either a collision (C or its adjoint) or a
+ * streaming shift of the pair "first" (S14 along x, S03 along y) or the pair
+ * "second" (S25) by +1 or -1 cell. */
+enum { OP_C = 0, OP_CDAG = 1, OP_S1P = 2, OP_S1M = 3, OP_S2P = 4, OP_S2M = 5 };
+
+/* Eq. 2e6 read right to left, i.e. in the order the factors act on Q.
+ * In the paper's left-to-right notation the product is
+ *   S25+ C^ S25- C . S14- C^ S14+ C . S25- C S25+ C^ . S14+ C S14- C^
+ * (C^ = adjoint), so the first factor to act is the rightmost C^.  Eq. 2e9
+ * has the same pattern with S03 in place of S14. */
+static const int U_SEQUENCE[16] = {
+    OP_CDAG, OP_S1M, OP_C,    OP_S1P,
+    OP_CDAG, OP_S2P, OP_C,    OP_S2M,
+    OP_C,    OP_S1P, OP_CDAG, OP_S1M,
+    OP_C,    OP_S2M, OP_CDAG, OP_S2P,
+};
+
+void orc_U(int nx, int ny, double *q, const double *theta, int axis,
+           double *tmp)
+{
+    /* axis 0: pairs S14 = (q1, q4) and S25 = (q2, q5)   (Eq. 2e5)
+     * axis 1: pairs S03 = (q0, q3) and S25 = (q2, q5)   (Eq. 2e9) */
+    int f_a = (axis == 0) ? 1 : 0, f_b = (axis == 0) ? 4 : 3;
+    for (int k = 0; k < 16; ++k) {
+        switch (U_SEQUENCE[k]) {
+        case OP_C:
+        case OP_CDAG: {
+            int dag = (U_SEQUENCE[k] == OP_CDAG);
+            if (axis == 0) orc_collide_x(nx, ny, q, theta, dag);
+            else           orc_collide_y(nx, ny, q, theta, dag);
+            break;
+        }
+        case OP_S1P: orc_stream(nx, ny, q, f_a, f_b, axis, +1, tmp); break;
+        case OP_S1M: orc_stream(nx, ny, q, f_a, f_b, axis, -1, tmp); break;
+        case OP_S2P: orc_stream(nx, ny, q, 2, 5, axis, +1, tmp); break;
+        case OP_S2M: orc_stream(nx, ny, q, 2, 5, axis, -1, tmp); break;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Potential operators V_x, V_y (Eqs. 2e11-2e13)                      */
+/* ------------------------------------------------------------------ */
+
+/* Printed shear (Eq. 2e11) with the q5 row sign of the LCU sum: only the
+ * rows q4 and q5 change,
+ *   q4 <- -sin(b2) q2 + cos(b2) q4,   q5 <- +sin(b0) q1 + cos(b0) q5. */
+static void potential_x_literal(int nx, int ny, double *q, const double *bx)
+{
+    size_t N = (size_t)nx * ny;
+    double *q1 = q + N, *q2 = q + 2 * N, *q4 = q + 4 * N, *q5 = q + 5 * N;
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            size_t k = SITE(i, j);
+            double b = bx[k], c = cos(b), s = sin(b);
+            q4[k] = -s * q2[k] + c * q4[k];
+            q5[k] = s * q1[k] + c * q5[k];
+        }
+    }
+}
+
+/* Printed shear (Eq. 2e12) with the q3 row read as sin(b3) q2 + cos(b3) q3:
+ *   q3 <- sin(b3) q2 + cos(b3) q3,   q5 <- -sin(b1) q0 + cos(b1) q5. */
+static void potential_y_literal(int nx, int ny, double *q, const double *by)
+{
+    size_t N = (size_t)nx * ny;
+    double *q0 = q, *q2 = q + 2 * N, *q3 = q + 3 * N, *q5 = q + 5 * N;
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            size_t k = SITE(i, j);
+            double b = by[k], c = cos(b), s = sin(b);
+            q3[k] = s * q2[k] + c * q3[k];
+            q5[k] = -s * q0[k] + c * q5[k];
+        }
+    }
+}
+
+/* Rotation reading.  The collide/stream product U_x recovers the symmetric
+ * operator (1/2)[(1/n) d_x + d_x (1/n)]; what Eqs. 2d2, 2d3, 2d5, 2d6 still
+ * need is a rotation at rate (1/2) (d_x n)/n^2 in the (q2, q4) and (q1, q5)
+ * planes, i.e. by the angle beta/2 over one step dt = delta^2:
+ *   (q2, q4) <- [[c, s], [-s, c]] (q2, q4)     angle beta_2 / 2
+ *   (q1, q5) <- [[c, -s], [s, c]] (q1, q5)     angle beta_0 / 2            */
+static void potential_x_rotation(int nx, int ny, double *q, const double *bx)
+{
+    size_t N = (size_t)nx * ny;
+    pair_rotate(nx, ny, q + 2 * N, q + 4 * N, bx, 0.5, +1.0, -1.0);
+    pair_rotate(nx, ny, q + 1 * N, q + 5 * N, bx, 0.5, -1.0, +1.0);
+}
+
+/* Same along y (Eqs. 2d1, 2d3, 2d4, 2d6):
+ *   (q2, q3) <- [[c, -s], [s, c]] (q2, q3)     angle beta_3 / 2
+ *   (q0, q5) <- [[c, s], [-s, c]] (q0, q5)     angle beta_1 / 2            */
+static void potential_y_rotation(int nx, int ny, double *q, const double *by)
+{
+    size_t N = (size_t)nx * ny;
+    pair_rotate(nx, ny, q + 2 * N, q + 3 * N, by, 0.5, -1.0, +1.0);
+    pair_rotate(nx, ny, q + 0 * N, q + 5 * N, by, 0.5, +1.0, -1.0);
+}
+
+void orc_V(int nx, int ny, double *q, const double *beta_x,
+           const double *beta_y, int vmode)
+{
+    if (vmode == ORC_V_ROTATION) {
+        potential_x_rotation(nx, ny, q, beta_x);
+        potential_y_rotation(nx, ny, q, beta_y);
+    } else if (vmode == ORC_V_LITERAL) {
+        potential_x_literal(nx, ny, q, beta_x);
+        potential_y_literal(nx, ny, q, beta_y);
+    }
+    /* ORC_V_NONE: V = I, the homogeneous step of Eq. 2e10 */
+}
+
+/* ------------------------------------------------------------------ */
+/* Full step (Eq. 2e14) and driver                                    */
+/* ------------------------------------------------------------------ */
+
+void orc_step(int nx, int ny, double *q, const double *theta,
+              const double *beta_x, const double *beta_y, int vmode,
+              double *tmp)
+{
+    orc_U(nx, ny, q, theta, 0, tmp);          /* U_x */
+    orc_U(nx, ny, q, theta, 1, tmp);          /* U_y */
+    orc_V(nx, ny, q, beta_x, beta_y, vmode);  /* V_x, then V_y */
+}
+
+int orc_run(int nx, int ny, double delta, const double *n, double *q,
+            long long steps, int vmode)
+{
+    size_t N = (size_t)nx * ny;
+    double *theta = malloc(N * sizeof(double));
+    double *bx = malloc(N * sizeof(double));
+    double *by = malloc(N * sizeof(double));
+    double *tmp = malloc(N * sizeof(double));
+    if (!theta || !bx || !by || !tmp) {
+        free(theta); free(bx); free(by); free(tmp);
+        return -1;
+    }
+    orc_angles(nx, ny, delta, n, theta, bx, by);
+    for (long long s = 0; s < steps; ++s)
+        orc_step(nx, ny, q, theta, bx, by, vmode, tmp);
+    free(theta); free(bx); free(by); free(tmp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Energy (Eq. A13), fields (inverse of Eq. 3b3), initial packet       */
+/* ------------------------------------------------------------------ */
+
+/* Sum over sites and components of q_c^2: the squared norm of Q, which is
+ * the total energy of Eq. A13 up to the cell area delta^2. */
+double orc_energy(int nx, int ny, const double *q)
+{
+    size_t N = (size_t)nx * ny;
+    double total = 0.0;
+    for (int c = 0; c < 6; ++c) {
+        double part = 0.0;
+#pragma omp parallel for reduction(+ : part) schedule(static)
+        for (long long k = 0; k < (long long)N; ++k)
+            part += q[(size_t)c * N + k] * q[(size_t)c * N + k];
+        total += part;
+    }
+    return total;
+}
+
+/* E = q_{0,1,2} / n and B = q_{3,4,5} (Eq. 3b3 with c = 1).  out holds six
+ * planes in the order E_x, E_y, E_z, B_x, B_y, B_z. */
+void orc_fields(int nx, int ny, const double *n, const double *q, double *out)
+{
+    size_t N = (size_t)nx * ny;
+#pragma omp parallel for schedule(static)
+    for (long long k = 0; k < (long long)N; ++k) {
+        for (int c = 0; c < 3; ++c) out[c * N + k] = q[c * N + k] / n[k];
+        for (int c = 3; c < 6; ++c) out[c * N + k] = q[c * N + k];
+    }
+}
+
+/* Minimum-image offset of coordinate x from x0 on a period L, in [-L/2, L/2). */
+static double min_image(double x, double x0, double L)
+{
+    double d = fmod(x - x0 + 0.5 * L, L);
+    if (d < 0.0) d += L;
+    return d - 0.5 * L;
+}
+
+/* E_z-polarised Gaussian packet (Sec. V-B), moving along the angle phi:
+ *   xi  = dx cos(phi) + dy sin(phi),  eta = -dx sin(phi) + dy cos(phi)
+ *   E_z = A exp(-xi^2 / w^2) cos(k0 xi) [ exp(-eta^2 / wt^2) if wt > 0 ]
+ * and the plane-wave magnetic field B = n k^ x E, which in Dyson variables
+ * reads q2 = n E_z, q3 = sin(phi) q2, q4 = -cos(phi) q2 (the rest zero).
+ * Fills the window of nwx x nwy sites whose first site is (i0, j0) of the
+ * global nx x ny lattice; n_win is the medium on that window. */
+void orc_packet(int nx, int ny, double delta, int i0, int j0, int nwx,
+                int nwy, const double *n_win, double x0, double y0,
+                double phi, double k0, double w, double wt, double amp,
+                double *q_win)
+{
+    size_t N = (size_t)nwx * nwy;
+    double Lx = nx * delta, Ly = ny * delta;
+    double cphi = cos(phi), sphi = sin(phi);
+    memset(q_win, 0, 6 * N * sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int jj = 0; jj < nwy; ++jj) {
+        for (int ii = 0; ii < nwx; ++ii) {
+            int gi = ((i0 + ii) % nx + nx) % nx;
+            int gj = ((j0 + jj) % ny + ny) % ny;
+            double dx = min_image(gi * delta, x0, Lx);
+            double dy = min_image(gj * delta, y0, Ly);
+            double xi = dx * cphi + dy * sphi;
+            double eta = -dx * sphi + dy * cphi;
+            double ez = amp * exp(-(xi * xi) / (w * w)) * cos(k0 * xi);
+            if (wt > 0.0) ez *= exp(-(eta * eta) / (wt * wt));
+            size_t k = (size_t)jj * nwx + ii;
+            double q2 = n_win[k] * ez;
+            q_win[2 * N + k] = q2;
+            q_win[3 * N + k] = sphi * q2;
+            q_win[4 * N + k] = -cphi * q2;
+        }
+    }
+}
+
+int orc_abi_version(void) { return 1; }
+
+/* Thread count of the OpenMP loops (1 when built without OpenMP). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
