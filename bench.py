@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Throughput of the 2D QLA step (Eq. 2e14) on GB300: site-updates/s.
+
+One bench step = ``--qla-steps`` (default 100) time steps of the whole lattice
+followed by the FP64 energy reduction (Eq. A13) read back to the host, the
+monitoring cadence of the 8192^2 workload.  Default workload: 8192 x 8192
+periodic lattice, unit spacing, rotated dielectric ellipse (n_in = 2, semi-axes
+1200 x 600, 30 degrees, tanh edge 8) in vacuum, E_z packet k0 = 0.2, width 300;
+FP32 storage and arithmetic, E_z polarisation (q2, q3, q4 live), 200 bench
+steps = the workload's 20000 time steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the plain CPU
+oracle on the host cores instead (bounded samples of the same workload).
+Under torchrun each rank runs its own replica of the workload (no data
+exchange: weak scaling); the time is the maximum over ranks.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--workload", default="ellipse_8192")
+    ap.add_argument("--qla-steps", type=int, default=100)
+    ap.add_argument("--time-block", type=int, default=0)
+    ap.add_argument("--six-planes", action="store_true",
+                    help="evolve all six amplitudes instead of the E_z triple")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2604_21128_gb300 import inputs
+    table = {"ellipse_8192": inputs.ellipse_8192, "bubble_16384": inputs.bubble_16384,
+             "ellipse_256": inputs.ellipse_256}
+    return table[name]()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu_id)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# Distributed helpers (replicas; the only collectives time the run)
+# ---------------------------------------------------------------------------
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline, and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(w, n_full, side, steps):
+    """Time the oracle on a side x side window of the workload (the medium
+    and packet of the full lattice, taken periodic on the window) for
+    ``steps`` steps; returns site-updates/s, seconds and the thread count."""
+    import numpy as np
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    # window straddling the ellipse's left edge, where the packet arrives
+    i0 = max(0, int(w.packet.x0 / w.delta) + int(w.packet.width / w.delta) - side // 2)
+    j0 = w.ny // 2 - side // 2
+    crop = np.ascontiguousarray(n_full[j0:j0 + side, i0:i0 + side])
+    q = oracle.packet(crop, w.delta, window=(i0, j0), global_shape=(w.ny, w.nx),
+                      **w.packet.as_dict())
+    t = time.perf_counter()
+    oracle.run(q, crop, w.delta, steps)
+    dt = time.perf_counter() - t
+    return side * side * steps / dt, dt, oracle.get_threads()
+
+
+def reference_arm(args):
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    w = workload(args.workload)
+    n_full = w.medium()
+    side, per = 512, 2
+    for _ in range(args.warmup):
+        oracle_sample(w, n_full, side, per)
+    total_t, su = 0.0, 0
+    for _ in range(args.steps):
+        _, dt, threads = oracle_sample(w, n_full, side, per)
+        total_t += dt
+        su += side * side * per
+    value = su / total_t
+    sample = ("%d x %d crop of the %s workload (same medium recipe and packet), %d steps per "
+              "bench step, plain FP64 CPU oracle" % (side, side, w.name, per))
+    line = {"impl": "reference", "metric": "site-updates/s", "value": value,
+            "unit": "site-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def kernel_traffic(k, sites):
+    """DRAM bytes per step-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2604_21128_gb300", "csrc", rec["source"])
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if sha != rec.get("source_sha256") or rec.get("time_block") != k:
+        return None
+    return rec["dram_bytes_per_site_step"] * sites * k
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    from paper_2604_21128_gb300 import build as qbuild
+    from paper_2604_21128_gb300 import qla
+
+    world, rank, local = dist_setup()
+    if world == 1:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    qbuild.build()
+    w = workload(args.workload)
+    te = not args.six_planes
+    P = 3 if te else 6
+    elt = 4 if args.precision == "fp32" else 8
+    n_host = torch.from_numpy(w.medium()).pin_memory()
+    pk = w.packet.as_dict()
+    S = args.qla_steps
+    sites = w.nx * w.ny
+
+    stream = torch.cuda.Stream(dev)
+    g = qla.Grid(w.nx, w.ny, w.delta, args.precision, te_only=te, stream=stream)
+    if args.time_block:
+        g.set_time_block(args.time_block)
+    g.set_medium(n_host)
+    g.set_packet(**pk)
+    e0 = g.energy()
+
+    for _ in range(args.warmup):
+        g.step(S)
+        g.energy()
+    torch.cuda.synchronize(dev)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local if world > 1 else 0)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    launches0 = g.launches
+    step_launches = 0
+    sampler.start()
+    time.sleep(0.3)
+    start.record(stream)
+    energies = []
+    for k in range(args.steps):
+        l0 = g.launches
+        ev[k][0].record(stream)
+        g.step(S)
+        ev[k][1].record(stream)
+        step_launches += g.launches - l0
+        energies.append(g.energy())
+    stop.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    launches = g.launches - launches0
+    elapsed = start.elapsed_time(stop) / 1e3
+    step_time = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    elapsed = max_over_ranks(world, elapsed)
+    barrier(world)
+    su_total = world * args.steps * S * sites
+    value = su_total / elapsed
+    drift = energies[-1] / e0 - 1 if e0 else float("nan")
+
+    # roofline of the dominant (step) kernel: algorithmic bytes per launch =
+    # 2 * P * element bytes per site-update x sites x steps per launch
+    k_used = S * args.steps / max(step_launches, 1)
+    bytes_per_su = 2 * P * elt
+    per_launch_s = step_time / max(step_launches, 1)
+    alg_bytes = bytes_per_su * sites * k_used
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / per_launch_s / 1e9
+    traffic = kernel_traffic(int(round(k_used)), sites)
+    g.close()
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_run(args, w, te, n_host, pk, world, dev)
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        side, nst = 2048, 6
+        v, dt, threads = oracle_sample(w, n_host.numpy(), side, nst)
+        cpu = {"value": v, "unit": "site-updates/s", "cores": threads, "kind": "oracle",
+               "sample": "%d x %d crop of the %s workload, %d steps (%.1f s), plain FP64 "
+                         "CPU oracle, OpenMP over rows" % (side, side, w.name, nst, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": w.name + ("_fp32" if elt == 4 else "_fp64")
+                       + ("_ez" if te else "_6planes"),
+                       "nx": w.nx, "ny": w.ny, "delta": w.delta,
+                       "qla_steps_per_bench_step": S, "planes": P,
+                       "potential": "rotation", "time_block": k_used,
+                       "energy_drift": drift,
+                       "l2": "state %.0f MB > 129 MB L2, no flush" % (2 * P * elt * sites / 2e6)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind,
+                         "bytes_per_site_update": bytes_per_su,
+                         "kernel_ms": 1e3 * per_launch_s},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e_run(args, w, te, n_host, pk, world, dev):
+    """Same metric through the public API from host buffers: the medium
+    copied from pinned host memory, the packet built, every bench step's
+    energy read back, the final E_z copied to pinned host memory."""
+    import torch
+    from paper_2604_21128_gb300 import qla
+    stream = torch.cuda.Stream(dev)
+    ez = torch.empty((w.ny, w.nx), dtype=torch.float64).pin_memory()
+    g = qla.Grid(w.nx, w.ny, w.delta, args.precision, te_only=te, stream=stream)
+    if args.time_block:
+        g.set_time_block(args.time_block)
+    S = args.qla_steps
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    g.set_medium(n_host)
+    g.set_packet(**pk)
+    for _ in range(args.steps):
+        g.step(S)
+        g.energy()
+    qla.qla_fields(g._ctx, w.nx, w.ny, Ez=ez)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t
+    dt = max_over_ranks(world, dt)
+    g.close()
+    sites = w.nx * w.ny
+    return {"value": world * args.steps * S * sites / dt, "unit": "site-updates/s",
+            "h2d_bytes_per_step": 8 * sites / args.steps,
+            "d2h_bytes_per_step": 8 + 8 * sites / args.steps}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

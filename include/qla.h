@@ -1,0 +1,166 @@
+/*
+ * qla.h -- C ABI of libqla, a GB300 (sm_103a) implementation of the qubit
+ * lattice algorithm (QLA) for Maxwell's equations in a 2D inhomogeneous
+ * scalar dielectric n(x, y), after Soe et al., arXiv 2604.21128.
+ *
+ * One context = one periodic nx x ny lattice of spacing delta on the current
+ * CUDA device, advanced by the step of Eq. 2e14,
+ *     Q(t + dt) = V_y V_x U_y U_x Q(t),      dt = delta^2 (Eq. 2e7),
+ * where Q holds the six Dyson amplitudes of Eq. 3b3,
+ *     (q0, q1, q2, q3, q4, q5) = (n E_x, n E_y, n E_z, c B_x, c B_y, c B_z),
+ * U_x / U_y are the collide-stream products of Eqs. 2e6 / 2e9 (collisions
+ * C_x Eq. 2e3, C_y Eq. 2e8 with theta = delta/(4n), Eq. 2e4; shifts Eq. 2e5)
+ * and V_x / V_y the potential operators of Eqs. 2e11-2e13.
+ *
+ * Conventions shared by every call:
+ *  - Host arrays are FP64, row-major with x fastest: element (i, j) at
+ *    [j*nx + i]; site (i, j) sits at the point (i*delta, j*delta).  The
+ *    lattice is periodic in x and y.  Host arrays are caller-owned and are
+ *    only read or written during the call.
+ *  - Every call that launches work enqueues it on the context's stream.
+ *    Calls that return host data (qla_energy, qla_get_state, qla_fields)
+ *    synchronise that stream; qla_step does not.
+ *  - Errors are return codes; nothing is thrown across the ABI.  A CUDA
+ *    error makes the context's status sticky (every later call returns
+ *    QLA_ECUDA); qla_last_error() gives the text.
+ *  - One context must be used from one host thread at a time.
+ */
+#ifndef QLA_H
+#define QLA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qla_ctx qla_ctx;
+
+typedef enum {
+    QLA_OK = 0,
+    QLA_EINVAL = 1,      /* bad argument (size, pointer, flag, non-finite or n <= 0) */
+    QLA_ESTATE = 2,      /* call out of order (e.g. step before medium and state) */
+    QLA_ENOMEM = 3,      /* device allocation failed or workspace too small */
+    QLA_ECUDA = 4,       /* a CUDA call failed; the context is unusable */
+    QLA_ETIMEOUT = 5,    /* a bounded device wait ran out */
+    QLA_ENONFINITE = 6   /* the energy came out NaN or infinite */
+} qla_status;
+
+typedef enum { QLA_FP64 = 0, QLA_FP32 = 1 } qla_precision;
+
+/* Context flags (bitwise or). */
+enum {
+    /* Evolve only q2, q3, q4 (E_z polarisation).  Exact when q0 = q1 = q5 = 0:
+     * C_x couples (q1,q5),(q2,q4); C_y couples (q0,q5),(q2,q3) (Eqs. 2e3, 2e8);
+     * shifts move single components; V acts in the same planes.  So the two
+     * triples never mix and q0, q1, q5 stay identically zero. */
+    QLA_TE_ONLY = 1u,
+    /* Potential operators as printed (Eqs. 2e11-2e12, shear by the full beta
+     * of Eq. 2e13), with the q5 row of V_x taken from the LCU sum
+     * (Eqs. 2f1-2f4: +sin(beta_0) q1) and the q3 row of V_y read as
+     * sin(beta_3) q2 + cos(beta_3) q3.  Not unitary.  Default (flag clear):
+     * rotation by beta/2 in the planes (q2,q4),(q1,q5) for V_x and
+     * (q2,q3),(q0,q5) for V_y, which makes Eq. 2e14 recover Eqs. 2d1-2d6
+     * to O(delta^2) and the step exactly unitary. */
+    QLA_POTENTIAL_LITERAL = 2u,
+    /* V = I: the homogeneous-medium step of Eq. 2e10. */
+    QLA_POTENTIAL_NONE = 4u
+};
+
+/* E_z-polarised Gaussian packet (Sec. V-B): with
+ *   xi  =  dx cos(angle) + dy sin(angle),  eta = -dx sin(angle) + dy cos(angle),
+ * (dx, dy) the minimum-image offset of a site from (x0, y0) on the periodic
+ * box, E_z = amplitude * exp(-xi^2/width^2) * cos(k0 xi), times
+ * exp(-eta^2/transverse_width^2) when transverse_width > 0 (0 = planar
+ * front).  B is the plane-wave field n k^ x E, so q2 = n E_z,
+ * q3 = sin(angle) q2, q4 = -cos(angle) q2, and q0 = q1 = q5 = 0.
+ * Lengths in physical units (cells * delta); k0 in radians per unit. */
+typedef struct {
+    double x0, y0, angle, k0, width, transverse_width, amplitude;
+} qla_packet;
+
+/* Bytes of device workspace a context of this shape needs (state ping-pong
+ * buffers, coefficient planes, the n plane, a FP64 staging plane and the
+ * reduction scratch).  0 for invalid arguments. */
+size_t qla_workspace_bytes(int nx, int ny, int precision, unsigned flags);
+
+/* Create a context.  nx, ny >= 1; delta > 0 and finite; precision is a
+ * qla_precision; cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream) on the current device.  workspace: device memory of at least
+ * qla_workspace_bytes() bytes, 256-byte aligned, owned by the caller and
+ * kept alive until qla_destroy(); or NULL, in which case the library
+ * allocates (and frees) its own.  On success *out receives the context; on
+ * failure *out is NULL and the return code says why. */
+qla_status qla_init_grid(qla_ctx **out, int nx, int ny, double delta,
+                         int precision, unsigned flags, void *cuda_stream,
+                         void *workspace, size_t workspace_bytes);
+
+/* Set the medium n(x, y) (nx*ny FP64 host values, every one finite and
+ * > 0) and derive the per-site coefficients: theta = delta/(4n) (Eq. 2e4),
+ * beta = delta^2 (dn/dx)/n^2 and likewise in y (Eq. 2e13), with dn/dx by
+ * the centred periodic difference (n[i+1] - n[i-1])/(2 delta).  The FP64
+ * angles are turned into cosine/sine coefficient planes; in FP32 mode the
+ * collision coefficients are stored as two FP32 words each (value + low
+ * part).  Returns QLA_EINVAL (and changes nothing) if any n is not finite
+ * or not positive. */
+qla_status qla_set_medium(qla_ctx *ctx, const double *n_host);
+
+/* Fill the state with the packet described by *p (see qla_packet) on the
+ * current medium.  QLA_ESTATE if no medium was set; QLA_EINVAL if width
+ * <= 0, transverse_width < 0 or any field is not finite. */
+qla_status qla_set_packet(qla_ctx *ctx, const qla_packet *p);
+
+/* Copy a raw state in: 6*nx*ny FP64 host values, planes q0..q5 in order.
+ * In QLA_TE_ONLY mode planes q0, q1, q5 must be all zero (QLA_EINVAL
+ * otherwise).  In FP32 mode the values are rounded to FP32. */
+qla_status qla_set_state(qla_ctx *ctx, const double *q_host);
+
+/* Copy the state out as 6*nx*ny FP64 host values (q0..q5; zeros for the
+ * planes a QLA_TE_ONLY context does not evolve).  Synchronises. */
+qla_status qla_get_state(qla_ctx *ctx, double *q_host);
+
+/* Advance n_steps >= 0 steps of Eq. 2e14 on the context's stream (returns
+ * without waiting).  n_steps == 0 is a no-op; otherwise QLA_ESTATE before
+ * both a medium and a state are set. */
+qla_status qla_step(qla_ctx *ctx, long long n_steps);
+
+/* Total energy, Eq. A13 without the cell area: the sum over sites and
+ * components of q_c^2, accumulated in FP64 in a fixed order (bitwise
+ * reproducible for a given lattice).  Synchronises.  QLA_ENONFINITE if the
+ * sum is NaN or infinite (the value is still written). */
+qla_status qla_energy(qla_ctx *ctx, double *out);
+
+/* Fields from the inverse of Eq. 3b3 (c = 1): E = (q0, q1, q2)/n,
+ * B = (q3, q4, q5); each output is nx*ny FP64 host values, NULL to skip.
+ * Synchronises. */
+qla_status qla_fields(qla_ctx *ctx, double *Ex, double *Ey, double *Ez,
+                      double *Bx, double *By, double *Bz);
+
+/* Read the six amplitudes q0..q5 at `count` sites (i[k], j[k]), each
+ * 0 <= i < nx, 0 <= j < ny, into out[6*k + c] (FP64; zeros for planes a
+ * QLA_TE_ONLY context does not evolve).  Synchronises.  QLA_EINVAL for an
+ * index out of range or count outside 0..65536. */
+qla_status qla_probe(qla_ctx *ctx, int count, const int *i, const int *j, double *out);
+
+/* Number of time steps the library fuses into one kernel launch (temporal
+ * blocking), 1..QLA_MAX_TIME_BLOCK; 0 restores the library's choice.
+ * Results do not depend on it beyond FP rounding order (FP64: not at all). */
+#define QLA_MAX_TIME_BLOCK 8
+qla_status qla_set_time_block(qla_ctx *ctx, int k);
+
+/* Kernel launches enqueued by this context since creation (diagnostics). */
+long long qla_launch_count(const qla_ctx *ctx);
+
+/* Text of the last error on this context ("" if none); valid until the next
+ * call on the context.  qla_status_string() names a status code. */
+const char *qla_last_error(const qla_ctx *ctx);
+const char *qla_status_string(qla_status s);
+
+/* Free the context (and the workspace if the library allocated it).
+ * Synchronises the context's stream first.  NULL is a no-op. */
+void qla_destroy(qla_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QLA_H */

@@ -1,0 +1,390 @@
+// C ABI of libqla (declared in include/qla.h): argument checking, the
+// workspace layout, host <-> device copies and the step driver.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "qla_internal.h"
+
+namespace qla {
+
+static size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+Layout layout_for(int nx, int ny, int prec, unsigned flags) {
+    Layout L{};
+    const size_t elt = prec == QLA_FP64 ? 8 : 4;
+    const int P = (flags & QLA_TE_ONLY) ? 3 : 6;
+    // rows padded to 32 elements: 128-byte aligned rows for FP32, 256 for FP64
+    L.pitch = (nx + 31) / 32 * 32;
+    L.plane_elems = size_t(ny) * L.pitch;
+    const size_t plane_bytes = align256(L.plane_elems * elt);
+    const size_t cC = prec == QLA_FP64 ? sizeof(double2) : sizeof(float4);
+    const size_t cV = prec == QLA_FP64 ? sizeof(double4) : sizeof(float4);
+    // energy partials: one per block of 256 threads x 8 sites, capped
+    const size_t sites = size_t(nx) * ny;
+    size_t nb = (sites + 2047) / 2048;
+    if (nb > 4096) nb = 4096;
+    if (nb < 1) nb = 1;
+    L.energy_blocks = int(nb);
+    size_t off = 0;
+    L.state[0] = off; off += align256(plane_bytes * P);
+    L.state[1] = off; off += align256(plane_bytes * P);
+    L.coefC = off;    off += align256(L.plane_elems * cC);
+    L.coefV = off;    off += align256(L.plane_elems * cV);
+    L.n = off;        off += align256(L.plane_elems * 8);
+    L.staging = off;  off += align256(sites * 8);
+    L.partials = off; off += align256(nb * 8);
+    L.result = off;   off += align256(8);
+    L.total = off;
+    return L;
+}
+
+}  // namespace qla
+
+using namespace qla;
+
+namespace {
+
+qla_status fail(qla_ctx *c, qla_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+qla_status fail(qla_ctx *c, qla_status s, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+        if (s == QLA_ECUDA) c->sticky = QLA_ECUDA;
+    }
+    return s;
+}
+
+qla_status cuda_fail(qla_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, QLA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define QLA_CUDA(c, call, what)                              \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail((c), e_, (what)); \
+    } while (0)
+
+// Make the context's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+qla_status usable(qla_ctx *c) {
+    if (!c) return QLA_EINVAL;
+    if (c->sticky != QLA_OK) return c->sticky;
+    return QLA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t qla_workspace_bytes(int nx, int ny, int precision, unsigned flags) {
+    if (nx < 1 || ny < 1 || (precision != QLA_FP64 && precision != QLA_FP32)) return 0;
+    if (size_t(nx) * size_t(ny) > (size_t(1) << 34)) return 0;
+    return layout_for(nx, ny, precision, flags).total;
+}
+
+qla_status qla_init_grid(qla_ctx **out, int nx, int ny, double delta, int precision,
+                         unsigned flags, void *cuda_stream, void *workspace,
+                         size_t workspace_bytes) {
+    if (!out) return QLA_EINVAL;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || !(delta > 0.0) || !std::isfinite(delta)) return QLA_EINVAL;
+    if (precision != QLA_FP64 && precision != QLA_FP32) return QLA_EINVAL;
+    if (flags & ~(unsigned)(QLA_TE_ONLY | QLA_POTENTIAL_LITERAL | QLA_POTENTIAL_NONE))
+        return QLA_EINVAL;
+    if ((flags & QLA_POTENTIAL_LITERAL) && (flags & QLA_POTENTIAL_NONE)) return QLA_EINVAL;
+    if (size_t(nx) * size_t(ny) > (size_t(1) << 34)) return QLA_EINVAL;
+    if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255)) return QLA_EINVAL;
+
+    qla_ctx *c = new (std::nothrow) qla_ctx();
+    if (!c) return QLA_ENOMEM;
+    c->nx = nx;
+    c->ny = ny;
+    c->delta = delta;
+    c->prec = precision;
+    c->flags = flags;
+    c->P = (flags & QLA_TE_ONLY) ? 3 : 6;
+    c->vmode = (flags & QLA_POTENTIAL_LITERAL) ? V_LITERAL
+             : (flags & QLA_POTENTIAL_NONE)    ? V_NONE
+                                               : V_ROTATION;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return QLA_ECUDA; }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+
+    const Layout L = layout_for(nx, ny, precision, flags);
+    if (workspace) {
+        if (workspace_bytes < L.total) { delete c; return QLA_ENOMEM; }
+        c->ws = static_cast<char *>(workspace);
+        c->ws_bytes = workspace_bytes;
+    } else {
+        void *p = nullptr;
+        if (cudaMalloc(&p, L.total) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return QLA_ENOMEM;
+        }
+        c->ws = static_cast<char *>(p);
+        c->ws_bytes = L.total;
+        c->owns_ws = true;
+    }
+    c->pitch = L.pitch;
+    c->plane_elems = L.plane_elems;
+    c->state[0] = c->ws + L.state[0];
+    c->state[1] = c->ws + L.state[1];
+    c->coefC = c->ws + L.coefC;
+    c->coefV = c->ws + L.coefV;
+    c->n = reinterpret_cast<double *>(c->ws + L.n);
+    c->staging = reinterpret_cast<double *>(c->ws + L.staging);
+    c->partials = reinterpret_cast<double *>(c->ws + L.partials);
+    c->result = reinterpret_cast<double *>(c->ws + L.result);
+    c->energy_blocks = L.energy_blocks;
+    // both state buffers start at zero (pad columns included)
+    if (cudaMemsetAsync(c->ws + L.state[0], 0, L.coefC - L.state[0], c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->owns_ws) cudaFree(c->ws);
+        delete c;
+        return QLA_ECUDA;
+    }
+    *out = c;
+    return QLA_OK;
+}
+
+qla_status qla_set_medium(qla_ctx *c, const double *n_host) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (!n_host) return fail(c, QLA_EINVAL, "qla_set_medium: null n");
+    const size_t N = size_t(c->nx) * c->ny;
+    for (size_t k = 0; k < N; ++k) {
+        const double v = n_host[k];
+        if (!(v > 0.0) || !std::isfinite(v))
+            return fail(c, QLA_EINVAL, "qla_set_medium: n[%zu] = %g is not finite and > 0", k, v);
+    }
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, QLA_ECUDA, "qla_set_medium: cannot select device");
+    QLA_CUDA(c, cudaMemcpyAsync(c->staging, n_host, N * 8, cudaMemcpyHostToDevice, c->stream),
+             "qla_set_medium: copy");
+    QLA_CUDA(c, launch_medium(c), "qla_set_medium: kernel");
+    c->has_medium = true;
+    return QLA_OK;
+}
+
+qla_status qla_set_packet(qla_ctx *c, const qla_packet *p) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (!p) return fail(c, QLA_EINVAL, "qla_set_packet: null packet");
+    const double v[7] = {p->x0, p->y0, p->angle, p->k0, p->width, p->transverse_width,
+                         p->amplitude};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(c, QLA_EINVAL, "qla_set_packet: non-finite field");
+    if (!(p->width > 0.0) || p->transverse_width < 0.0)
+        return fail(c, QLA_EINVAL, "qla_set_packet: width must be > 0, transverse_width >= 0");
+    if (!c->has_medium) return fail(c, QLA_ESTATE, "qla_set_packet: set the medium first");
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, QLA_ECUDA, "qla_set_packet: cannot select device");
+    if (c->P == 6)
+        QLA_CUDA(c, cudaMemsetAsync(c->state[c->cur], 0,
+                                    c->plane_elems * (c->prec == QLA_FP64 ? 8 : 4) * 6, c->stream),
+                 "qla_set_packet: clear");
+    QLA_CUDA(c, launch_packet(c, *p), "qla_set_packet: kernel");
+    c->has_state = true;
+    return QLA_OK;
+}
+
+qla_status qla_set_state(qla_ctx *c, const double *q_host) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (!q_host) return fail(c, QLA_EINVAL, "qla_set_state: null state");
+    const size_t N = size_t(c->nx) * c->ny;
+    for (size_t k = 0; k < 6 * N; ++k)
+        if (!std::isfinite(q_host[k]))
+            return fail(c, QLA_EINVAL, "qla_set_state: non-finite value at %zu", k);
+    if (c->P == 3) {
+        const int absent[3] = {0, 1, 5};
+        for (int a : absent)
+            for (size_t k = 0; k < N; ++k)
+                if (q_host[size_t(a) * N + k] != 0.0)
+                    return fail(c, QLA_EINVAL,
+                                "qla_set_state: E_z context needs q%d == 0 (site %zu)", a, k);
+    }
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, QLA_ECUDA, "qla_set_state: cannot select device");
+    for (int comp = 0; comp < 6; ++comp) {
+        const int plane = c->P == 6 ? comp : plane_of<3>(comp);
+        if (plane < 0) continue;
+        QLA_CUDA(c, cudaMemcpyAsync(c->staging, q_host + size_t(comp) * N, N * 8,
+                                    cudaMemcpyHostToDevice, c->stream),
+                 "qla_set_state: copy");
+        QLA_CUDA(c, launch_from_f64(c, plane, c->staging), "qla_set_state: convert");
+    }
+    // the staging plane is reused per component: wait before the host buffer
+    // may change and before the next copy overwrites staging
+    QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_set_state: sync");
+    c->has_state = true;
+    return QLA_OK;
+}
+
+qla_status qla_get_state(qla_ctx *c, double *q_host) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (!q_host) return fail(c, QLA_EINVAL, "qla_get_state: null output");
+    const size_t N = size_t(c->nx) * c->ny;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, QLA_ECUDA, "qla_get_state: cannot select device");
+    for (int comp = 0; comp < 6; ++comp) {
+        const int plane = c->P == 6 ? comp : plane_of<3>(comp);
+        if (plane < 0) {
+            std::memset(q_host + size_t(comp) * N, 0, N * 8);
+            continue;
+        }
+        QLA_CUDA(c, launch_to_f64(c, plane, c->staging), "qla_get_state: convert");
+        QLA_CUDA(c, cudaMemcpyAsync(q_host + size_t(comp) * N, c->staging, N * 8,
+                                    cudaMemcpyDeviceToHost, c->stream),
+                 "qla_get_state: copy");
+        QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_get_state: sync");
+    }
+    return QLA_OK;
+}
+
+qla_status qla_step(qla_ctx *c, long long n_steps) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (n_steps < 0) return fail(c, QLA_EINVAL, "qla_step: n_steps < 0");
+    if (n_steps == 0) return QLA_OK;
+    if (!c->has_medium || !c->has_state)
+        return fail(c, QLA_ESTATE, "qla_step: set a medium and a state first");
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, QLA_ECUDA, "qla_step: cannot select device");
+    for (long long k = 0; k < n_steps; ++k) {
+        QLA_CUDA(c, launch_step_tile(c, c->state[c->cur], c->state[c->cur ^ 1]),
+                 "qla_step: kernel");
+        c->launches++;
+        c->cur ^= 1;
+    }
+    return QLA_OK;
+}
+
+qla_status qla_energy(qla_ctx *c, double *out) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (!out) return fail(c, QLA_EINVAL, "qla_energy: null output");
+    if (!c->has_state) return fail(c, QLA_ESTATE, "qla_energy: no state");
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, QLA_ECUDA, "qla_energy: cannot select device");
+    QLA_CUDA(c, launch_energy(c), "qla_energy: kernel");
+    QLA_CUDA(c, cudaMemcpyAsync(out, c->result, 8, cudaMemcpyDeviceToHost, c->stream),
+             "qla_energy: copy");
+    QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_energy: sync");
+    if (!std::isfinite(*out)) return fail(c, QLA_ENONFINITE, "qla_energy: energy is %g", *out);
+    return QLA_OK;
+}
+
+qla_status qla_fields(qla_ctx *c, double *Ex, double *Ey, double *Ez, double *Bx, double *By,
+                      double *Bz) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (!c->has_state || !c->has_medium) return fail(c, QLA_ESTATE, "qla_fields: no state");
+    double *outs[6] = {Ex, Ey, Ez, Bx, By, Bz};
+    const size_t N = size_t(c->nx) * c->ny;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, QLA_ECUDA, "qla_fields: cannot select device");
+    for (int comp = 0; comp < 6; ++comp) {
+        if (!outs[comp]) continue;
+        QLA_CUDA(c, launch_fields(c, comp, c->staging), "qla_fields: kernel");
+        QLA_CUDA(c, cudaMemcpyAsync(outs[comp], c->staging, N * 8, cudaMemcpyDeviceToHost,
+                                    c->stream),
+                 "qla_fields: copy");
+        QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_fields: sync");
+    }
+    return QLA_OK;
+}
+
+qla_status qla_probe(qla_ctx *c, int count, const int *i, const int *j, double *out) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (count < 0 || count > 65536) return fail(c, QLA_EINVAL, "qla_probe: count %d", count);
+    if (count == 0) return QLA_OK;
+    if (!i || !j || !out) return fail(c, QLA_EINVAL, "qla_probe: null pointer");
+    if (!c->has_state) return fail(c, QLA_ESTATE, "qla_probe: no state");
+    std::vector<int> ij(2 * size_t(count));
+    for (int k = 0; k < count; ++k) {
+        if (i[k] < 0 || i[k] >= c->nx || j[k] < 0 || j[k] >= c->ny)
+            return fail(c, QLA_EINVAL, "qla_probe: site %d = (%d, %d) outside the lattice", k,
+                        i[k], j[k]);
+        ij[k] = i[k];
+        ij[count + k] = j[k];
+    }
+    // the staging plane (nx*ny doubles) holds the indices and the output;
+    // a probe list larger than it is rejected
+    const size_t need = 2 * size_t(count) * sizeof(int) + 6 * size_t(count) * sizeof(double) + 64;
+    if (need > size_t(c->nx) * c->ny * 8)
+        return fail(c, QLA_EINVAL, "qla_probe: %d sites do not fit this lattice's staging", count);
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, QLA_ECUDA, "qla_probe: cannot select device");
+    double *dout = c->staging;
+    int *dij = reinterpret_cast<int *>(c->staging + 6 * size_t(count));
+    QLA_CUDA(c, cudaMemcpyAsync(dij, ij.data(), ij.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                c->stream),
+             "qla_probe: copy in");
+    QLA_CUDA(c, launch_probe(c, count, dij, dout), "qla_probe: kernel");
+    QLA_CUDA(c, cudaMemcpyAsync(out, dout, 6 * size_t(count) * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream),
+             "qla_probe: copy out");
+    QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_probe: sync");
+    return QLA_OK;
+}
+
+qla_status qla_set_time_block(qla_ctx *c, int k) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (k < 0 || k > QLA_MAX_TIME_BLOCK)
+        return fail(c, QLA_EINVAL, "qla_set_time_block: k = %d outside 0..%d", k,
+                    QLA_MAX_TIME_BLOCK);
+    c->time_block = k;
+    return QLA_OK;
+}
+
+long long qla_launch_count(const qla_ctx *c) { return c ? c->launches : 0; }
+
+const char *qla_last_error(const qla_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+const char *qla_status_string(qla_status s) {
+    switch (s) {
+    case QLA_OK: return "QLA_OK";
+    case QLA_EINVAL: return "QLA_EINVAL";
+    case QLA_ESTATE: return "QLA_ESTATE";
+    case QLA_ENOMEM: return "QLA_ENOMEM";
+    case QLA_ECUDA: return "QLA_ECUDA";
+    case QLA_ETIMEOUT: return "QLA_ETIMEOUT";
+    case QLA_ENONFINITE: return "QLA_ENONFINITE";
+    }
+    return "QLA_UNKNOWN";
+}
+
+void qla_destroy(qla_ctx *c) {
+    if (!c) return;
+    {
+        DeviceGuard dg(c->device);
+        cudaStreamSynchronize(c->stream);
+        if (c->owns_ws) cudaFree(c->ws);
+        cudaGetLastError();
+    }
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,194 @@
+// Internal declarations of libqla: the context, the coefficient records and
+// the device-side rotation helpers shared by the kernels.  Not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/qla.h"
+
+namespace qla {
+
+// ----------------------------------------------------------------------------
+// Amplitude numbering (Eq. 3b3) and plane mapping.  A context stores P live
+// planes: P = 6 holds q0..q5 in order; P = 3 (E_z polarisation) holds
+// q2, q3, q4 as planes 0, 1, 2.  plane_of<P>(c) is -1 for an absent q_c.
+// ----------------------------------------------------------------------------
+template <int P>
+__host__ __device__ constexpr int plane_of(int c) {
+    return P == 6 ? c : (c >= 2 && c <= 4 ? c - 2 : -1);
+}
+
+// ----------------------------------------------------------------------------
+// The eight collisions of one evolution operator U (Eqs. 2e6, 2e9).
+//
+// Written as acting on Q, U = C^ S1- C S1+ | C^ S2+ C S2- | C S1+ C^ S1- |
+// C S2- C^ S2+ (each group read left to right = order of action; S1 is S14
+// along x, S03 along y; S2 is S25).  Inside a group the shifted component
+// returns to its place after the second collision, so each group is a
+// site-local collision followed by a collision of "bonds" that pair the
+// unshifted component at site i with the shifted one at site i + sigma,
+// rotated with the angle of site i.  No data moves: U is eight layers of
+// disjoint 2x2 rotations.  Per layer: adjoint flag, which component of each
+// pair is the shifted one (0 none, 1 the S1 mover, 2 the S25 mover), sigma.
+// ----------------------------------------------------------------------------
+struct Layer { int dag, mover, shift; };
+__host__ __device__ constexpr Layer layer_of(int l) {
+    return l == 0 ? Layer{1, 0, 0} : l == 1 ? Layer{0, 1, -1}
+         : l == 2 ? Layer{1, 0, 0} : l == 3 ? Layer{0, 2, +1}
+         : l == 4 ? Layer{0, 0, 0} : l == 5 ? Layer{1, 1, +1}
+         : l == 6 ? Layer{0, 0, 0} : Layer{1, 2, -1};
+}
+
+// Pairs rotated by a collision.  a is the first component of the pair in
+// the printed matrix (its row holds cos, -g sin), b the second; m1 is the
+// component moved by S14 (x) or S03 (y), the other is moved by S25.
+//   x (Eq. 2e3):  (q1, q5) with q1 = S14 mover;  (q2, q4) with q4 = S14 mover
+//   y (Eq. 2e8):  (q0, q5) with q0 = S03 mover;  (q2, q3) with q3 = S03 mover
+// Sign g of the sine: C_x rotates by +theta, C_y by -theta; adjoints flip.
+struct Pair { int a, b; bool a_is_m1; };
+__host__ __device__ constexpr Pair pair_of(bool xdir, int k) {
+    return xdir ? (k == 0 ? Pair{1, 5, true} : Pair{2, 4, false})
+                : (k == 0 ? Pair{0, 5, true} : Pair{2, 3, false});
+}
+
+// ----------------------------------------------------------------------------
+// Coefficient records, one per site.
+//   FP64: CoefC = (cos theta, sin theta); CoefV = (cos phi_x, sin phi_x,
+//         cos phi_y, sin phi_y) with phi = beta/2 (rotation reading) or beta
+//         (printed shear).
+//   FP32: CoefC = (gamma_hi, s_hi, gamma_lo, s_lo), gamma = 1 - cos theta,
+//         s = sin theta, each split into an FP32 value and the FP32 rounding
+//         of the remainder, so the collision angle and norm carry ~48 bits;
+//         CoefV = (gamma_x, s_x, gamma_y, s_y) single words.
+// ----------------------------------------------------------------------------
+template <typename T> struct Coef;
+template <> struct Coef<double> { using C = double2; using V = double4; };
+template <> struct Coef<float>  { using C = float4;  using V = float4; };
+
+// (a, b) <- [[c, -g s], [g s, c]] (a, b) with g = +-1.
+__device__ __forceinline__ void rotate(double &a, double &b, double2 k, double g) {
+    const double s = g * k.y;
+    const double na = k.x * a - s * b;
+    const double nb = s * a + k.x * b;
+    a = na;
+    b = nb;
+}
+
+// Same rotation written as a - (gamma a + g s b), b - (gamma b - g s a) with
+// two-word gamma and s; the small terms are accumulated first.
+__device__ __forceinline__ void rotate(float &a, float &b, float4 k, float g) {
+    const float sh = g * k.y, sl = g * k.w;
+    const float ta = fmaf(k.x, a, fmaf(sh, b, fmaf(k.z, a, sl * b)));
+    const float tb = fmaf(k.x, b, fmaf(-sh, a, fmaf(k.z, b, -sl * a)));
+    a -= ta;
+    b -= tb;
+}
+
+// Single-word rotation used for V in FP32: (gamma, s) = (1 - cos, sin).
+__device__ __forceinline__ void rotate1(float &a, float &b, float gam, float s, float g) {
+    const float sg = g * s;
+    const float ta = fmaf(gam, a, sg * b);
+    const float tb = fmaf(gam, b, -sg * a);
+    a -= ta;
+    b -= tb;
+}
+__device__ __forceinline__ void rotate1(double &a, double &b, double c, double s, double g) {
+    const double sg = g * s;
+    const double na = c * a - sg * b;
+    const double nb = sg * a + c * b;
+    a = na;
+    b = nb;
+}
+
+// Printed shear row: y <- c y + g s x (only y changes).
+__device__ __forceinline__ void shear1(float x, float &y, float gam, float s, float g) {
+    y -= fmaf(gam, y, -g * s * x);
+}
+__device__ __forceinline__ void shear1(double x, double &y, double c, double s, double g) {
+    y = c * y + g * s * x;
+}
+
+enum VMode { V_ROTATION = 0, V_LITERAL = 1, V_NONE = 2 };
+
+// Potential operators at one site: V_x then V_y (Eq. 2e14).  q[] holds the
+// six amplitudes (entries absent in E_z mode are ignored).  kv = CoefV.
+template <typename T, int P, int VM, typename KV>
+__device__ __forceinline__ void apply_potential(T (&q)[6], KV kv) {
+    if constexpr (VM == V_ROTATION) {
+        // V_x: (q2,q4) by [[c, s], [-s, c]]; (q1,q5) by [[c, -s], [s, c]]
+        rotate1(q[2], q[4], kv.x, kv.y, T(-1));
+        if constexpr (P == 6) rotate1(q[1], q[5], kv.x, kv.y, T(1));
+        // V_y: (q2,q3) by [[c, -s], [s, c]]; (q0,q5) by [[c, s], [-s, c]]
+        rotate1(q[2], q[3], kv.z, kv.w, T(1));
+        if constexpr (P == 6) rotate1(q[0], q[5], kv.z, kv.w, T(-1));
+    } else if constexpr (VM == V_LITERAL) {
+        // V_x: q4 <- -sin q2 + cos q4; q5 <- +sin q1 + cos q5
+        shear1(q[2], q[4], kv.x, kv.y, T(-1));
+        if constexpr (P == 6) shear1(q[1], q[5], kv.x, kv.y, T(1));
+        // V_y: q3 <- sin q2 + cos q3; q5 <- -sin q0 + cos q5
+        shear1(q[2], q[3], kv.z, kv.w, T(1));
+        if constexpr (P == 6) shear1(q[0], q[5], kv.z, kv.w, T(-1));
+    }
+}
+
+__host__ __device__ inline int wrap(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+}  // namespace qla
+
+// ----------------------------------------------------------------------------
+// Context.
+// ----------------------------------------------------------------------------
+struct qla_ctx {
+    int nx = 0, ny = 0, pitch = 0;  // pitch: elements per stored row
+    double delta = 1.0;
+    int prec = 0;                   // qla_precision
+    unsigned flags = 0;
+    int P = 6;                      // live planes
+    int vmode = 0;                  // qla::VMode
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    bool owns_ws = false;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    void *state[2] = {nullptr, nullptr};
+    int cur = 0;
+    size_t plane_elems = 0;         // ny * pitch
+    void *coefC = nullptr;
+    void *coefV = nullptr;
+    double *n = nullptr;            // ny * pitch
+    double *staging = nullptr;      // ny * nx
+    double *partials = nullptr;     // energy partial sums
+    double *result = nullptr;       // final energy (device)
+    int energy_blocks = 0;
+    bool has_medium = false, has_state = false;
+    int time_block = 0;
+    long long launches = 0;
+    qla_status sticky = QLA_OK;
+    std::string err;
+};
+
+namespace qla {
+// Workspace layout: offsets of each region (bytes, 256-aligned).
+struct Layout {
+    size_t state[2], coefC, coefV, n, staging, partials, result, total;
+    size_t plane_elems;
+    int pitch, energy_blocks;
+};
+Layout layout_for(int nx, int ny, int prec, unsigned flags);
+
+// Launchers (host), each returns the cudaError_t of its launch.
+cudaError_t launch_medium(qla_ctx *c);
+cudaError_t launch_packet(qla_ctx *c, const qla_packet &p);
+cudaError_t launch_from_f64(qla_ctx *c, int plane, const double *src);
+cudaError_t launch_to_f64(qla_ctx *c, int plane, double *dst);
+cudaError_t launch_fields(qla_ctx *c, int comp, double *dst);
+cudaError_t launch_energy(qla_ctx *c);
+cudaError_t launch_probe(qla_ctx *c, int count, const int *ij_dev, double *out_dev);
+cudaError_t launch_step_tile(qla_ctx *c, const void *in, void *out);
+}  // namespace qla

@@ -33,22 +33,26 @@ def ellipse_medium(nx: int, ny: int, delta: float, a: float, b: float,
                    n_in: float, n_out: float, edge: float, angle: float = 0.0,
                    centre=None) -> np.ndarray:
     """Index map (ny, nx) float64 of a smooth ellipse; lengths in physical
-    units (cells * delta).  ``centre`` defaults to the box centre."""
+    units (cells * delta).  ``centre`` defaults to the box centre.  Built in
+    row blocks so large lattices need little temporary memory."""
     Lx, Ly = nx * delta, ny * delta
     xc, yc = (0.5 * Lx, 0.5 * Ly) if centre is None else centre
-    x = np.arange(nx) * delta
-    y = np.arange(ny) * delta
-    dx = _min_image(x[None, :] - xc, Lx)
-    dy = _min_image(y[:, None] - yc, Ly)
     ca, sa = math.cos(angle), math.sin(angle)
-    X = dx * ca + dy * sa
-    Y = -dx * sa + dy * ca
-    rho = np.sqrt((X / a) ** 2 + (Y / b) ** 2)
-    g = np.sqrt((X / a ** 2) ** 2 + (Y / b ** 2) ** 2)
-    with np.errstate(divide="ignore", invalid="ignore"):
-        grad = np.where(rho > 0, g / np.where(rho > 0, rho, 1.0), 1.0)
-        s = np.where(rho > 0, (rho - 1.0) / grad, -min(a, b))
-    return n_out + (n_in - n_out) * 0.5 * (1.0 - np.tanh(s / edge))
+    dx = _min_image(np.arange(nx) * delta - xc, Lx)[None, :]
+    out = np.empty((ny, nx))
+    rows = max(1, (1 << 22) // max(nx, 1))
+    for j0 in range(0, ny, rows):
+        j1 = min(ny, j0 + rows)
+        dy = _min_image(np.arange(j0, j1) * delta - yc, Ly)[:, None]
+        X = dx * ca + dy * sa
+        Y = -dx * sa + dy * ca
+        rho = np.sqrt((X / a) ** 2 + (Y / b) ** 2)
+        g = np.sqrt((X / a ** 2) ** 2 + (Y / b ** 2) ** 2)
+        pos = rho > 0
+        grad = np.where(pos, g / np.where(pos, rho, 1.0), 1.0)
+        s = np.where(pos, (rho - 1.0) / grad, -min(a, b))
+        out[j0:j1] = n_out + (n_in - n_out) * 0.5 * (1.0 - np.tanh(s / edge))
+    return out
 
 
 def slab_medium(nx: int, ny: int, delta: float, x1: float, x2: float,

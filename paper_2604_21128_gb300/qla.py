@@ -1,0 +1,285 @@
+"""Thin Python binding of libqla (the C ABI declared in include/qla.h).
+
+The module-level functions carry the C names and only marshal arguments:
+every step of the computation runs in the CUDA library.  ``Grid`` wraps one
+context and takes its device workspace and stream from PyTorch.
+
+Loading fails loudly: if ``libqla.so`` has not been built, or no CUDA device
+is present when a context is created, an exception is raised.  There is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqla.so")
+
+QLA_FP64, QLA_FP32 = 0, 1
+QLA_TE_ONLY = 1
+QLA_POTENTIAL_LITERAL = 2
+QLA_POTENTIAL_NONE = 4
+QLA_MAX_TIME_BLOCK = 8
+
+STATUS = {0: "QLA_OK", 1: "QLA_EINVAL", 2: "QLA_ESTATE", 3: "QLA_ENOMEM",
+          4: "QLA_ECUDA", 5: "QLA_ETIMEOUT", 6: "QLA_ENONFINITE"}
+
+
+class QLAError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__("%s%s" % (STATUS.get(status, str(status)), (": " + msg) if msg else ""))
+
+
+class qla_packet(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("x0", "y0", "angle", "k0", "width", "transverse_width", "amplitude")]
+
+
+_lib = None
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+def load():
+    """Load libqla.so (raises OSError if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError("libqla.so not built: run __graft_entry__.build() "
+                          "(or python paper_2604_21128_gb300/build.py)")
+        lib = ctypes.CDLL(LIB_PATH)
+        c_int, c_ll, c_sz, c_vp, c_u = (ctypes.c_int, ctypes.c_longlong, ctypes.c_size_t,
+                                        ctypes.c_void_p, ctypes.c_uint)
+        lib.qla_workspace_bytes.argtypes = [c_int, c_int, c_int, c_u]
+        lib.qla_workspace_bytes.restype = c_sz
+        lib.qla_init_grid.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, ctypes.c_double,
+                                      c_int, c_u, c_vp, c_vp, c_sz]
+        for name, args in (("qla_set_medium", [c_vp, c_vp]),
+                           ("qla_set_packet", [c_vp, ctypes.POINTER(qla_packet)]),
+                           ("qla_set_state", [c_vp, c_vp]),
+                           ("qla_get_state", [c_vp, c_vp]),
+                           ("qla_step", [c_vp, c_ll]),
+                           ("qla_energy", [c_vp, _DP]),
+                           ("qla_fields", [c_vp] + [c_vp] * 6),
+                           ("qla_set_time_block", [c_vp, c_int]),
+                           ("qla_probe", [c_vp, c_int, c_vp, c_vp, c_vp])):
+            getattr(lib, name).argtypes = args
+            getattr(lib, name).restype = c_int
+        lib.qla_init_grid.restype = c_int
+        lib.qla_launch_count.argtypes = [c_vp]
+        lib.qla_launch_count.restype = c_ll
+        lib.qla_last_error.argtypes = [c_vp]
+        lib.qla_last_error.restype = ctypes.c_char_p
+        lib.qla_status_string.argtypes = [c_int]
+        lib.qla_status_string.restype = ctypes.c_char_p
+        lib.qla_destroy.argtypes = [c_vp]
+        lib.qla_destroy.restype = None
+        _lib = lib
+    return _lib
+
+
+def _check(ctx, status):
+    if status != 0:
+        msg = load().qla_last_error(ctx).decode() if ctx else ""
+        raise QLAError(status, msg)
+
+
+def _host_ptr(a, n_expected, writable=False):
+    """Pointer to a contiguous FP64 host buffer (numpy array or CPU tensor)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("host arrays must be C-contiguous float64")
+        if writable and not a.flags.writeable:
+            raise TypeError("output array is read-only")
+        if a.size != n_expected:
+            raise ValueError("expected %d values, got %d" % (n_expected, a.size))
+        return ctypes.c_void_p(a.ctypes.data)
+    import torch
+    if not isinstance(a, torch.Tensor) or a.device.type != "cpu" or a.dtype != torch.float64 \
+            or not a.is_contiguous() or a.numel() != n_expected:
+        raise TypeError("host buffers must be contiguous float64 CPU tensors or numpy arrays")
+    return ctypes.c_void_p(a.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# C-named functions
+# ---------------------------------------------------------------------------
+
+def qla_workspace_bytes(nx, ny, precision, flags):
+    return int(load().qla_workspace_bytes(nx, ny, precision, flags))
+
+
+def qla_init_grid(nx, ny, delta, precision, flags, cuda_stream, workspace, workspace_bytes):
+    ctx = ctypes.c_void_p()
+    st = load().qla_init_grid(ctypes.byref(ctx), int(nx), int(ny), float(delta), int(precision),
+                              int(flags), ctypes.c_void_p(cuda_stream or 0),
+                              ctypes.c_void_p(workspace or 0), int(workspace_bytes))
+    _check(None, st)
+    return ctx
+
+
+def qla_set_medium(ctx, n, nx, ny):
+    _check(ctx, load().qla_set_medium(ctx, _host_ptr(n, nx * ny)))
+
+
+def qla_set_packet(ctx, x0, y0, angle, k0, width, transverse_width=0.0, amplitude=1.0):
+    p = qla_packet(float(x0), float(y0), float(angle), float(k0), float(width),
+                   float(transverse_width), float(amplitude))
+    _check(ctx, load().qla_set_packet(ctx, ctypes.byref(p)))
+
+
+def qla_set_state(ctx, q, nx, ny):
+    _check(ctx, load().qla_set_state(ctx, _host_ptr(q, 6 * nx * ny)))
+
+
+def qla_get_state(ctx, out, nx, ny):
+    _check(ctx, load().qla_get_state(ctx, _host_ptr(out, 6 * nx * ny, writable=True)))
+
+
+def qla_step(ctx, n_steps):
+    _check(ctx, load().qla_step(ctx, int(n_steps)))
+
+
+def qla_energy(ctx):
+    v = ctypes.c_double()
+    _check(ctx, load().qla_energy(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def qla_fields(ctx, nx, ny, Ex=None, Ey=None, Ez=None, Bx=None, By=None, Bz=None):
+    ptrs = [_host_ptr(a, nx * ny, writable=True) if a is not None else ctypes.c_void_p(0)
+            for a in (Ex, Ey, Ez, Bx, By, Bz)]
+    _check(ctx, load().qla_fields(ctx, *ptrs))
+
+
+def qla_probe(ctx, i, j):
+    """Amplitudes q0..q5 at sites (i[k], j[k]); returns an array (count, 6)."""
+    i = np.ascontiguousarray(i, dtype=np.int32)
+    j = np.ascontiguousarray(j, dtype=np.int32)
+    if i.shape != j.shape or i.ndim != 1:
+        raise ValueError("i and j must be 1-D of equal length")
+    out = np.empty((i.size, 6))
+    _check(ctx, load().qla_probe(ctx, int(i.size), ctypes.c_void_p(i.ctypes.data),
+                                 ctypes.c_void_p(j.ctypes.data), ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def qla_set_time_block(ctx, k):
+    _check(ctx, load().qla_set_time_block(ctx, int(k)))
+
+
+def qla_launch_count(ctx):
+    return int(load().qla_launch_count(ctx))
+
+
+def qla_last_error(ctx):
+    return load().qla_last_error(ctx).decode()
+
+
+def qla_destroy(ctx):
+    load().qla_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Grid:
+    """One QLA lattice on a CUDA device.
+
+    precision: "fp64" or "fp32"; te_only: evolve only q2, q3, q4;
+    potential: "rotation" (default reading), "literal" or "none".
+    The device workspace is a torch uint8 tensor; work is enqueued on
+    ``stream`` (default: torch's current stream on the device)."""
+
+    def __init__(self, nx, ny, delta=1.0, precision="fp64", te_only=False,
+                 potential="rotation", device=None, stream=None):
+        import torch
+        load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libqla needs a CUDA device; none is available")
+        self.nx, self.ny, self.delta = int(nx), int(ny), float(delta)
+        self.precision = {"fp64": QLA_FP64, "fp32": QLA_FP32}[precision]
+        flags = (QLA_TE_ONLY if te_only else 0) | {
+            "rotation": 0, "literal": QLA_POTENTIAL_LITERAL, "none": QLA_POTENTIAL_NONE}[potential]
+        self.flags = flags
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else (device if isinstance(device, int) else device.index or 0))
+        nbytes = qla_workspace_bytes(self.nx, self.ny, self.precision, flags)
+        if nbytes == 0:
+            raise QLAError(1, "invalid lattice")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self._ctx = qla_init_grid(self.nx, self.ny, self.delta, self.precision, flags,
+                                      self.stream.cuda_stream, self.workspace.data_ptr(), nbytes)
+
+    # context-managed device selection for every call
+    def _dev(self):
+        import torch
+        return torch.cuda.device(self.device)
+
+    def set_medium(self, n):
+        with self._dev():
+            qla_set_medium(self._ctx, n, self.nx, self.ny)
+
+    def set_packet(self, x0, y0, angle, k0, width, transverse_width=0.0, amplitude=1.0):
+        with self._dev():
+            qla_set_packet(self._ctx, x0, y0, angle, k0, width, transverse_width, amplitude)
+
+    def set_state(self, q):
+        with self._dev():
+            qla_set_state(self._ctx, q, self.nx, self.ny)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty((6, self.ny, self.nx))
+        with self._dev():
+            qla_get_state(self._ctx, out, self.nx, self.ny)
+        return out
+
+    def step(self, n_steps):
+        with self._dev():
+            qla_step(self._ctx, n_steps)
+
+    def energy(self):
+        with self._dev():
+            return qla_energy(self._ctx)
+
+    def fields(self):
+        out = {k: np.empty((self.ny, self.nx)) for k in ("Ex", "Ey", "Ez", "Bx", "By", "Bz")}
+        with self._dev():
+            qla_fields(self._ctx, self.nx, self.ny, **out)
+        return out
+
+    def probe(self, i, j):
+        with self._dev():
+            return qla_probe(self._ctx, i, j)
+
+    def set_time_block(self, k):
+        qla_set_time_block(self._ctx, k)
+
+    @property
+    def launches(self):
+        return qla_launch_count(self._ctx)
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            with self._dev():
+                qla_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

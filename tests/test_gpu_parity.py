@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the oracle.
+
+Bars: FP64 within 1e-12 relative L2 (the stated target after 400 steps);
+FP32 within the error budget derived from FP32 rounding; everything on the
+same seeded inputs.  Sizes span several tiles with ragged tails; a separate
+check samples sites of the full 8192^2 workload in the launch configuration
+the benchmark times.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_21128_gb300 import build as qbuild
+from paper_2604_21128_gb300 import inputs, qla
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    qbuild.build()
+    oracle.set_threads(os.cpu_count() or 1)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def gpu_run(n, delta, steps, q0=None, packet=None, precision="fp64", te=False,
+            potential="rotation", time_block=0):
+    ny, nx = n.shape
+    with qla.Grid(nx, ny, delta, precision, te_only=te, potential=potential) as g:
+        if time_block:
+            g.set_time_block(time_block)
+        g.set_medium(n)
+        if q0 is not None:
+            g.set_state(q0)
+        else:
+            g.set_packet(**packet)
+        g.step(steps)
+        return g.get_state(), g.energy()
+
+
+# ---------------------------------------------------------------------------
+# FP64: 1e-12 relative L2
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("te", [False, True])
+def test_ellipse_256_fp64_400_steps(te):
+    w = inputs.ellipse_256()
+    n = w.medium()
+    pk = w.packet.as_dict()
+    q0 = oracle.packet(n, w.delta, **pk)
+    want = oracle.run(q0, n, w.delta, w.steps)
+    got, e = gpu_run(n, w.delta, w.steps, packet=pk, te=te)
+    assert rel_l2(got, want) <= 1e-12
+    assert abs(e / oracle.energy(want) - 1) <= 1e-12
+    assert np.all(got[[0, 1, 5]] == 0)
+
+
+@pytest.mark.parametrize("potential", ["rotation", "literal", "none"])
+@pytest.mark.parametrize("shape", [(67, 45), (33, 17), (8, 8), (9, 9), (1, 1), (3, 5),
+                                   (130, 3), (40, 96)])
+def test_random_state_fp64_ragged(shape, potential):
+    nx, ny = shape
+    n = inputs.random_medium(nx, ny, seed=nx * 100 + ny, lo=1.0, hi=3.5)
+    q0 = inputs.random_state(nx, ny, seed=nx + 7 * ny)
+    want = oracle.run(q0, n, 0.7, 7, potential)
+    got, _ = gpu_run(n, 0.7, 7, q0=q0, potential=potential)
+    assert rel_l2(got, want) <= 1e-12, (shape, potential, rel_l2(got, want))
+
+
+def test_random_state_fp64_te_matches_six_plane():
+    nx, ny = 50, 38
+    n = inputs.random_medium(nx, ny, seed=3)
+    q0 = inputs.random_state(nx, ny, seed=4, planes=3)
+    want = oracle.run(q0, n, 1.0, 11)
+    got, _ = gpu_run(n, 1.0, 11, q0=q0, te=True)
+    assert rel_l2(got, want) <= 1e-12
+
+
+def test_packet_matches_oracle():
+    w = inputs.scaled(inputs.ellipse_256(), 200, 136, 0)
+    n = w.medium()
+    for pk in (w.packet.as_dict(),
+               dict(x0=13.3, y0=120.0, angle=2.2, k0=0.4, width=9.0, transverse_width=17.0,
+                    amplitude=0.7)):
+        want = oracle.packet(n, w.delta, **pk)
+        for prec, tol in (("fp64", 1e-14), ("fp32", 1e-7)):
+            got, _ = gpu_run(n, w.delta, 0, packet=pk, precision=prec)
+            assert np.max(np.abs(got - want)) <= tol * np.abs(want).max()
+
+
+def test_fields_and_energy_match_oracle():
+    w = inputs.scaled(inputs.ellipse_256(), 96, 80, 30)
+    n = w.medium()
+    pk = w.packet.as_dict()
+    q = oracle.run(oracle.packet(n, w.delta, **pk), n, w.delta, 30)
+    want = oracle.fields(q, n)
+    with qla.Grid(96, 80, w.delta) as g:
+        g.set_medium(n)
+        g.set_packet(**pk)
+        g.step(30)
+        f = g.fields()
+        e1, e2 = g.energy(), g.energy()
+    for c, k in enumerate(("Ex", "Ey", "Ez", "Bx", "By", "Bz")):
+        assert np.max(np.abs(f[k] - want[c])) <= 1e-13
+    assert e1 == e2  # fixed reduction order
+    assert abs(e1 / oracle.energy(q) - 1) <= 1e-13
+
+
+def test_checkpoint_resume_is_bitwise():
+    nx, ny = 72, 56
+    n = inputs.random_medium(nx, ny, seed=8)
+    for prec in ("fp64", "fp32"):
+        q0 = inputs.random_state(nx, ny, seed=9)
+        full, _ = gpu_run(n, 1.0, 20, q0=q0, precision=prec)
+        half, _ = gpu_run(n, 1.0, 10, q0=q0, precision=prec)
+        resumed, _ = gpu_run(n, 1.0, 10, q0=half, precision=prec)
+        assert np.array_equal(full, resumed), prec
+
+
+# ---------------------------------------------------------------------------
+# FP32: stored and rotated in FP32 (collision coefficients in two words)
+# ---------------------------------------------------------------------------
+
+def test_fp32_ellipse_256_400_steps():
+    w = inputs.ellipse_256()
+    n = w.medium()
+    pk = w.packet.as_dict()
+    want = oracle.run(oracle.packet(n, w.delta, **pk), n, w.delta, w.steps)
+    got, e = gpu_run(n, w.delta, w.steps, packet=pk, precision="fp32", te=True)
+    err = rel_l2(got, want)
+    assert err <= 2e-6, err
+    assert abs(e / oracle.energy(want) - 1) <= 1e-5
+
+
+def test_fp32_ten_thousand_steps_error_budget():
+    """FP32 against the FP64 oracle after 10^4 steps: relative L2 <= 1e-5
+    (the ellipse workload scaled to 128^2, so the packet crosses the box and
+    the dielectric many times)."""
+    w = inputs.scaled(inputs.ellipse_256(), 128, 128, 10000)
+    n = w.medium()
+    pk = w.packet.as_dict()
+    want = oracle.run(oracle.packet(n, w.delta, **pk), n, w.delta, w.steps)
+    got, e = gpu_run(n, w.delta, w.steps, packet=pk, precision="fp32", te=True)
+    err = rel_l2(got, want)
+    drift = e / oracle.energy(want) - 1
+    print("fp32 1e4 steps: rel L2 %.3e, energy drift %.3e" % (err, drift))
+    assert err <= 1e-5
+    assert abs(drift) <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Error paths
+# ---------------------------------------------------------------------------
+
+def test_error_paths():
+    with qla.Grid(16, 12) as g:
+        with pytest.raises(qla.QLAError) as e:
+            g.step(1)
+        assert e.value.status == 2  # ESTATE
+        with pytest.raises(qla.QLAError) as e:
+            g.set_packet(1.0, 1.0, 0.0, 0.1, 3.0)
+        assert e.value.status == 2
+        bad = np.ones((12, 16))
+        bad[3, 4] = 0.0
+        with pytest.raises(qla.QLAError) as e:
+            g.set_medium(bad)
+        assert e.value.status == 1
+        bad[3, 4] = float("nan")
+        with pytest.raises(qla.QLAError):
+            g.set_medium(bad)
+        g.set_medium(np.ones((12, 16)))
+        with pytest.raises(qla.QLAError):
+            g.set_packet(1.0, 1.0, 0.0, 0.1, 0.0)
+        with pytest.raises(qla.QLAError):
+            g.step(-1)
+        with pytest.raises(qla.QLAError):
+            g.probe([16], [0])
+    with qla.Grid(16, 12, te_only=True) as g:
+        g.set_medium(np.ones((12, 16)))
+        q = np.zeros((6, 12, 16))
+        q[0, 1, 1] = 1.0
+        with pytest.raises(qla.QLAError) as e:
+            g.set_state(q)
+        assert e.value.status == 1
+        g.step(0)  # a no-op, even without a state
+        q[0, 1, 1] = 0.0
+        q[2, 1, 1] = 1.0
+        g.set_state(q)
+        g.step(3)
+        assert g.energy() == pytest.approx(1.0, rel=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Full size: 8192^2, the benchmark's precision, planes and launch settings
+# ---------------------------------------------------------------------------
+
+def test_full_size_8192_sampled_sites():
+    """Run the benchmark workload (8192^2, FP32, E_z planes, default time
+    block) for 24 steps and compare sampled sites with the oracle run on a
+    periodic window around each site (exact inside the dependence cone)."""
+    w = inputs.ellipse_8192()
+    steps = 24
+    n = w.medium()
+    pk = w.packet.as_dict()
+    rng = np.random.default_rng(2026)
+    x0 = int(pk["x0"])
+    ii = np.concatenate([x0 + rng.integers(-400, 400, 10), rng.integers(0, w.nx, 4),
+                         [0, w.nx - 1]])
+    jj = np.concatenate([rng.integers(0, w.ny, 14), [0, w.ny - 1]])
+    with qla.Grid(w.nx, w.ny, w.delta, "fp32", te_only=True) as g:
+        g.set_medium(n)
+        g.set_packet(**pk)
+        g.step(steps)
+        got = g.probe(ii, jj)
+        e = g.energy()
+    half = oracle.reach_per_step() * steps + 2
+    for k in range(len(ii)):
+        want = oracle.run_window(n, w.delta, pk, steps, (int(ii[k]), int(jj[k])), half)
+        assert np.max(np.abs(got[k] - want)) <= 2e-5, (ii[k], jj[k], got[k], want)
+    assert np.all(got[:, [0, 1, 5]] == 0)
+    assert math.isfinite(e) and e > 0
