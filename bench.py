@@ -50,7 +50,9 @@ def parse():
 def workload(name):
     from paper_2604_21128_gb300 import inputs
     table = {"ellipse_8192": inputs.ellipse_8192, "bubble_16384": inputs.bubble_16384,
-             "ellipse_256": inputs.ellipse_256}
+             "ellipse_256": inputs.ellipse_256,
+             # the 8192^2 geometry on 4096^2: a small case for ncu captures
+             "ellipse_4096": lambda: inputs.scaled(inputs.ellipse_8192(), 4096, 4096, 20000)}
     return table[name]()
 
 

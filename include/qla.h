@@ -148,6 +148,16 @@ qla_status qla_probe(qla_ctx *ctx, int count, const int *i, const int *j, double
 #define QLA_MAX_TIME_BLOCK 8
 qla_status qla_set_time_block(qla_ctx *ctx, int k);
 
+/* Step kernel.  QLA_KERNEL_AUTO picks the register-resident marching
+ * kernel when nx is a multiple of its per-lane column count (4 for FP32
+ * E_z contexts, 2 otherwise), nx >= 32 times that count and ny >= 8, and the
+ * shared-memory tile kernel otherwise.  QLA_KERNEL_TILE / QLA_KERNEL_MARCH
+ * force one (QLA_EINVAL if the marching kernel does not support the
+ * lattice).  Both compute the same operator sequence; FP64 results agree to
+ * rounding order. */
+typedef enum { QLA_KERNEL_AUTO = 0, QLA_KERNEL_TILE = 1, QLA_KERNEL_MARCH = 2 } qla_step_kernel;
+qla_status qla_set_step_kernel(qla_ctx *ctx, int kernel);
+
 /* Kernel launches enqueued by this context since creation (diagnostics). */
 long long qla_launch_count(const qla_ctx *ctx);
 

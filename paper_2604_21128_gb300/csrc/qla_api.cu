@@ -270,8 +270,11 @@ qla_status qla_step(qla_ctx *c, long long n_steps) {
         return fail(c, QLA_ESTATE, "qla_step: set a medium and a state first");
     DeviceGuard dg(c->device);
     if (!dg.ok) return fail(c, QLA_ECUDA, "qla_step: cannot select device");
+    const bool march = c->step_kernel == QLA_KERNEL_MARCH ||
+                       (c->step_kernel == QLA_KERNEL_AUTO && march_supported(c));
     for (long long k = 0; k < n_steps; ++k) {
-        QLA_CUDA(c, launch_step_tile(c, c->state[c->cur], c->state[c->cur ^ 1]),
+        QLA_CUDA(c, march ? launch_step_march(c, c->state[c->cur], c->state[c->cur ^ 1])
+                          : launch_step_tile(c, c->state[c->cur], c->state[c->cur ^ 1]),
                  "qla_step: kernel");
         c->launches++;
         c->cur ^= 1;
@@ -356,6 +359,18 @@ qla_status qla_set_time_block(qla_ctx *c, int k) {
         return fail(c, QLA_EINVAL, "qla_set_time_block: k = %d outside 0..%d", k,
                     QLA_MAX_TIME_BLOCK);
     c->time_block = k;
+    return QLA_OK;
+}
+
+qla_status qla_set_step_kernel(qla_ctx *c, int kernel) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (kernel < QLA_KERNEL_AUTO || kernel > QLA_KERNEL_MARCH)
+        return fail(c, QLA_EINVAL, "qla_set_step_kernel: unknown kernel %d", kernel);
+    if (kernel == QLA_KERNEL_MARCH && !march_supported(c))
+        return fail(c, QLA_EINVAL, "qla_set_step_kernel: the marching kernel needs nx a multiple "
+                                   "of its lane width, nx >= 32 lane widths and ny >= 8");
+    c->step_kernel = kernel;
     return QLA_OK;
 }
 

@@ -36,13 +36,13 @@ __device__ __forceinline__ void split(double v, float &hi, float &lo) {
 
 __device__ __forceinline__ void store_coef(float4 *cC, float4 *cV, size_t g, double th,
                                            double px, double py) {
-    // gamma = 1 - cos = 2 sin^2(theta/2), computed without cancellation
-    const double sh = sin(0.5 * th);
-    const double gam = 2.0 * sh * sh, s = sin(th);
+    double s, c;
+    sincos(th, &s, &c);
     float4 k;
-    split(gam, k.x, k.z);
+    split(c, k.x, k.z);
     split(s, k.y, k.w);
     cC[g] = k;
+    // gamma = 1 - cos = 2 sin^2(phi/2), computed without cancellation
     const double shx = sin(0.5 * px), shy = sin(0.5 * py);
     cV[g] = make_float4(__double2float_rn(2.0 * shx * shx), __double2float_rn(sin(px)),
                         __double2float_rn(2.0 * shy * shy), __double2float_rn(sin(py)));

@@ -58,32 +58,35 @@ __host__ __device__ constexpr Pair pair_of(bool xdir, int k) {
 //   FP64: CoefC = (cos theta, sin theta); CoefV = (cos phi_x, sin phi_x,
 //         cos phi_y, sin phi_y) with phi = beta/2 (rotation reading) or beta
 //         (printed shear).
-//   FP32: CoefC = (gamma_hi, s_hi, gamma_lo, s_lo), gamma = 1 - cos theta,
-//         s = sin theta, each split into an FP32 value and the FP32 rounding
-//         of the remainder, so the collision angle and norm carry ~48 bits;
-//         CoefV = (gamma_x, s_x, gamma_y, s_y) single words.
+//   FP32: CoefC = (c_hi, s_hi, c_lo, s_lo): cos theta and sin theta each
+//         split into an FP32 value and the FP32 rounding of the remainder,
+//         so the collision angle and norm carry ~48 bits (single FP32 words
+//         would shift the phase speed by ~1e-7 per step and drift the norm);
+//         CoefV = (gamma_x, s_x, gamma_y, s_y), gamma = 1 - cos, single words.
 // ----------------------------------------------------------------------------
 template <typename T> struct Coef;
 template <> struct Coef<double> { using C = double2; using V = double4; };
 template <> struct Coef<float>  { using C = float4;  using V = float4; };
 
 // (a, b) <- [[c, -g s], [g s, c]] (a, b) with g = +-1.
+// Explicit FMAs fix the rounding, so every kernel produces the same bits.
 __device__ __forceinline__ void rotate(double &a, double &b, double2 k, double g) {
     const double s = g * k.y;
-    const double na = k.x * a - s * b;
-    const double nb = s * a + k.x * b;
+    const double na = fma(k.x, a, -(s * b));
+    const double nb = fma(k.x, b, s * a);
     a = na;
     b = nb;
 }
 
-// Same rotation written as a - (gamma a + g s b), b - (gamma b - g s a) with
-// two-word gamma and s; the small terms are accumulated first.
+// Same rotation with two-word c and s: the low-word terms are accumulated
+// first, then the sine term, and the cosine term last, so each output is
+// rounded once at its own magnitude (plus once at the sine term's).
 __device__ __forceinline__ void rotate(float &a, float &b, float4 k, float g) {
     const float sh = g * k.y, sl = g * k.w;
-    const float ta = fmaf(k.x, a, fmaf(sh, b, fmaf(k.z, a, sl * b)));
-    const float tb = fmaf(k.x, b, fmaf(-sh, a, fmaf(k.z, b, -sl * a)));
-    a -= ta;
-    b -= tb;
+    const float na = fmaf(k.x, a, fmaf(-sh, b, fmaf(k.z, a, -sl * b)));
+    const float nb = fmaf(k.x, b, fmaf(sh, a, fmaf(k.z, b, sl * a)));
+    a = na;
+    b = nb;
 }
 
 // Single-word rotation used for V in FP32: (gamma, s) = (1 - cos, sin).
@@ -96,8 +99,8 @@ __device__ __forceinline__ void rotate1(float &a, float &b, float gam, float s, 
 }
 __device__ __forceinline__ void rotate1(double &a, double &b, double c, double s, double g) {
     const double sg = g * s;
-    const double na = c * a - sg * b;
-    const double nb = sg * a + c * b;
+    const double na = fma(c, a, -(sg * b));
+    const double nb = fma(c, b, sg * a);
     a = na;
     b = nb;
 }
@@ -107,7 +110,7 @@ __device__ __forceinline__ void shear1(float x, float &y, float gam, float s, fl
     y -= fmaf(gam, y, -g * s * x);
 }
 __device__ __forceinline__ void shear1(double x, double &y, double c, double s, double g) {
-    y = c * y + g * s * x;
+    y = fma(c, y, g * s * x);
 }
 
 enum VMode { V_ROTATION = 0, V_LITERAL = 1, V_NONE = 2 };
@@ -168,6 +171,7 @@ struct qla_ctx {
     int energy_blocks = 0;
     bool has_medium = false, has_state = false;
     int time_block = 0;
+    int step_kernel = 0;            // qla_step_kernel
     long long launches = 0;
     qla_status sticky = QLA_OK;
     std::string err;
@@ -191,4 +195,6 @@ cudaError_t launch_fields(qla_ctx *c, int comp, double *dst);
 cudaError_t launch_energy(qla_ctx *c);
 cudaError_t launch_probe(qla_ctx *c, int count, const int *ij_dev, double *out_dev);
 cudaError_t launch_step_tile(qla_ctx *c, const void *in, void *out);
+cudaError_t launch_step_march(qla_ctx *c, const void *in, void *out);
+bool march_supported(const qla_ctx *c);
 }  // namespace qla

@@ -23,6 +23,7 @@ QLA_TE_ONLY = 1
 QLA_POTENTIAL_LITERAL = 2
 QLA_POTENTIAL_NONE = 4
 QLA_MAX_TIME_BLOCK = 8
+QLA_KERNEL_AUTO, QLA_KERNEL_TILE, QLA_KERNEL_MARCH = 0, 1, 2
 
 STATUS = {0: "QLA_OK", 1: "QLA_EINVAL", 2: "QLA_ESTATE", 3: "QLA_ENOMEM",
           4: "QLA_ECUDA", 5: "QLA_ETIMEOUT", 6: "QLA_ENONFINITE"}
@@ -65,7 +66,8 @@ def load():
                            ("qla_energy", [c_vp, _DP]),
                            ("qla_fields", [c_vp] + [c_vp] * 6),
                            ("qla_set_time_block", [c_vp, c_int]),
-                           ("qla_probe", [c_vp, c_int, c_vp, c_vp, c_vp])):
+                           ("qla_probe", [c_vp, c_int, c_vp, c_vp, c_vp]),
+                           ("qla_set_step_kernel", [c_vp, c_int])):
             getattr(lib, name).argtypes = args
             getattr(lib, name).restype = c_int
         lib.qla_init_grid.restype = c_int
@@ -171,6 +173,10 @@ def qla_set_time_block(ctx, k):
     _check(ctx, load().qla_set_time_block(ctx, int(k)))
 
 
+def qla_set_step_kernel(ctx, kernel):
+    _check(ctx, load().qla_set_step_kernel(ctx, int(kernel)))
+
+
 def qla_launch_count(ctx):
     return int(load().qla_launch_count(ctx))
 
@@ -258,6 +264,11 @@ class Grid:
     def probe(self, i, j):
         with self._dev():
             return qla_probe(self._ctx, i, j)
+
+    def set_step_kernel(self, kernel):
+        """"auto", "tile" or "march" (see qla_set_step_kernel)."""
+        k = {"auto": QLA_KERNEL_AUTO, "tile": QLA_KERNEL_TILE, "march": QLA_KERNEL_MARCH}
+        qla_set_step_kernel(self._ctx, k.get(kernel, kernel))
 
     def set_time_block(self, k):
         qla_set_time_block(self._ctx, k)

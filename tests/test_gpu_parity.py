@@ -30,9 +30,10 @@ def rel_l2(a, b):
 
 
 def gpu_run(n, delta, steps, q0=None, packet=None, precision="fp64", te=False,
-            potential="rotation", time_block=0):
+            potential="rotation", time_block=0, kernel="auto"):
     ny, nx = n.shape
     with qla.Grid(nx, ny, delta, precision, te_only=te, potential=potential) as g:
+        g.set_step_kernel(kernel)
         if time_block:
             g.set_time_block(time_block)
         g.set_medium(n)
@@ -48,14 +49,20 @@ def gpu_run(n, delta, steps, q0=None, packet=None, precision="fp64", te=False,
 # FP64: 1e-12 relative L2
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("te", [False, True])
-def test_ellipse_256_fp64_400_steps(te):
+@pytest.fixture(scope="module")
+def ellipse_256_oracle():
     w = inputs.ellipse_256()
     n = w.medium()
     pk = w.packet.as_dict()
     q0 = oracle.packet(n, w.delta, **pk)
-    want = oracle.run(q0, n, w.delta, w.steps)
-    got, e = gpu_run(n, w.delta, w.steps, packet=pk, te=te)
+    return w, n, pk, oracle.run(q0, n, w.delta, w.steps)
+
+
+@pytest.mark.parametrize("kernel", ["tile", "march"])
+@pytest.mark.parametrize("te", [False, True])
+def test_ellipse_256_fp64_400_steps(te, kernel, ellipse_256_oracle):
+    w, n, pk, want = ellipse_256_oracle
+    got, e = gpu_run(n, w.delta, w.steps, packet=pk, te=te, kernel=kernel)
     assert rel_l2(got, want) <= 1e-12
     assert abs(e / oracle.energy(want) - 1) <= 1e-12
     assert np.all(got[[0, 1, 5]] == 0)
@@ -71,6 +78,30 @@ def test_random_state_fp64_ragged(shape, potential):
     want = oracle.run(q0, n, 0.7, 7, potential)
     got, _ = gpu_run(n, 0.7, 7, q0=q0, potential=potential)
     assert rel_l2(got, want) <= 1e-12, (shape, potential, rel_l2(got, want))
+
+
+@pytest.mark.parametrize("potential", ["rotation", "literal", "none"])
+@pytest.mark.parametrize("shape", [(64, 8), (66, 9), (128, 37), (250, 64), (96, 130), (320, 11)])
+def test_march_kernel_fp64_against_oracle(shape, potential):
+    nx, ny = shape
+    n = inputs.random_medium(nx, ny, seed=nx * 31 + ny, lo=1.0, hi=3.5)
+    q0 = inputs.random_state(nx, ny, seed=nx + 3 * ny)
+    want = oracle.run(q0, n, 0.8, 9, potential)
+    got, _ = gpu_run(n, 0.8, 9, q0=q0, potential=potential, kernel="march")
+    assert rel_l2(got, want) <= 1e-12, (shape, potential, rel_l2(got, want))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("te", [False, True])
+@pytest.mark.parametrize("shape", [(128, 40), (256, 77), (520, 64)])
+def test_march_and_tile_kernels_agree_bitwise(shape, te, precision):
+    nx, ny = shape
+    n = inputs.random_medium(nx, ny, seed=nx + ny, lo=1.0, hi=3.0)
+    q0 = inputs.random_state(nx, ny, seed=5 * nx + ny, planes=3 if te else 6)
+    a, ea = gpu_run(n, 1.0, 13, q0=q0, precision=precision, te=te, kernel="tile")
+    b, eb = gpu_run(n, 1.0, 13, q0=q0, precision=precision, te=te, kernel="march")
+    assert np.array_equal(a, b)
+    assert ea == eb
 
 
 def test_random_state_fp64_te_matches_six_plane():
