@@ -158,6 +158,45 @@ qla_status qla_set_time_block(qla_ctx *ctx, int k);
 typedef enum { QLA_KERNEL_AUTO = 0, QLA_KERNEL_TILE = 1, QLA_KERNEL_MARCH = 2 } qla_step_kernel;
 qla_status qla_set_step_kernel(qla_ctx *ctx, int kernel);
 
+/* Energy of caller-owned device planes, allocating nothing.
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory: a process whose device memory is all held
+ * by another allocator (a framework's caching pool, a pre-planned serving
+ * budget), or a loop that must not enter the CUDA allocator.  It computes
+ * the same quantity as qla_energy -- the FP64 sum over sites and planes of
+ * q^2 (Eq. A13 without the cell area) -- for planes the caller owns, with no
+ * context and no workspace.
+ *
+ * planes: device pointer; n_planes (1..6) planes of FP64 (precision
+ * QLA_FP64) or FP32 (QLA_FP32) values, element (p, j, i) at
+ * planes[p * plane_stride + j * row_pitch + i] (strides in elements;
+ * row_pitch >= nx, plane_stride >= row_pitch * ny).  out_dev: device pointer
+ * to one double that receives the sum.  The work is enqueued on cuda_stream
+ * (NULL = legacy default stream) on the current device and the call returns
+ * without waiting.
+ *
+ * The reduction's partial sums live in one fixed device array inside the
+ * library, QLA_NOALLOC_MAX_PARTIALS doubles (128 KiB), which every GPU that
+ * loads the library holds until the process exits.  One partial covers
+ * QLA_NOALLOC_SITES_PER_PARTIAL sites, so lattices of more than
+ * QLA_NOALLOC_MAX_PARTIALS * QLA_NOALLOC_SITES_PER_PARTIAL = 2^28 sites
+ * (16384 x 16384) are rejected with QLA_EINVAL before anything runs.  Every
+ * call overwrites the partials it reads, so nothing carries over from the
+ * previous call; but all calls share that array, so calls whose work
+ * overlaps on the GPU (concurrent streams, or several host threads) race and
+ * must be ordered by the caller.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  The result is bitwise reproducible for a given size
+ * and agrees with qla_energy to rounding order.
+ * Errors: QLA_EINVAL for a null pointer or a bad size/precision/stride,
+ * QLA_ECUDA if the lookup or a launch fails. */
+#define QLA_NOALLOC_MAX_PARTIALS 16384
+#define QLA_NOALLOC_SITES_PER_PARTIAL 16384
+qla_status qla_energy_noalloc(const void *planes, int precision, int n_planes, int nx,
+                              int ny, long long row_pitch, long long plane_stride,
+                              void *cuda_stream, double *out_dev);
+
 /* Kernel launches enqueued by this context since creation (diagnostics). */
 long long qla_launch_count(const qla_ctx *ctx);
 
