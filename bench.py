@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--workload", default="ellipse_8192")
     ap.add_argument("--qla-steps", type=int, default=100)
     ap.add_argument("--time-block", type=int, default=0)
+    ap.add_argument("--lane-cols", type=int, default=0, help="marching kernel tuning")
+    ap.add_argument("--rows", type=int, default=0, help="marching kernel tuning")
     ap.add_argument("--six-planes", action="store_true",
                     help="evolve all six amplitudes instead of the E_z triple")
     ap.add_argument("--no-e2e", action="store_true")
@@ -96,6 +98,12 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
             out, _ = self.proc.communicate()
+        return self.parse(out)
+
+    @staticmethod
+    def parse(out):
+        """Median SM clock, max clock and the throttle reasons seen in the
+        CSV lines of the nvidia-smi query in FIELDS."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.splitlines():
@@ -139,11 +147,13 @@ def barrier(world):
 
 
 def max_over_ranks(world, value):
+    """Largest value over the ranks (the run's time is its slowest rank's)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -251,6 +261,7 @@ def gpu_arm(args):
     g = qla.Grid(w.nx, w.ny, w.delta, args.precision, te_only=te, stream=stream)
     if args.time_block:
         g.set_time_block(args.time_block)
+    g.set_march_tuning(args.lane_cols, args.rows)
     g.set_medium(n_host)
     g.set_packet(**pk)
     e0 = g.energy()
@@ -326,6 +337,7 @@ def gpu_arm(args):
                        "nx": w.nx, "ny": w.ny, "delta": w.delta,
                        "qla_steps_per_bench_step": S, "planes": P,
                        "potential": "rotation", "time_block": k_used,
+                       "lane_cols": args.lane_cols or "auto", "rows": args.rows or "auto",
                        "energy_drift": drift,
                        "l2": "state %.0f MB > 129 MB L2, no flush" % (2 * P * elt * sites / 2e6)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -356,6 +368,7 @@ def e2e_run(args, w, te, n_host, pk, world, dev):
     g = qla.Grid(w.nx, w.ny, w.delta, args.precision, te_only=te, stream=stream)
     if args.time_block:
         g.set_time_block(args.time_block)
+    g.set_march_tuning(args.lane_cols, args.rows)
     S = args.qla_steps
     barrier(world)
     torch.cuda.synchronize(dev)

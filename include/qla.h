@@ -149,8 +149,8 @@ qla_status qla_probe(qla_ctx *ctx, int count, const int *i, const int *j, double
 qla_status qla_set_time_block(qla_ctx *ctx, int k);
 
 /* Step kernel.  QLA_KERNEL_AUTO picks the register-resident marching
- * kernel when nx is a multiple of its per-lane column count (4 for FP32
- * E_z contexts, 2 otherwise), nx >= 32 times that count and ny >= 8, and the
+ * kernel when nx is a multiple of its per-lane column count (2 by default;
+ * see qla_set_march_tuning), nx >= 32 times that count and ny >= 8, and the
  * shared-memory tile kernel otherwise.  QLA_KERNEL_TILE / QLA_KERNEL_MARCH
  * force one (QLA_EINVAL if the marching kernel does not support the
  * lattice).  Both compute the same operator sequence; FP64 results agree to
@@ -196,6 +196,13 @@ qla_status qla_set_step_kernel(qla_ctx *ctx, int kernel);
 qla_status qla_energy_noalloc(const void *planes, int precision, int n_planes, int nx,
                               int ny, long long row_pitch, long long plane_stride,
                               void *cuda_stream, double *out_dev);
+
+/* Tuning of the marching kernel: lane_cols = columns per lane (0 = library
+ * choice; 2 or 4 for FP32 E_z contexts, other contexts always use 2), rows =
+ * rows per work item (0 = chosen from the occupancy so one wave of items
+ * fills the GPU; else rounded up to a multiple of 4).  Results do not
+ * depend on either.  QLA_EINVAL for other values. */
+qla_status qla_set_march_tuning(qla_ctx *ctx, int lane_cols, int rows);
 
 /* Kernel launches enqueued by this context since creation (diagnostics). */
 long long qla_launch_count(const qla_ctx *ctx);

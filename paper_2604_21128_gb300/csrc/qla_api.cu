@@ -21,8 +21,7 @@ Layout layout_for(int nx, int ny, int prec, unsigned flags) {
     L.pitch = (nx + 31) / 32 * 32;
     L.plane_elems = size_t(ny) * L.pitch;
     const size_t plane_bytes = align256(L.plane_elems * elt);
-    const size_t cC = prec == QLA_FP64 ? sizeof(double2) : sizeof(float4);
-    const size_t cV = prec == QLA_FP64 ? sizeof(double4) : sizeof(float4);
+    const size_t rec = prec == QLA_FP64 ? sizeof(MedRec<double>) : sizeof(MedRec<float>);
     // energy partials: one per block of 256 threads x 8 sites, capped
     const size_t sites = size_t(nx) * ny;
     size_t nb = (sites + 2047) / 2048;
@@ -32,8 +31,10 @@ Layout layout_for(int nx, int ny, int prec, unsigned flags) {
     size_t off = 0;
     L.state[0] = off; off += align256(plane_bytes * P);
     L.state[1] = off; off += align256(plane_bytes * P);
-    L.coefC = off;    off += align256(L.plane_elems * cC);
-    L.coefV = off;    off += align256(L.plane_elems * cV);
+    L.midx = off;     off += align256(L.plane_elems * 4);
+    L.table = off;    off += align256((UNIFORM_SLOTS + sites) * rec);
+    L.keys = off;     off += align256(UNIFORM_SLOTS * 8);
+    L.counter = off;  off += align256(4);
     L.n = off;        off += align256(L.plane_elems * 8);
     L.staging = off;  off += align256(sites * 8);
     L.partials = off; off += align256(nb * 8);
@@ -147,15 +148,17 @@ qla_status qla_init_grid(qla_ctx **out, int nx, int ny, double delta, int precis
     c->plane_elems = L.plane_elems;
     c->state[0] = c->ws + L.state[0];
     c->state[1] = c->ws + L.state[1];
-    c->coefC = c->ws + L.coefC;
-    c->coefV = c->ws + L.coefV;
+    c->midx = reinterpret_cast<uint32_t *>(c->ws + L.midx);
+    c->table = c->ws + L.table;
+    c->keys = reinterpret_cast<unsigned long long *>(c->ws + L.keys);
+    c->counter = reinterpret_cast<unsigned *>(c->ws + L.counter);
     c->n = reinterpret_cast<double *>(c->ws + L.n);
     c->staging = reinterpret_cast<double *>(c->ws + L.staging);
     c->partials = reinterpret_cast<double *>(c->ws + L.partials);
     c->result = reinterpret_cast<double *>(c->ws + L.result);
     c->energy_blocks = L.energy_blocks;
     // both state buffers start at zero (pad columns included)
-    if (cudaMemsetAsync(c->ws + L.state[0], 0, L.coefC - L.state[0], c->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(c->ws + L.state[0], 0, L.midx - L.state[0], c->stream) != cudaSuccess) {
         cudaGetLastError();
         if (c->owns_ws) cudaFree(c->ws);
         delete c;
@@ -179,6 +182,8 @@ qla_status qla_set_medium(qla_ctx *c, const double *n_host) {
     if (!dg.ok) return fail(c, QLA_ECUDA, "qla_set_medium: cannot select device");
     QLA_CUDA(c, cudaMemcpyAsync(c->staging, n_host, N * 8, cudaMemcpyHostToDevice, c->stream),
              "qla_set_medium: copy");
+    QLA_CUDA(c, cudaMemsetAsync(c->keys, 0, UNIFORM_SLOTS * 8, c->stream), "qla_set_medium: clear");
+    QLA_CUDA(c, cudaMemsetAsync(c->counter, 0, 4, c->stream), "qla_set_medium: clear");
     QLA_CUDA(c, launch_medium(c), "qla_set_medium: kernel");
     c->has_medium = true;
     return QLA_OK;
@@ -203,6 +208,7 @@ qla_status qla_set_packet(qla_ctx *c, const qla_packet *p) {
                  "qla_set_packet: clear");
     QLA_CUDA(c, launch_packet(c, *p), "qla_set_packet: kernel");
     c->has_state = true;
+    c->pending_v = false;
     return QLA_OK;
 }
 
@@ -236,6 +242,7 @@ qla_status qla_set_state(qla_ctx *c, const double *q_host) {
     // may change and before the next copy overwrites staging
     QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_set_state: sync");
     c->has_state = true;
+    c->pending_v = false;
     return QLA_OK;
 }
 
@@ -252,7 +259,7 @@ qla_status qla_get_state(qla_ctx *c, double *q_host) {
             std::memset(q_host + size_t(comp) * N, 0, N * 8);
             continue;
         }
-        QLA_CUDA(c, launch_to_f64(c, plane, c->staging), "qla_get_state: convert");
+        QLA_CUDA(c, launch_to_f64(c, comp, c->staging), "qla_get_state: convert");
         QLA_CUDA(c, cudaMemcpyAsync(q_host + size_t(comp) * N, c->staging, N * 8,
                                     cudaMemcpyDeviceToHost, c->stream),
                  "qla_get_state: copy");
@@ -273,11 +280,13 @@ qla_status qla_step(qla_ctx *c, long long n_steps) {
     const bool march = c->step_kernel == QLA_KERNEL_MARCH ||
                        (c->step_kernel == QLA_KERNEL_AUTO && march_supported(c));
     for (long long k = 0; k < n_steps; ++k) {
-        QLA_CUDA(c, march ? launch_step_march(c, c->state[c->cur], c->state[c->cur ^ 1])
-                          : launch_step_tile(c, c->state[c->cur], c->state[c->cur ^ 1]),
+        const bool vin = c->pending_v;
+        QLA_CUDA(c, march ? launch_step_march(c, c->state[c->cur], c->state[c->cur ^ 1], vin)
+                          : launch_step_tile(c, c->state[c->cur], c->state[c->cur ^ 1], vin),
                  "qla_step: kernel");
         c->launches++;
         c->cur ^= 1;
+        c->pending_v = c->vmode != V_NONE;
     }
     return QLA_OK;
 }
@@ -371,6 +380,18 @@ qla_status qla_set_step_kernel(qla_ctx *c, int kernel) {
         return fail(c, QLA_EINVAL, "qla_set_step_kernel: the marching kernel needs nx a multiple "
                                    "of its lane width, nx >= 32 lane widths and ny >= 8");
     c->step_kernel = kernel;
+    return QLA_OK;
+}
+
+qla_status qla_set_march_tuning(qla_ctx *c, int lane_cols, int rows) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (lane_cols != 0 && lane_cols != 2 && lane_cols != 4)
+        return fail(c, QLA_EINVAL, "qla_set_march_tuning: lane_cols %d not 0, 2 or 4", lane_cols);
+    if (rows < 0 || rows > (1 << 20))
+        return fail(c, QLA_EINVAL, "qla_set_march_tuning: rows %d", rows);
+    c->march_lx = lane_cols;
+    c->march_seg = rows;
     return QLA_OK;
 }
 

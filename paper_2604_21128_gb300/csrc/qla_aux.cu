@@ -1,6 +1,8 @@
 // Per-run kernels around the step: medium coefficients (Eqs. 2e4, 2e13),
 // the initial packet (Sec. V-B), the energy reduction (Eq. A13), the inverse
 // Dyson map to fields (Eq. 3b3) and FP64 <-> storage conversions.
+#include <cooperative_groups.h>
+
 #include "qla_internal.h"
 
 namespace qla {
@@ -18,15 +20,14 @@ inline int grid_for(size_t n, int threads = AUX_THREADS) {
 // centred periodic difference (Eq. 2e13); V angle = beta/2 (rotation
 // reading) or beta (printed shear).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void store_coef(double2 *cC, double4 *cV, size_t g, double th,
-                                           double px, double py) {
+__device__ __forceinline__ void make_rec(MedRec<double> &r, double th, double px, double py) {
     double s, c;
     sincos(th, &s, &c);
-    cC[g] = make_double2(c, s);
+    r.c = make_double2(c, s);
     double sx, cx, sy, cy;
     sincos(px, &sx, &cx);
     sincos(py, &sy, &cy);
-    cV[g] = make_double4(cx, sx, cy, sy);
+    r.v = make_double4(cx, sx, cy, sy);
 }
 
 __device__ __forceinline__ void split(double v, float &hi, float &lo) {
@@ -34,37 +35,87 @@ __device__ __forceinline__ void split(double v, float &hi, float &lo) {
     lo = __double2float_rn(v - double(hi));
 }
 
-__device__ __forceinline__ void store_coef(float4 *cC, float4 *cV, size_t g, double th,
-                                           double px, double py) {
+__device__ __forceinline__ void make_rec(MedRec<float> &r, double th, double px, double py) {
     double s, c;
     sincos(th, &s, &c);
-    float4 k;
-    split(c, k.x, k.z);
-    split(s, k.y, k.w);
-    cC[g] = k;
+    split(c, r.c.x, r.c.z);
+    split(s, r.c.y, r.c.w);
     // gamma = 1 - cos = 2 sin^2(phi/2), computed without cancellation
     const double shx = sin(0.5 * px), shy = sin(0.5 * py);
-    cV[g] = make_float4(__double2float_rn(2.0 * shx * shx), __double2float_rn(sin(px)),
-                        __double2float_rn(2.0 * shy * shy), __double2float_rn(sin(py)));
+    r.v = make_float4(__double2float_rn(2.0 * shx * shx), __double2float_rn(sin(px)),
+                      __double2float_rn(2.0 * shy * shy), __double2float_rn(sin(py)));
 }
 
+__device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+// One pass over the sites: classify, hand out a record index, write each
+// record once.  A site whose four neighbours carry exactly its n has beta = 0
+// and a record that depends on n alone; those share one record per distinct
+// n through an open-addressing table of UNIFORM_SLOTS keys (n's bits; n > 0
+// so a key is never 0, the empty mark).  The site that claims a key writes
+// its record.  All other sites get consecutive fresh indices after the
+// shared slots (one atomic per group of lanes) and write their own record.
+// Index values depend on scheduling; record contents do not, so results are
+// reproducible bit for bit.
 template <typename T>
 __global__ void k_medium(const double *__restrict__ n, int nx, int ny, int pitch, double delta,
-                         double vscale, typename Coef<T>::C *cC, typename Coef<T>::V *cV) {
+                         double vscale, unsigned long long *__restrict__ keys,
+                         unsigned *__restrict__ counter, uint32_t *__restrict__ midx,
+                         MedRec<T> *__restrict__ table) {
+    namespace cg = cooperative_groups;
     const size_t N = size_t(nx) * ny;
     for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < N;
          t += size_t(gridDim.x) * blockDim.x) {
         const int j = int(t / nx), i = int(t - size_t(j) * nx);
         const size_t g = size_t(j) * pitch + i;
         const double nn = n[g];
-        const double th = delta / (4.0 * nn);
         const double nxp = n[size_t(j) * pitch + wrap(i + 1, nx)];
         const double nxm = n[size_t(j) * pitch + wrap(i - 1, nx)];
         const double nyp = n[size_t(wrap(j + 1, ny)) * pitch + i];
         const double nym = n[size_t(wrap(j - 1, ny)) * pitch + i];
-        const double bx = (nxp - nxm) / (2.0 * delta) / (nn * nn) * delta * delta;
-        const double by = (nyp - nym) / (2.0 * delta) / (nn * nn) * delta * delta;
-        store_coef(cC, cV, g, th, vscale * bx, vscale * by);
+        bool shared = nxp == nn && nxm == nn && nyp == nn && nym == nn;
+        bool owner = false;
+        uint32_t id = 0;
+        if (shared) {
+            const unsigned long long key = static_cast<unsigned long long>(__double_as_longlong(nn));
+            unsigned h = unsigned(mix64(key)) & (UNIFORM_SLOTS - 1);
+            bool placed = false;
+            for (int probe = 0; probe < UNIFORM_SLOTS; ++probe) {
+                const unsigned long long prev = atomicCAS(&keys[h], 0ull, key);
+                if (prev == 0ull || prev == key) {
+                    owner = prev == 0ull;
+                    id = h;
+                    placed = true;
+                    break;
+                }
+                h = (h + 1) & (UNIFORM_SLOTS - 1);
+            }
+            shared = placed;  // a full table: fall back to an own record
+        }
+        if (!shared) {
+            cg::coalesced_group grp = cg::coalesced_threads();
+            unsigned base = 0;
+            if (grp.thread_rank() == 0) base = atomicAdd(counter, grp.size());
+            base = grp.shfl(base, 0);
+            id = UNIFORM_SLOTS + base + grp.thread_rank();
+            owner = true;
+        }
+        if (owner) {
+            const double th = delta / (4.0 * nn);
+            const double bx = (nxp - nxm) / (2.0 * delta) / (nn * nn) * delta * delta;
+            const double by = (nyp - nym) / (2.0 * delta) / (nn * nn) * delta * delta;
+            MedRec<T> r;
+            make_rec(r, th, vscale * bx, vscale * by);
+            table[id] = r;
+        }
+        midx[g] = id;
     }
 }
 
@@ -130,16 +181,21 @@ __global__ void k_from_f64(const double *__restrict__ src, T *__restrict__ dst, 
     }
 }
 
-// dst[t] = src / n (E components) or src (B components); src == null -> 0.
-template <typename T>
-__global__ void k_to_f64(const T *__restrict__ src, const double *__restrict__ n,
-                         double *__restrict__ dst, int nx, int ny, int pitch) {
+// dst[t] = q_comp / n (with n) or q_comp, where q is the state at the site
+// (pending potential operator applied; absent planes read as zero).
+template <typename T, int P, int VM>
+__global__ void k_to_f64(const T *__restrict__ q, size_t plane_elems, int comp,
+                         const double *__restrict__ n, double *__restrict__ dst, int nx, int ny,
+                         int pitch, bool vin, const uint32_t *__restrict__ midx,
+                         const MedRec<T> *__restrict__ table) {
     const size_t N = size_t(nx) * ny;
     for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < N;
          t += size_t(gridDim.x) * blockDim.x) {
         const int j = int(t / nx), i = int(t - size_t(j) * nx);
         const size_t g = size_t(j) * pitch + i;
-        double v = src ? double(src[g]) : 0.0;
+        T s[6];
+        load_site<T, P, VM>(q, plane_elems, g, vin, midx, table, s);
+        double v = double(s[comp]);
         if (n) v /= n[g];
         dst[t] = v;
     }
@@ -165,19 +221,23 @@ __device__ __forceinline__ double block_sum(double v) {
     return v;  // valid in thread 0
 }
 
-template <typename T, int P>
+template <typename T, int P, int VM>
 __global__ void __launch_bounds__(AUX_THREADS)
 k_energy_partial(const T *__restrict__ q, int nx, int ny, int pitch, size_t plane_elems,
-                 double *__restrict__ partials) {
+                 double *__restrict__ partials, bool vin, const uint32_t *__restrict__ midx,
+                 const MedRec<T> *__restrict__ table) {
     const size_t N = size_t(nx) * ny;
     double acc = 0.0;
     for (size_t t = blockIdx.x * size_t(AUX_THREADS) + threadIdx.x; t < N;
          t += size_t(gridDim.x) * AUX_THREADS) {
         const int j = int(t / nx), i = int(t - size_t(j) * nx);
         const size_t g = size_t(j) * pitch + i;
+        T s[6];
+        load_site<T, P, VM>(q, plane_elems, g, vin, midx, table, s);
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const double v = double(q[p * plane_elems + g]);
+        for (int c = 0; c < 6; ++c) {
+            if (plane_of<P>(c) < 0) continue;
+            const double v = double(s[c]);
             acc = fma(v, v, acc);
         }
     }
@@ -194,42 +254,20 @@ k_energy_final(const double *__restrict__ partials, int count, double *__restric
 }
 
 // Gather q at listed sites: ij holds i[0..count) then j[0..count).
-template <typename T, int P>
+template <typename T, int P, int VM>
 __global__ void k_probe(const T *__restrict__ q, const int *__restrict__ ij, int count,
-                        int pitch, size_t plane_elems, double *__restrict__ out) {
+                        int pitch, size_t plane_elems, double *__restrict__ out, bool vin,
+                        const uint32_t *__restrict__ midx, const MedRec<T> *__restrict__ table) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= count) return;
     const size_t g = size_t(ij[count + k]) * pitch + ij[k];
+    T s[6];
+    load_site<T, P, VM>(q, plane_elems, g, vin, midx, table, s);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        const int p = plane_of<P>(c);
-        out[6 * k + c] = p >= 0 ? double(q[p * plane_elems + g]) : 0.0;
-    }
+    for (int c = 0; c < 6; ++c) out[6 * k + c] = double(s[c]);
 }
 
 }  // namespace
-
-cudaError_t launch_probe(qla_ctx *c, int count, const int *ij_dev, double *out_dev) {
-    const int nb = (count + AUX_THREADS - 1) / AUX_THREADS;
-    const void *q = c->state[c->cur];
-    if (c->prec == QLA_FP64) {
-        if (c->P == 6)
-            k_probe<double, 6><<<nb, AUX_THREADS, 0, c->stream>>>(
-                static_cast<const double *>(q), ij_dev, count, c->pitch, c->plane_elems, out_dev);
-        else
-            k_probe<double, 3><<<nb, AUX_THREADS, 0, c->stream>>>(
-                static_cast<const double *>(q), ij_dev, count, c->pitch, c->plane_elems, out_dev);
-    } else {
-        if (c->P == 6)
-            k_probe<float, 6><<<nb, AUX_THREADS, 0, c->stream>>>(
-                static_cast<const float *>(q), ij_dev, count, c->pitch, c->plane_elems, out_dev);
-        else
-            k_probe<float, 3><<<nb, AUX_THREADS, 0, c->stream>>>(
-                static_cast<const float *>(q), ij_dev, count, c->pitch, c->plane_elems, out_dev);
-    }
-    c->launches++;
-    return cudaGetLastError();
-}
 
 cudaError_t launch_medium(qla_ctx *c) {
     const size_t N = size_t(c->nx) * c->ny;
@@ -242,12 +280,12 @@ cudaError_t launch_medium(qla_ctx *c) {
     const double vscale = c->vmode == V_ROTATION ? 0.5 : 1.0;
     if (c->prec == QLA_FP64)
         k_medium<double><<<grid_for(N), AUX_THREADS, 0, c->stream>>>(
-            c->n, c->nx, c->ny, c->pitch, c->delta, vscale,
-            static_cast<double2 *>(c->coefC), static_cast<double4 *>(c->coefV));
+            c->n, c->nx, c->ny, c->pitch, c->delta, vscale, c->keys, c->counter, c->midx,
+            static_cast<MedRec<double> *>(c->table));
     else
         k_medium<float><<<grid_for(N), AUX_THREADS, 0, c->stream>>>(
-            c->n, c->nx, c->ny, c->pitch, c->delta, vscale, static_cast<float4 *>(c->coefC),
-            static_cast<float4 *>(c->coefV));
+            c->n, c->nx, c->ny, c->pitch, c->delta, vscale, c->keys, c->counter, c->midx,
+            static_cast<MedRec<float> *>(c->table));
     c->launches++;
     return cudaGetLastError();
 }
@@ -293,60 +331,63 @@ cudaError_t launch_from_f64(qla_ctx *c, int plane, const double *src) {
     return cudaGetLastError();
 }
 
-static cudaError_t to_f64(qla_ctx *c, int plane, const double *n, double *dst) {
+// Read-out launchers: one instantiation per (precision, planes, V reading).
+template <typename T, int P, int VM>
+static cudaError_t readout_t(qla_ctx *c, int what, int comp, const double *n, double *dst,
+                             int count, const int *ij) {
     const size_t N = size_t(c->nx) * c->ny;
-    if (c->prec == QLA_FP64) {
-        const double *src =
-            plane >= 0 ? static_cast<const double *>(c->state[c->cur]) + plane * c->plane_elems
-                       : nullptr;
-        k_to_f64<double><<<grid_for(N), AUX_THREADS, 0, c->stream>>>(src, n, dst, c->nx, c->ny,
-                                                                      c->pitch);
+    const T *q = static_cast<const T *>(c->state[c->cur]);
+    const MedRec<T> *table = static_cast<const MedRec<T> *>(c->table);
+    const bool vin = c->pending_v;
+    if (what == 0) {
+        k_to_f64<T, P, VM><<<grid_for(N), AUX_THREADS, 0, c->stream>>>(
+            q, c->plane_elems, comp, n, dst, c->nx, c->ny, c->pitch, vin, c->midx, table);
+    } else if (what == 1) {
+        k_energy_partial<T, P, VM><<<c->energy_blocks, AUX_THREADS, 0, c->stream>>>(
+            q, c->nx, c->ny, c->pitch, c->plane_elems, c->partials, vin, c->midx, table);
     } else {
-        const float *src =
-            plane >= 0 ? static_cast<const float *>(c->state[c->cur]) + plane * c->plane_elems
-                       : nullptr;
-        k_to_f64<float><<<grid_for(N), AUX_THREADS, 0, c->stream>>>(src, n, dst, c->nx, c->ny,
-                                                                     c->pitch);
+        k_probe<T, P, VM><<<(count + AUX_THREADS - 1) / AUX_THREADS, AUX_THREADS, 0, c->stream>>>(
+            q, ij, count, c->pitch, c->plane_elems, dst, vin, c->midx, table);
     }
     c->launches++;
     return cudaGetLastError();
 }
 
-cudaError_t launch_to_f64(qla_ctx *c, int plane, double *dst) {
-    return to_f64(c, plane, nullptr, dst);
+template <typename T, int P>
+static cudaError_t readout_p(qla_ctx *c, int what, int comp, const double *n, double *dst,
+                             int count, const int *ij) {
+    switch (c->vmode) {
+    case V_ROTATION: return readout_t<T, P, V_ROTATION>(c, what, comp, n, dst, count, ij);
+    case V_LITERAL:  return readout_t<T, P, V_LITERAL>(c, what, comp, n, dst, count, ij);
+    default:         return readout_t<T, P, V_NONE>(c, what, comp, n, dst, count, ij);
+    }
+}
+
+static cudaError_t readout(qla_ctx *c, int what, int comp, const double *n, double *dst,
+                           int count = 0, const int *ij = nullptr) {
+    if (c->prec == QLA_FP64)
+        return c->P == 6 ? readout_p<double, 6>(c, what, comp, n, dst, count, ij)
+                         : readout_p<double, 3>(c, what, comp, n, dst, count, ij);
+    return c->P == 6 ? readout_p<float, 6>(c, what, comp, n, dst, count, ij)
+                     : readout_p<float, 3>(c, what, comp, n, dst, count, ij);
+}
+
+cudaError_t launch_to_f64(qla_ctx *c, int comp, double *dst) {
+    return readout(c, 0, comp, nullptr, dst);
 }
 
 cudaError_t launch_fields(qla_ctx *c, int comp, double *dst) {
-    const int plane = c->P == 6 ? comp : plane_of<3>(comp);
-    return to_f64(c, plane, comp < 3 ? c->n : nullptr, dst);
+    return readout(c, 0, comp, comp < 3 ? c->n : nullptr, dst);
+}
+
+cudaError_t launch_probe(qla_ctx *c, int count, const int *ij_dev, double *out_dev) {
+    return readout(c, 2, 0, nullptr, out_dev, count, ij_dev);
 }
 
 cudaError_t launch_energy(qla_ctx *c) {
-    const void *q = c->state[c->cur];
-    const int nb = c->energy_blocks;
-    if (c->prec == QLA_FP64) {
-        if (c->P == 6)
-            k_energy_partial<double, 6><<<nb, AUX_THREADS, 0, c->stream>>>(
-                static_cast<const double *>(q), c->nx, c->ny, c->pitch, c->plane_elems,
-                c->partials);
-        else
-            k_energy_partial<double, 3><<<nb, AUX_THREADS, 0, c->stream>>>(
-                static_cast<const double *>(q), c->nx, c->ny, c->pitch, c->plane_elems,
-                c->partials);
-    } else {
-        if (c->P == 6)
-            k_energy_partial<float, 6><<<nb, AUX_THREADS, 0, c->stream>>>(
-                static_cast<const float *>(q), c->nx, c->ny, c->pitch, c->plane_elems,
-                c->partials);
-        else
-            k_energy_partial<float, 3><<<nb, AUX_THREADS, 0, c->stream>>>(
-                static_cast<const float *>(q), c->nx, c->ny, c->pitch, c->plane_elems,
-                c->partials);
-    }
-    c->launches++;
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = readout(c, 1, 0, nullptr, nullptr);
     if (e != cudaSuccess) return e;
-    k_energy_final<<<1, AUX_THREADS, 0, c->stream>>>(c->partials, nb, c->result);
+    k_energy_final<<<1, AUX_THREADS, 0, c->stream>>>(c->partials, c->energy_blocks, c->result);
     c->launches++;
     return cudaGetLastError();
 }

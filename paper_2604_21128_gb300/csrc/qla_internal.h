@@ -68,6 +68,18 @@ template <typename T> struct Coef;
 template <> struct Coef<double> { using C = double2; using V = double4; };
 template <> struct Coef<float>  { using C = float4;  using V = float4; };
 
+// Per-site medium record: collision and potential coefficients together.
+// Sites whose four neighbours have the same n as the site itself (the bulk
+// of any piecewise-uniform medium) share one record per distinct n; every
+// other site (the boundary layers) has its own.  A 32-bit index per site
+// selects the record, so a step reads 4 bytes of medium per site instead of
+// the 32 (FP32) or 48 (FP64) bytes of a full record.
+template <typename T> struct MedRec {
+    typename Coef<T>::C c;
+    typename Coef<T>::V v;
+};
+constexpr int UNIFORM_SLOTS = 4096;  // open-addressing slots for shared records
+
 // (a, b) <- [[c, -g s], [g s, c]] (a, b) with g = +-1.
 // Explicit FMAs fix the rounding, so every kernel produces the same bits.
 __device__ __forceinline__ void rotate(double &a, double &b, double2 k, double g) {
@@ -136,6 +148,22 @@ __device__ __forceinline__ void apply_potential(T (&q)[6], KV kv) {
     }
 }
 
+// The six amplitudes of the state at site g (storage offset), with the
+// pending potential operator applied when vin (entries absent in E_z mode
+// are zero).
+template <typename T, int P, int VM>
+__device__ __forceinline__ void load_site(const T *q, size_t plane, size_t g, bool vin,
+                                          const uint32_t *midx, const MedRec<T> *table,
+                                          T (&s)[6]) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const int p = plane_of<P>(c);
+        s[c] = p >= 0 ? q[p * plane + g] : T(0);
+    }
+    if constexpr (VM != V_NONE)
+        if (vin) apply_potential<T, P, VM>(s, table[midx[g]].v);
+}
+
 __host__ __device__ inline int wrap(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;
@@ -162,14 +190,22 @@ struct qla_ctx {
     void *state[2] = {nullptr, nullptr};
     int cur = 0;
     size_t plane_elems = 0;         // ny * pitch
-    void *coefC = nullptr;
-    void *coefV = nullptr;
+    uint32_t *midx = nullptr;       // record index per site (ny * pitch)
+    void *table = nullptr;          // MedRec<T>[UNIFORM_SLOTS + nx*ny]
+    unsigned long long *keys = nullptr;  // UNIFORM_SLOTS hash keys (n bits)
+    unsigned *counter = nullptr;    // records handed to non-uniform sites
+    int march_lx = 0, march_seg = 0;  // tuning (0 = automatic)
     double *n = nullptr;            // ny * pitch
     double *staging = nullptr;      // ny * nx
     double *partials = nullptr;     // energy partial sums
     double *result = nullptr;       // final energy (device)
     int energy_blocks = 0;
     bool has_medium = false, has_state = false;
+    // True once a step has run since the state was last set: the buffer then
+    // holds U_y U_x Q of the last step and the state Q itself is V applied to
+    // it (the step kernels apply that V to their input; read-outs apply it
+    // on the fly with the same device code).
+    bool pending_v = false;
     int time_block = 0;
     int step_kernel = 0;            // qla_step_kernel
     long long launches = 0;
@@ -180,7 +216,7 @@ struct qla_ctx {
 namespace qla {
 // Workspace layout: offsets of each region (bytes, 256-aligned).
 struct Layout {
-    size_t state[2], coefC, coefV, n, staging, partials, result, total;
+    size_t state[2], midx, table, keys, counter, n, staging, partials, result, total;
     size_t plane_elems;
     int pitch, energy_blocks;
 };
@@ -190,11 +226,12 @@ Layout layout_for(int nx, int ny, int prec, unsigned flags);
 cudaError_t launch_medium(qla_ctx *c);
 cudaError_t launch_packet(qla_ctx *c, const qla_packet &p);
 cudaError_t launch_from_f64(qla_ctx *c, int plane, const double *src);
-cudaError_t launch_to_f64(qla_ctx *c, int plane, double *dst);
+cudaError_t launch_to_f64(qla_ctx *c, int comp, double *dst);
 cudaError_t launch_fields(qla_ctx *c, int comp, double *dst);
 cudaError_t launch_energy(qla_ctx *c);
 cudaError_t launch_probe(qla_ctx *c, int count, const int *ij_dev, double *out_dev);
-cudaError_t launch_step_tile(qla_ctx *c, const void *in, void *out);
-cudaError_t launch_step_march(qla_ctx *c, const void *in, void *out);
+cudaError_t launch_step_tile(qla_ctx *c, const void *in, void *out, bool vin);
+cudaError_t launch_step_march(qla_ctx *c, const void *in, void *out, bool vin);
 bool march_supported(const qla_ctx *c);
+int march_lane_cols(const qla_ctx *c);
 }  // namespace qla

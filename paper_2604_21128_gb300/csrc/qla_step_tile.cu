@@ -8,7 +8,8 @@
 // every staged row, U_y to the tile's columns, as eight layers of disjoint
 // 2x2 rotations each (see layer_of in qla_internal.h); bonds that would
 // leave the staged region are skipped, which only corrupts halo cells that
-// no output depends on.  V_x, V_y and the store happen in registers.
+// no output depends on.  The previous step's V_x, V_y (when pending) are
+// applied to every staged site on load; the buffer written holds U_y U_x Q.
 #include "qla_internal.h"
 
 namespace qla {
@@ -86,11 +87,10 @@ __device__ __forceinline__ void apply_U(T *s, const typename Coef<T>::C *sc) {
     layer_pass<T, P, XDIR, 7, RX, RY, TX>(s, sc); __syncthreads();
 }
 
-template <typename T, int P, int VM>
+template <typename T, int P, int VM, bool VIN>
 __global__ void __launch_bounds__(THREADS)
 k_step_tile(const T *__restrict__ in, T *__restrict__ out,
-            const typename Coef<T>::C *__restrict__ coefC,
-            const typename Coef<T>::V *__restrict__ coefV,
+            const uint32_t *__restrict__ midx, const MedRec<T> *__restrict__ table,
             int nx, int ny, int pitch, size_t plane_elems) {
     using CC = typename Coef<T>::C;
     constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
@@ -105,9 +105,15 @@ k_step_tile(const T *__restrict__ in, T *__restrict__ out,
         const int r = t / RX, c = t - r * RX;
         const int gx = wrap(x0 - HALO + c, nx), gy = wrap(y0 - HALO + r, ny);
         const size_t g = size_t(gy) * pitch + gx;
+        // the pending potential operator of the previous step first
+        T q[6];
+        load_site<T, P, VM>(in, plane_elems, g, VIN, midx, table, q);
 #pragma unroll
-        for (int p = 0; p < P; ++p) s[p * plane + t] = in[p * plane_elems + g];
-        sc[t] = coefC[g];
+        for (int k = 0; k < 6; ++k) {
+            const int p = plane_of<P>(k);
+            if (p >= 0) s[p * plane + t] = q[k];
+        }
+        sc[t] = table[midx[g]].c;
     }
     __syncthreads();
     apply_U<T, P, true, RX, RY, TX>(s, sc);    // U_x (Eq. 2e6)
@@ -125,7 +131,6 @@ k_step_tile(const T *__restrict__ in, T *__restrict__ out,
             q[k] = p >= 0 ? s[p * plane + st] : T(0);
         }
         const size_t g = size_t(gy) * pitch + gx;
-        if constexpr (VM != V_NONE) apply_potential<T, P, VM>(q, coefV[g]);  // V_y V_x
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const int p = plane_of<P>(k);
@@ -134,12 +139,12 @@ k_step_tile(const T *__restrict__ in, T *__restrict__ out,
     }
 }
 
-template <typename T, int P, int VM>
+template <typename T, int P, int VM, bool VIN>
 cudaError_t launch_tile_t(qla_ctx *c, const void *in, void *out) {
     constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
     constexpr int RX = TX + 2 * HALO, RY = TY + 2 * HALO;
     const size_t smem = size_t(RX) * RY * (sizeof(typename Coef<T>::C) + P * sizeof(T));
-    auto kern = k_step_tile<T, P, VM>;
+    auto kern = k_step_tile<T, P, VM, VIN>;
     static bool configured = false;  // per instantiation, per process
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -150,29 +155,32 @@ cudaError_t launch_tile_t(qla_ctx *c, const void *in, void *out) {
     dim3 grid((c->nx + TX - 1) / TX, (c->ny + TY - 1) / TY);
     kern<<<grid, THREADS, smem, c->stream>>>(
         static_cast<const T *>(in), static_cast<T *>(out),
-        static_cast<const typename Coef<T>::C *>(c->coefC),
-        static_cast<const typename Coef<T>::V *>(c->coefV), c->nx, c->ny, c->pitch,
+        c->midx, static_cast<const MedRec<T> *>(c->table), c->nx, c->ny, c->pitch,
         c->plane_elems);
     return cudaGetLastError();
 }
 
 template <typename T, int P>
-cudaError_t launch_tile_vm(qla_ctx *c, const void *in, void *out) {
+cudaError_t launch_tile_vm(qla_ctx *c, const void *in, void *out, bool vin) {
     switch (c->vmode) {
-    case V_ROTATION: return launch_tile_t<T, P, V_ROTATION>(c, in, out);
-    case V_LITERAL:  return launch_tile_t<T, P, V_LITERAL>(c, in, out);
-    default:         return launch_tile_t<T, P, V_NONE>(c, in, out);
+    case V_ROTATION:
+        return vin ? launch_tile_t<T, P, V_ROTATION, true>(c, in, out)
+                   : launch_tile_t<T, P, V_ROTATION, false>(c, in, out);
+    case V_LITERAL:
+        return vin ? launch_tile_t<T, P, V_LITERAL, true>(c, in, out)
+                   : launch_tile_t<T, P, V_LITERAL, false>(c, in, out);
+    default: return launch_tile_t<T, P, V_NONE, false>(c, in, out);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_step_tile(qla_ctx *c, const void *in, void *out) {
+cudaError_t launch_step_tile(qla_ctx *c, const void *in, void *out, bool vin) {
     if (c->prec == QLA_FP64)
-        return c->P == 6 ? launch_tile_vm<double, 6>(c, in, out)
-                         : launch_tile_vm<double, 3>(c, in, out);
-    return c->P == 6 ? launch_tile_vm<float, 6>(c, in, out)
-                     : launch_tile_vm<float, 3>(c, in, out);
+        return c->P == 6 ? launch_tile_vm<double, 6>(c, in, out, vin)
+                         : launch_tile_vm<double, 3>(c, in, out, vin);
+    return c->P == 6 ? launch_tile_vm<float, 6>(c, in, out, vin)
+                     : launch_tile_vm<float, 3>(c, in, out, vin);
 }
 
 }  // namespace qla

@@ -67,7 +67,8 @@ def load():
                            ("qla_fields", [c_vp] + [c_vp] * 6),
                            ("qla_set_time_block", [c_vp, c_int]),
                            ("qla_probe", [c_vp, c_int, c_vp, c_vp, c_vp]),
-                           ("qla_set_step_kernel", [c_vp, c_int])):
+                           ("qla_set_step_kernel", [c_vp, c_int]),
+                           ("qla_set_march_tuning", [c_vp, c_int, c_int])):
             getattr(lib, name).argtypes = args
             getattr(lib, name).restype = c_int
         lib.qla_init_grid.restype = c_int
@@ -177,6 +178,10 @@ def qla_set_step_kernel(ctx, kernel):
     _check(ctx, load().qla_set_step_kernel(ctx, int(kernel)))
 
 
+def qla_set_march_tuning(ctx, lane_cols=0, rows=0):
+    _check(ctx, load().qla_set_march_tuning(ctx, int(lane_cols), int(rows)))
+
+
 def qla_launch_count(ctx):
     return int(load().qla_launch_count(ctx))
 
@@ -269,6 +274,9 @@ class Grid:
         """"auto", "tile" or "march" (see qla_set_step_kernel)."""
         k = {"auto": QLA_KERNEL_AUTO, "tile": QLA_KERNEL_TILE, "march": QLA_KERNEL_MARCH}
         qla_set_step_kernel(self._ctx, k.get(kernel, kernel))
+
+    def set_march_tuning(self, lane_cols=0, rows=0):
+        qla_set_march_tuning(self._ctx, lane_cols, rows)
 
     def set_time_block(self, k):
         qla_set_time_block(self._ctx, k)

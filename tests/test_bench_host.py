@@ -1,0 +1,62 @@
+"""Host-side logic of bench.py on CPU: the multi-rank timing helpers over a
+world of two gloo ranks, and the clock-record parser."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    bench.barrier(world)
+    t = bench.max_over_ranks(world, 1.5 + rank)   # rank 1 is the slow one
+    bench.barrier(world)
+    q.put((rank, t))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(60)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=5) for _ in range(2))
+    assert got == {0: 2.5, 1: 2.5}
+
+
+def test_single_rank_helpers_are_identity():
+    bench.barrier(1)
+    assert bench.max_over_ranks(1, 3.25) == 3.25
+
+
+def test_clock_parser():
+    text = "\n".join([
+        "0, 1980, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2070, 2070, 1100.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2010, 2070, 1000.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ])
+    rec = bench.ClockSampler.parse(text)
+    assert rec["sm_mhz"] == 2010 and rec["sm_max_mhz"] == 2070 and rec["samples"] == 3
+    assert rec["reasons"] == ["sw_power_cap"]
+    assert bench.ClockSampler.parse("") is None

@@ -30,10 +30,11 @@ def rel_l2(a, b):
 
 
 def gpu_run(n, delta, steps, q0=None, packet=None, precision="fp64", te=False,
-            potential="rotation", time_block=0, kernel="auto"):
+            potential="rotation", time_block=0, kernel="auto", lane_cols=0, rows=0):
     ny, nx = n.shape
     with qla.Grid(nx, ny, delta, precision, te_only=te, potential=potential) as g:
         g.set_step_kernel(kernel)
+        g.set_march_tuning(lane_cols, rows)
         if time_block:
             g.set_time_block(time_block)
         g.set_medium(n)
@@ -102,6 +103,32 @@ def test_march_and_tile_kernels_agree_bitwise(shape, te, precision):
     b, eb = gpu_run(n, 1.0, 13, q0=q0, precision=precision, te=te, kernel="march")
     assert np.array_equal(a, b)
     assert ea == eb
+
+
+@pytest.mark.parametrize("lane_cols,rows", [(2, 0), (4, 0), (2, 36), (4, 12)])
+def test_march_tunings_agree_bitwise(lane_cols, rows):
+    """Lane width and segment height change the work split, not the result."""
+    nx, ny = 256, 100
+    n = inputs.random_medium(nx, ny, seed=21, lo=1.0, hi=2.5)
+    q0 = inputs.random_state(nx, ny, seed=22, planes=3)
+    ref, _ = gpu_run(n, 1.0, 9, q0=q0, precision="fp32", te=True, kernel="tile")
+    got, _ = gpu_run(n, 1.0, 9, q0=q0, precision="fp32", te=True, kernel="march",
+                     lane_cols=lane_cols, rows=rows)
+    assert np.array_equal(ref, got)
+
+
+def test_medium_with_more_distinct_values_than_shared_slots():
+    """4356 plateaus of distinct n: more keys than the 4096 shared-record
+    slots, so part of the uniform sites take their own records."""
+    nx = ny = 198
+    rng = np.random.default_rng(5)
+    vals = rng.uniform(1.0, 3.0, (ny // 3, nx // 3))
+    n = np.kron(vals, np.ones((3, 3)))
+    q0 = inputs.random_state(nx, ny, seed=6)
+    want = oracle.run(q0, n, 1.0, 6)
+    for kernel in ("tile", "march"):
+        got, _ = gpu_run(n, 1.0, 6, q0=q0, kernel=kernel)
+        assert rel_l2(got, want) <= 1e-12, kernel
 
 
 def test_random_state_fp64_te_matches_six_plane():
