@@ -27,7 +27,7 @@ __device__ __forceinline__ void make_rec(MedRec<double> &r, double th, double px
     double sx, cx, sy, cy;
     sincos(px, &sx, &cx);
     sincos(py, &sy, &cy);
-    r.v = make_double4(cx, sx, cy, sy);
+    r.v = make_double4_16a(cx, sx, cy, sy);
 }
 
 __device__ __forceinline__ void split(double v, float &hi, float &lo) {

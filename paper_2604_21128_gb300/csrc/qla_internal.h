@@ -65,7 +65,7 @@ __host__ __device__ constexpr Pair pair_of(bool xdir, int k) {
 //         CoefV = (gamma_x, s_x, gamma_y, s_y), gamma = 1 - cos, single words.
 // ----------------------------------------------------------------------------
 template <typename T> struct Coef;
-template <> struct Coef<double> { using C = double2; using V = double4; };
+template <> struct Coef<double> { using C = double2; using V = double4_16a; };
 template <> struct Coef<float>  { using C = float4;  using V = float4; };
 
 // Per-site medium record: collision and potential coefficients together.

@@ -24,9 +24,10 @@
 //    does not touch are stored right after U_x, the others four rows later.
 // The collision coefficients of the four rows in flight sit in a register
 // ring; records come from the medium table through a 4-byte index per site.
-// The next row's state and records and the indices two rows ahead are loaded
-// one iteration early.  The march loop is unrolled by four so that every ring
-// slot is a fixed register.
+// Rows are staged three ahead into a per-warp shared-memory ring by per-lane
+// cp.async copies (no registers held while the loads fly); the next row's
+// records are looked up one iteration early.  The march loop is unrolled by
+// four so that every ring slot is a fixed register or buffer.
 #include "qla_internal.h"
 
 namespace qla {
@@ -204,76 +205,105 @@ __device__ __forceinline__ void iload(const uint32_t *p, uint32_t (&v)[LX]) {
     else { v[0] = t.x; v[1] = t.y; }
 }
 
+// Per-lane asynchronous global -> shared copies (no registers held while
+// the data is in flight); each lane later reads back only what it copied.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(gmem), "n"(BYTES)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+constexpr int NSLOT = 4;   // rows staged per warp: the current one and 3 ahead
+
 template <typename T, int P, int LX, int VM, bool VIN>
 struct March {
     using CC = typename Coef<T>::C;
     using CV = typename Coef<T>::V;
     static constexpr int W = 32 * LX;   // window columns
     static constexpr int WOUT = W - 8;  // stored columns
+    // one staged row: P planes of W values, then W record indices
+    struct Slot {
+        T q[P][W];
+        uint32_t idx[W];
+    };
 
+    // this lane's column in each array (offsets below are element offsets
+    // of a row start, 32-bit: ny * pitch < 2^31 is checked on the host)
     const T *in;
     T *out;
     const uint32_t *midx;
     const MedRec<T> *table;
-    int nx, ny, pitch, seg_h, n_wx, n_items;
-    size_t plane;
+    uint32_t plane, total;  // plane stride; ny * pitch
+    int pitch;
+    Slot *ring;             // this warp's NSLOT staged rows
+    int lc;                 // this lane's first column in the window
 
     // state carried along the march
     T carry[4][2][2][LX];   // [neighbour layer][pair][value][x]
     CC kring[LAG][LX];      // collision coefficients of the rows in flight
-    T qbuf[2][6][LX];       // this row and the prefetched next row (by parity)
-    uint32_t ibuf[2][LX];   // record indices of rows J (parity of J) and J+1
     CC knext[LX];           // row J+1's records, looked up one row early
     CV vnext[LX];
-    // wrapped row offsets: next state row, index row two ahead, output rows
-    size_t o_in, o_idx, o_now, o_out;
+    // row offsets: next row to stage, the two output rows
+    uint32_t o_in, o_now, o_out;
 
-    __device__ __forceinline__ size_t next_row(size_t o) const {
-        o += pitch;
-        return o == size_t(ny) * pitch ? 0 : o;
+    __device__ __forceinline__ uint32_t next_row(uint32_t o) const {
+        o += uint32_t(pitch);
+        return o == total ? 0u : o;
     }
 
-    template <int B>
-    __device__ __forceinline__ void fetch_state(size_t ro) {
+    // Stage the row at offset o_in into slot S (one commit group).
+    template <int S>
+    __device__ __forceinline__ void stage() {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            const int p = plane_of<P>(c);
-            if (p >= 0) vload<T, LX>(in + p * plane + ro, qbuf[B][c]);
-        }
+        for (int p = 0; p < P; ++p)
+            cp_async<LX * sizeof(T)>(&ring[S].q[p][lc], in + p * plane + o_in);
+        cp_async<LX * 4>(&ring[S].idx[lc], midx + o_in);
+        cp_async_commit();
+        o_in = next_row(o_in);
     }
 
-    template <int B>
+    template <int S>
     __device__ __forceinline__ void lookup_next() {
 #pragma unroll
         for (int x = 0; x < LX; ++x) {
-            const MedRec<T> *r = table + ibuf[B][x];
+            const MedRec<T> *r = table + ring[S].idx[lc + x];
             knext[x] = r->c;
             if constexpr (VIN) vnext[x] = r->v;
         }
     }
 
     // One march iteration for input row J; PH = (J - J0) mod 4 picks the
-    // ring slots, its parity the prefetch buffers.  On entry qbuf[B] holds row
-    // J, knext/vnext its records, ibuf[B^1] the indices of row J+1.
+    // register ring slots and the staging slot of row J.  On entry knext,
+    // vnext hold row J's records.  Rows J and J - 4 are stored when they
+    // fall in [st_lo, st_lo + st_n).
     template <int PH>
-    __device__ __forceinline__ void iter(int J, int xl, int y_lo, int y_hi, int lane) {
+    __device__ __forceinline__ void iter(int J, int st_lo, unsigned st_n) {
         constexpr int S0 = PH, S1 = (PH + 3) & 3, S2 = (PH + 2) & 3, S3 = (PH + 1) & 3;
-        constexpr int B = PH & 1;
-        T (&q)[6][LX] = qbuf[B];
-        CV kv[LX];
+        // stage row J + 3 into the slot row J - 1 used; wait for row J + 1
+        stage<(PH + 3) & (NSLOT - 1)>();
+        cp_async_wait<NSLOT - 2>();
+        T q[6][LX];
 #pragma unroll
-        for (int x = 0; x < LX; ++x) {
-            kring[S0][x] = knext[x];
-            if constexpr (VIN) kv[x] = vnext[x];
+        for (int c = 0; c < 6; ++c) {
+            const int p = plane_of<P>(c);
+            if (p >= 0) {
+#pragma unroll
+                for (int x = 0; x < LX; ++x) q[c][x] = ring[PH].q[p][lc + x];
+            }
         }
-        // loads for later rows fly while this row computes: the next row's
-        // state, the indices two rows ahead, the next row's records
-        fetch_state<B ^ 1>(o_in + xl);
-        o_in = next_row(o_in);
-        iload<T, LX>(midx + o_idx + xl, ibuf[B]);
-        o_idx = next_row(o_idx);
-        lookup_next<B ^ 1>();
-
+#pragma unroll
+        for (int x = 0; x < LX; ++x) kring[S0][x] = knext[x];
         // the previous step's V_x, V_y on the entering row
         if constexpr (VIN) {
 #pragma unroll
@@ -281,22 +311,23 @@ struct March {
                 T s[6];
 #pragma unroll
                 for (int c = 0; c < 6; ++c) s[c] = plane_of<P>(c) >= 0 ? q[c][x] : T(0);
-                apply_potential<T, P, VM>(s, kv[x]);
+                apply_potential<T, P, VM>(s, vnext[x]);
 #pragma unroll
                 for (int c = 0; c < 6; ++c)
                     if (plane_of<P>(c) >= 0) q[c][x] = s[c];
             }
         }
+        // row J + 1's records fly while this row computes
+        lookup_next<(PH + 1) & (NSLOT - 1)>();
+
         apply_ux<T, P, LX>(q, kring[S0]);                          // U_x, row J
 
-        // lanes whose columns are all inside [4, W - 4) hold output columns
-        const bool lane_out = lane * LX >= 4 && lane * LX + LX <= W - 4;
         // planes U_y does not touch are final for row J now
-        if (J >= y_lo && J < y_hi && lane_out) {
+        if (unsigned(J - st_lo) < st_n) {
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
                 const int p = plane_of<P>(c);
-                if (p >= 0 && !in_y_pair<P>(c)) vstore<T, LX>(out + p * plane + o_now + xl, q[c]);
+                if (p >= 0 && !in_y_pair<P>(c)) vstore<T, LX>(out + p * plane + o_now, q[c]);
             }
         }
         o_now = next_row(o_now);
@@ -311,27 +342,32 @@ struct March {
         uy_neighbour<T, P, LX, 7>(q, carry[3], kring[S3]);         // L8 -> row J-4
 
         // the U_y planes of row J - 4 are final
-        const int R = J - LAG;
-        if (R >= y_lo && R < y_hi && lane_out) {
+        if (unsigned(J - LAG - st_lo) < st_n) {
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
                 const int p = plane_of<P>(c);
-                if (p >= 0 && in_y_pair<P>(c)) vstore<T, LX>(out + p * plane + o_out + xl, q[c]);
+                if (p >= 0 && in_y_pair<P>(c)) vstore<T, LX>(out + p * plane + o_out, q[c]);
             }
         }
         o_out = next_row(o_out);
     }
 
-    __device__ __forceinline__ void run() {
+    __device__ __forceinline__ void run(int nx, int ny, int seg_h, int n_wx, int n_items,
+                                        Slot *warp_ring) {
         const int lane = threadIdx.x & 31;
         const int item = blockIdx.x * WARPS + (threadIdx.x >> 5);
         if (item >= n_items) return;
+        ring = warp_ring;
+        lc = lane * LX;
         const int wx = item % n_wx, wy = item / n_wx;
         // window columns [x0, x0 + W), x0 = wx*WOUT - 4 (periodic)
         int xl = wx * WOUT - 4 + lane * LX;
         const bool lane_store_ok = xl >= 0 ? xl < nx : true;
         xl %= nx;
         if (xl < 0) xl += nx;
+        in += xl;
+        out += xl;
+        midx += xl;
         const int y_lo = wy * seg_h;
         const int y_hi = min(ny, y_lo + seg_h);
 #pragma unroll
@@ -342,27 +378,28 @@ struct March {
                 for (int c = 0; c < 2; ++c)
 #pragma unroll
                     for (int x = 0; x < LX; ++x) carry[a][b][c][x] = T(0);
-        // rows y_lo-4 .. y_hi+3 enter; rows y_lo .. y_hi-1 are stored
+        // rows y_lo-4 .. y_hi+3 enter; rows y_lo .. y_hi-1 are stored by the
+        // lanes whose columns are all inside [4, W - 4) and below nx
         const int J0 = y_lo - LAG;
         const int J1 = y_hi + LAG;  // exclusive
-        // lanes whose output columns fall beyond nx (last window) must not
-        // store: make their segment empty
-        const int st_lo = lane_store_ok ? y_lo : y_hi;
-        const size_t o0 = size_t(wrap(J0, ny)) * pitch;
-        fetch_state<0>(o0 + xl);
-        iload<T, LX>(midx + o0 + xl, ibuf[0]);
-        o_in = next_row(o0);
-        iload<T, LX>(midx + o_in + xl, ibuf[1]);
-        o_idx = next_row(o_in);
-        o_now = o0;
-        o_out = size_t(wrap(J0 - LAG, ny)) * pitch;
+        const bool lane_out = lc >= 4 && lc + LX <= W - 4 && lane_store_ok;
+        const unsigned st_n = lane_out ? unsigned(y_hi - y_lo) : 0u;
+        o_in = uint32_t(wrap(J0, ny)) * uint32_t(pitch);
+        o_now = o_in;
+        o_out = uint32_t(wrap(J0 - LAG, ny)) * uint32_t(pitch);
+        // rows J0, J0+1, J0+2 in flight; row J0's records before the loop
+        stage<0>();
+        stage<1>();
+        stage<2>();
+        cp_async_wait<2>();
         lookup_next<0>();
         for (int J = J0; J < J1; J += 4) {
-            iter<0>(J + 0, xl, st_lo, y_hi, lane);
-            iter<1>(J + 1, xl, st_lo, y_hi, lane);
-            iter<2>(J + 2, xl, st_lo, y_hi, lane);
-            iter<3>(J + 3, xl, st_lo, y_hi, lane);
+            iter<0>(J + 0, y_lo, st_n);
+            iter<1>(J + 1, y_lo, st_n);
+            iter<2>(J + 2, y_lo, st_n);
+            iter<3>(J + 3, y_lo, st_n);
         }
+        cp_async_wait<0>();
     }
 };
 
@@ -378,29 +415,27 @@ __global__ void __launch_bounds__(32 * WARPS, min_blocks<T, P, LX>())
 k_step_march(const T *__restrict__ in, T *__restrict__ out, const uint32_t *__restrict__ midx,
              const MedRec<T> *__restrict__ table, int nx, int ny, int pitch, size_t plane,
              int seg_h, int n_wx, int n_items) {
-    March<T, P, LX, VM, VIN> m;
+    using M = March<T, P, LX, VM, VIN>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename M::Slot *ring =
+        reinterpret_cast<typename M::Slot *>(smem_raw) + (threadIdx.x >> 5) * NSLOT;
+    M m;
     m.in = in;
     m.out = out;
     m.midx = midx;
     m.table = table;
-    m.nx = nx;
-    m.ny = ny;
     m.pitch = pitch;
-    m.plane = plane;
-    m.seg_h = seg_h;
-    m.n_wx = n_wx;
-    m.n_items = n_items;
-    m.run();
+    m.plane = uint32_t(plane);
+    m.total = uint32_t(ny) * uint32_t(pitch);
+    m.run(nx, ny, seg_h, n_wx, n_items, ring);
 }
 
-// Segment height: as many equal work items as resident warp slots (one full
-// wave, or several if a segment would exceed 512 rows), each at least 32 rows
-// and a multiple of 4.
+// Segment height: about two work items per resident warp slot (measured
+// on the 8192^2 lattice: one exact wave leaves the schedulers less slack
+// than two), rows a multiple of 4 and at least 32.
 inline int pick_segment(int ny, int n_wx, long long resident_warps) {
     if (resident_warps < 1) resident_warps = 1;
-    long long waves = 1;
-    while ((long long)n_wx * ny / (resident_warps * waves) > 512) ++waves;
-    long long n_wy = resident_warps * waves / n_wx;
+    long long n_wy = 2 * resident_warps / n_wx;
     if (n_wy < 1) n_wy = 1;
     int seg = int((ny + n_wy - 1) / n_wy);
     if (seg < 32) seg = 32;
@@ -411,10 +446,14 @@ template <typename T, int P, int LX, int VM, bool VIN>
 cudaError_t launch_t(qla_ctx *c, const void *in, void *out) {
     constexpr int WOUT = 32 * LX - 8;
     auto kern = k_step_march<T, P, LX, VM, VIN>;
+    const size_t smem = sizeof(typename March<T, P, LX, VM, VIN>::Slot) * NSLOT * WARPS;
     static int blocks_per_sm = -1;  // per instantiation, per process
     if (blocks_per_sm < 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(smem));
+        if (e != cudaSuccess) return e;
         int b = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * WARPS, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * WARPS, smem);
         if (e != cudaSuccess) return e;
         blocks_per_sm = b > 0 ? b : 1;
     }
@@ -427,7 +466,7 @@ cudaError_t launch_t(qla_ctx *c, const void *in, void *out) {
     const int n_wy = (c->ny + seg - 1) / seg;
     const int n_items = n_wx * n_wy;
     const int blocks = (n_items + WARPS - 1) / WARPS;
-    kern<<<blocks, 32 * WARPS, 0, c->stream>>>(
+    kern<<<blocks, 32 * WARPS, smem, c->stream>>>(
         static_cast<const T *>(in), static_cast<T *>(out), c->midx,
         static_cast<const MedRec<T> *>(c->table), c->nx, c->ny, c->pitch, c->plane_elems, seg,
         n_wx, n_items);
@@ -461,7 +500,8 @@ int march_lane_cols(const qla_ctx *c) {
 
 bool march_supported(const qla_ctx *c) {
     const int lx = march_lane_cols(c);
-    return c->nx % lx == 0 && c->nx >= 32 * lx && c->ny >= 8;
+    return c->nx % lx == 0 && c->nx >= 32 * lx && c->ny >= 8 &&
+           c->plane_elems < (size_t(1) << 31);
 }
 
 cudaError_t launch_step_march(qla_ctx *c, const void *in, void *out, bool vin) {
