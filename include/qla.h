@@ -204,6 +204,78 @@ qla_status qla_energy_noalloc(const void *planes, int precision, int n_planes, i
  * depend on either.  QLA_EINVAL for other values. */
 qla_status qla_set_march_tuning(qla_ctx *ctx, int lane_cols, int rows);
 
+/* ------------------------------------------------------------------------
+ * Batched lattices.  A batch holds `count` independent periodic lattices
+ * (sizes nx[k] x ny[k], common delta, precision and flags) in one workspace
+ * and advances all of them together with one persistent kernel launch per
+ * chunk of steps: every warp of a co-resident (cooperative) grid takes work
+ * items -- a column window and row segment of some lattice -- and the grid
+ * synchronises between steps with a barrier whose wait is bounded.
+ * Instance k is an ordinary context (qla_batch_instance): set its medium and
+ * packet or state, read its energy, fields or probes with the qla_* calls.
+ * ------------------------------------------------------------------------ */
+typedef struct qla_batch qla_batch;
+
+/* Workspace bytes for a batch (0 for invalid arguments). */
+size_t qla_batch_workspace_bytes(int count, const int *nx, const int *ny, int precision,
+                                 unsigned flags);
+
+/* Create a batch of `count` >= 1 lattices; every nx[k] must be a multiple
+ * of 4 and >= 128, every ny[k] >= 8 (the marching kernel's requirements).
+ * workspace / workspace_bytes / cuda_stream as for qla_init_grid. */
+qla_status qla_batch_create(qla_batch **out, int count, const int *nx, const int *ny,
+                            double delta, int precision, unsigned flags, void *cuda_stream,
+                            void *workspace, size_t workspace_bytes);
+
+/* The context of instance k (owned by the batch; do not destroy it). */
+qla_ctx *qla_batch_instance(qla_batch *b, int k);
+
+/* Advance every instance by n_steps >= 0 steps of Eq. 2e14: persistent
+ * launches of at most QLA_BATCH_CHUNK steps each, enqueued on the batch's
+ * stream.  Every instance must have a medium and a state.  Returns
+ * QLA_ETIMEOUT (and leaves the states undefined) if a grid barrier's bounded
+ * wait ran out; the check synchronises the stream after the last chunk. */
+#define QLA_BATCH_CHUNK 1000
+qla_status qla_batch_step(qla_batch *b, long long n_steps);
+
+/* Run n_steps steps reading every instance's energy every `every` steps:
+ * the whole sequence (persistent step launches and batched energy
+ * reductions) is captured once as a CUDA graph and replayed.  energies
+ * receives (n_steps / every) * count doubles, row r holding all instances'
+ * energies after (r + 1) * every steps.  n_steps must be a multiple of every.
+ * Synchronises. */
+qla_status qla_batch_run(qla_batch *b, long long n_steps, long long every, double *energies);
+
+/* Energy (as qla_energy) of every instance into out[0..count). Synchronises. */
+qla_status qla_batch_energy(qla_batch *b, double *out);
+
+/* Autotuner: time each candidate (columns per lane in {2, 4}, rows per work
+ * item in {64, 128, 256}) on `trial_steps` real steps and keep the fastest.
+ * The states advance by 6 * trial_steps steps, as if qla_batch_step had
+ * been called.  *chosen_lane_cols / *chosen_rows (may be NULL) receive the
+ * choice. */
+qla_status qla_batch_autotune(qla_batch *b, int trial_steps, int *chosen_lane_cols,
+                              int *chosen_rows);
+
+/* Tiling used by later qla_batch_step / qla_batch_run calls (as for
+ * qla_set_march_tuning; 0 = library choice). */
+qla_status qla_batch_set_tuning(qla_batch *b, int lane_cols, int rows);
+
+/* Test hook for the bounded grid barrier (never needed in normal use):
+ * budget_cycles > 0 sets each barrier wait's limit in SM clock cycles
+ * (default 2^31, about one second); skip_block >= 0 makes that block skip
+ * its arrival at the first barrier, so every other block's wait runs out
+ * and the step returns QLA_ETIMEOUT with no fault.  -1 restores normal. */
+qla_status qla_batch_debug_barrier(qla_batch *b, long long budget_cycles, int skip_block);
+
+/* Kernel launches enqueued by the batch (persistent and energy). */
+long long qla_batch_launch_count(const qla_batch *b);
+
+const char *qla_batch_last_error(const qla_batch *b);
+
+/* Free the batch (and its workspace if the library allocated it). */
+void qla_batch_destroy(qla_batch *b);
+
 /* Kernel launches enqueued by this context since creation (diagnostics). */
 long long qla_launch_count(const qla_ctx *ctx);
 

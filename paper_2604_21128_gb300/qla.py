@@ -72,6 +72,27 @@ def load():
             getattr(lib, name).argtypes = args
             getattr(lib, name).restype = c_int
         lib.qla_init_grid.restype = c_int
+        lib.qla_batch_workspace_bytes.argtypes = [c_int, c_vp, c_vp, c_int, c_u]
+        lib.qla_batch_workspace_bytes.restype = c_sz
+        lib.qla_batch_create.argtypes = [ctypes.POINTER(c_vp), c_int, c_vp, c_vp,
+                                         ctypes.c_double, c_int, c_u, c_vp, c_vp, c_sz]
+        lib.qla_batch_create.restype = c_int
+        lib.qla_batch_instance.argtypes = [c_vp, c_int]
+        lib.qla_batch_instance.restype = c_vp
+        for name, args in (("qla_batch_step", [c_vp, c_ll]),
+                           ("qla_batch_run", [c_vp, c_ll, c_ll, c_vp]),
+                           ("qla_batch_energy", [c_vp, c_vp]),
+                           ("qla_batch_autotune", [c_vp, c_int, c_vp, c_vp]),
+                           ("qla_batch_set_tuning", [c_vp, c_int, c_int]),
+                           ("qla_batch_debug_barrier", [c_vp, c_ll, c_int])):
+            getattr(lib, name).argtypes = args
+            getattr(lib, name).restype = c_int
+        lib.qla_batch_launch_count.argtypes = [c_vp]
+        lib.qla_batch_launch_count.restype = c_ll
+        lib.qla_batch_last_error.argtypes = [c_vp]
+        lib.qla_batch_last_error.restype = ctypes.c_char_p
+        lib.qla_batch_destroy.argtypes = [c_vp]
+        lib.qla_batch_destroy.restype = None
         lib.qla_launch_count.argtypes = [c_vp]
         lib.qla_launch_count.restype = c_ll
         lib.qla_last_error.argtypes = [c_vp]
@@ -286,10 +307,129 @@ class Grid:
         return qla_launch_count(self._ctx)
 
     def close(self):
+        if getattr(self, "_borrowed", False):
+            self._ctx = None
+            return
         if getattr(self, "_ctx", None):
             with self._dev():
                 qla_destroy(self._ctx)
             self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# ---------------------------------------------------------------------------
+# Batched lattices
+# ---------------------------------------------------------------------------
+
+def _bcheck(b, status):
+    if status != 0:
+        raise QLAError(status, load().qla_batch_last_error(b).decode() if b else "")
+
+
+class Batch:
+    """Many independent lattices advanced together by one persistent launch
+    per chunk of steps (qla_batch_* in the C ABI).  ``instance(k)`` is a
+    ``Grid``-like view of lattice k (medium, packet, state, energy, fields).
+    """
+
+    def __init__(self, sizes, delta=1.0, precision="fp32", te_only=False,
+                 potential="rotation", device=None, stream=None):
+        import torch
+        lib = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libqla needs a CUDA device; none is available")
+        self.count = len(sizes)
+        nx = np.ascontiguousarray([int(a) for a, _ in sizes], dtype=np.int32)
+        ny = np.ascontiguousarray([int(b) for _, b in sizes], dtype=np.int32)
+        self.sizes = list(zip(nx.tolist(), ny.tolist()))
+        prec = {"fp64": QLA_FP64, "fp32": QLA_FP32}[precision]
+        flags = (QLA_TE_ONLY if te_only else 0) | {
+            "rotation": 0, "literal": QLA_POTENTIAL_LITERAL, "none": QLA_POTENTIAL_NONE}[potential]
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else device)
+        nbytes = int(lib.qla_batch_workspace_bytes(self.count, ctypes.c_void_p(nx.ctypes.data),
+                                                   ctypes.c_void_p(ny.ctypes.data), prec, flags))
+        if nbytes == 0:
+            raise QLAError(1, "invalid batch (each nx a multiple of 4 and >= 128, ny >= 8)")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            b = ctypes.c_void_p()
+            st = lib.qla_batch_create(ctypes.byref(b), self.count, ctypes.c_void_p(nx.ctypes.data),
+                                      ctypes.c_void_p(ny.ctypes.data), float(delta), prec, flags,
+                                      ctypes.c_void_p(self.stream.cuda_stream),
+                                      ctypes.c_void_p(self.workspace.data_ptr()), nbytes)
+            _bcheck(None, st)
+            self._b = b
+
+    def _dev(self):
+        import torch
+        return torch.cuda.device(self.device)
+
+    def instance(self, k):
+        """A Grid bound to lattice k (owned by the batch)."""
+        ctx = load().qla_batch_instance(self._b, int(k))
+        if not ctx:
+            raise IndexError(k)
+        g = Grid.__new__(Grid)
+        g.nx, g.ny = self.sizes[k]
+        g.device, g.stream = self.device, self.stream
+        g._ctx = ctypes.c_void_p(ctx)
+        g._borrowed = True
+        return g
+
+    def step(self, n_steps):
+        with self._dev():
+            _bcheck(self._b, load().qla_batch_step(self._b, int(n_steps)))
+
+    def run(self, n_steps, every):
+        """Graph-captured run; returns energies of shape (n_steps // every, count)."""
+        out = np.empty((int(n_steps) // int(every), self.count))
+        with self._dev():
+            _bcheck(self._b, load().qla_batch_run(self._b, int(n_steps), int(every),
+                                                  ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def energy(self):
+        out = np.empty(self.count)
+        with self._dev():
+            _bcheck(self._b, load().qla_batch_energy(self._b, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def autotune(self, trial_steps=2):
+        lx, rows = ctypes.c_int(), ctypes.c_int()
+        with self._dev():
+            _bcheck(self._b, load().qla_batch_autotune(self._b, int(trial_steps), ctypes.byref(lx),
+                                                       ctypes.byref(rows)))
+        return lx.value, rows.value
+
+    def set_tuning(self, lane_cols=0, rows=0):
+        _bcheck(self._b, load().qla_batch_set_tuning(self._b, int(lane_cols), int(rows)))
+
+    def debug_barrier(self, budget_cycles=0, skip_block=-1):
+        _bcheck(self._b, load().qla_batch_debug_barrier(self._b, int(budget_cycles),
+                                                        int(skip_block)))
+
+    @property
+    def launches(self):
+        return int(load().qla_batch_launch_count(self._b))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            with self._dev():
+                load().qla_batch_destroy(self._b)
+            self._b = None
 
     def __del__(self):
         try:
