@@ -276,6 +276,80 @@ const char *qla_batch_last_error(const qla_batch *b);
 /* Free the batch (and its workspace if the library allocated it). */
 void qla_batch_destroy(qla_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Learned surrogate.  Not part of the paper's method: a convolutional
+ * operator that advances an FP32 E_z lattice (rotation reading) K steps at
+ * once, trained on trajectories this library computes, with plain QLA as
+ * the fallback and judge.  Network: five levels of widths 32, 64, 128, 256,
+ * 256; 3x3 periodic convolutions, leaky ReLU 0.1, 2x2 average pooling,
+ * nearest 2x upsampling with additive skips; BF16 weights and activations,
+ * FP32 accumulation on the tensor cores, FP32 master weights and Adam.
+ * Inputs per site (features, FP32 [h][w][6]): q2, q3, q4, n - 1.5,
+ * 4 dn/dx, 4 dn/dy; output ([h][w][3]): the change of q2, q3, q4.
+ * ------------------------------------------------------------------------ */
+typedef struct surr_net surr_net;
+
+/* Device workspace bytes for a network on h x w lattices (multiples of 16)
+ * and batches of up to max_batch; 0 for invalid sizes. */
+size_t surr_workspace_bytes(int height, int width, int max_batch);
+
+/* Create a network with seeded initial weights in a caller-owned device
+ * workspace (256-byte aligned, kept alive until surr_destroy). */
+qla_status surr_create(surr_net **out, int height, int width, int max_batch,
+                       unsigned long long seed, void *cuda_stream, void *workspace,
+                       size_t workspace_bytes);
+
+/* Number of parameters, and their host copy: per convolution (10 of them,
+ * encoder levels 0..4, decoder levels 3..0, output) the weights as
+ * (cout, cin, 3, 3) then the biases (cout), real channel counts (the first
+ * convolution has cin = 6, the last cout = 3). */
+long long surr_param_count(const surr_net *n);
+qla_status surr_get_params(surr_net *n, float *host);
+qla_status surr_set_params(surr_net *n, const float *host);
+
+/* Forward pass on B samples: feat_dev [B][h][w][6] -> out_dev [B][h][w][3]
+ * (device FP32).  Asynchronous on the network's stream. */
+qla_status surr_forward(surr_net *n, const float *feat_dev, int B, float *out_dev);
+
+/* Mean-square loss against target_dev [B][h][w][3] and its gradient with
+ * respect to every parameter (grad_host, surr_param_count floats, same
+ * layout as surr_get_params; NULL to skip).  Synchronises. */
+qla_status surr_loss_grad(surr_net *n, const float *feat_dev, const float *target_dev, int B,
+                          double *loss, float *grad_host);
+
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) at learning rate lr. */
+qla_status surr_train_step(surr_net *n, const float *feat_dev, const float *target_dev, int B,
+                           float lr, double *loss);
+
+/* Features of a context's current state into feat_dev ([ny][nx][6]). */
+qla_status surr_features(qla_ctx *ctx, float *feat_dev);
+
+/* Advance `windows` windows of K steps: each window the network proposes
+ * the state K steps on; it is accepted only if the energy changes by at
+ * most energy_tol (relative; the exact step conserves it) and the discrete
+ * divergence of B changes by at most div_tol relative to |grad B| (the exact
+ * dynamics keep div B constant); otherwise the window is recomputed with
+ * qla_step(ctx, K).  scratch_dev: 12 * nx * ny floats.  *accepted receives
+ * the number of accepted windows; energies (may be NULL) the energy after
+ * each window.  The network must have been created for nx x ny. */
+qla_status surr_advance(qla_ctx *ctx, surr_net *n, int windows, int K, double energy_tol,
+                        double div_tol, float *scratch_dev, int *accepted, double *energies);
+
+const char *surr_last_error(const surr_net *n);
+void surr_destroy(surr_net *n);
+
+/* The network's two contraction kernels on their own (device pointers,
+ * NHWC, channel counts multiples of 32), for tests:
+ *   out[p][co] = sum_{tap, ci} w[co][tap][ci] in[p + shift(tap)][ci]
+ *   dw[co][tap][ci] = sum_p dz[p][co] in[p + shift(tap)][ci]
+ * with tap = 3 (dy + 1) + (dx + 1), shifts periodic in y and x; in, w, dz
+ * BF16, out and dw FP32; part holds splits * cout * 9 * cin floats. */
+qla_status surr_conv3x3_raw(const void *in_bf16, int B, int H, int W, int cin,
+                            const void *w_bf16, int cout, float *out_f32, void *cuda_stream);
+qla_status surr_weight_grad_raw(const void *dz_bf16, const void *in_bf16, int B, int H, int W,
+                                int cout, int cin, int splits, float *part, float *dw_f32,
+                                void *cuda_stream);
+
 /* Kernel launches enqueued by this context since creation (diagnostics). */
 long long qla_launch_count(const qla_ctx *ctx);
 

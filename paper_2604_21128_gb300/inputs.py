@@ -205,3 +205,25 @@ def random_medium(nx: int, ny: int, seed: int, lo=1.0, hi=3.0, smooth=2) -> np.n
         r = (r + np.roll(r, 1, 0) + np.roll(r, -1, 0) + np.roll(r, 1, 1) + np.roll(r, -1, 1)) / 5
     r = (r - r.min()) / max(r.max() - r.min(), 1e-12)
     return lo + (hi - lo) * r
+
+
+def surrogate_instance(rng, size=256):
+    """One seeded training lattice for the learned surrogate: the vacuum
+    bubble of the 16384^2 workload scaled to ``size`` (semi-axes 37.5 x 18.75
+    at 256, n = 1 inside a uniform n = 2, edge 1.5 cells) at a random
+    orientation and offset, and a Gaussian E_z packet with random angle,
+    k0 in [0.15, 0.35] rad/cell, width in [8, 16] cells and transverse width
+    in [24, 64] cells (wavenumbers stay resolved on the coarse lattice, so
+    they are drawn in cells rather than scaled).  Returns (medium kwargs for
+    ellipse_medium, packet kwargs)."""
+    f = size / 16384.0
+    ang = float(rng.uniform(0.0, math.pi))
+    c = size / 2 + rng.uniform(-0.1, 0.1, 2) * size
+    med = dict(a=2400.0 * f, b=1200.0 * f, n_in=1.0, n_out=2.0, edge=max(1.5, 8.0 * f),
+               angle=ang, centre=(float(c[0]), float(c[1])))
+    phi = float(rng.uniform(0.0, 2 * math.pi))
+    r = 0.3 * size
+    pk = dict(x0=float(c[0] - r * math.cos(phi)), y0=float(c[1] - r * math.sin(phi)), angle=phi,
+              k0=float(rng.uniform(0.15, 0.35)), width=float(rng.uniform(8.0, 16.0)),
+              transverse_width=float(rng.uniform(24.0, 64.0)), amplitude=1.0)
+    return med, pk

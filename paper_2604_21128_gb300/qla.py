@@ -93,6 +93,31 @@ def load():
         lib.qla_batch_last_error.restype = ctypes.c_char_p
         lib.qla_batch_destroy.argtypes = [c_vp]
         lib.qla_batch_destroy.restype = None
+        lib.surr_workspace_bytes.argtypes = [c_int, c_int, c_int]
+        lib.surr_workspace_bytes.restype = c_sz
+        lib.surr_create.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, c_int, ctypes.c_ulonglong,
+                                    c_vp, c_vp, c_sz]
+        lib.surr_create.restype = c_int
+        lib.surr_param_count.argtypes = [c_vp]
+        lib.surr_param_count.restype = c_ll
+        for name, args in (("surr_get_params", [c_vp, c_vp]),
+                           ("surr_set_params", [c_vp, c_vp]),
+                           ("surr_forward", [c_vp, c_vp, c_int, c_vp]),
+                           ("surr_loss_grad", [c_vp, c_vp, c_vp, c_int, c_vp, c_vp]),
+                           ("surr_train_step", [c_vp, c_vp, c_vp, c_int, ctypes.c_float, c_vp]),
+                           ("surr_features", [c_vp, c_vp]),
+                           ("surr_advance", [c_vp, c_vp, c_int, c_int, ctypes.c_double,
+                                             ctypes.c_double, c_vp, c_vp, c_vp]),
+                           ("surr_conv3x3_raw", [c_vp, c_int, c_int, c_int, c_int, c_vp, c_int,
+                                                 c_vp, c_vp]),
+                           ("surr_weight_grad_raw", [c_vp, c_vp, c_int, c_int, c_int, c_int, c_int,
+                                                     c_int, c_vp, c_vp, c_vp])):
+            getattr(lib, name).argtypes = args
+            getattr(lib, name).restype = c_int
+        lib.surr_last_error.argtypes = [c_vp]
+        lib.surr_last_error.restype = ctypes.c_char_p
+        lib.surr_destroy.argtypes = [c_vp]
+        lib.surr_destroy.restype = None
         lib.qla_launch_count.argtypes = [c_vp]
         lib.qla_launch_count.restype = c_ll
         lib.qla_last_error.argtypes = [c_vp]
