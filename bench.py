@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--rows", type=int, default=0, help="marching kernel tuning")
     ap.add_argument("--six-planes", action="store_true",
                     help="evolve all six amplitudes instead of the E_z triple")
+    ap.add_argument("--surr-windows", type=int, default=20000)
+    ap.add_argument("--surr-train-steps", type=int, default=16000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -469,8 +471,100 @@ def batch_arm(args):
     return 0
 
 
+def surrogate_arm(args):
+    """Learned surrogate on 256^2 lattices: train on windows from the
+    library's own runs, then advance 64 chained windows of K = 32 steps on
+    held-out lattices with the energy / div B checks and QLA fallback, and
+    compare time and final state with plain GPU QLA (the judge)."""
+    import numpy as np
+    import torch
+
+    from paper_2604_21128_gb300 import build as qbuild
+    from paper_2604_21128_gb300 import inputs, qla
+    from paper_2604_21128_gb300 import surrogate as S
+
+    torch.cuda.set_device(0)
+    qbuild.build()
+    size, K, windows = 256, 32, 64
+    t0 = time.perf_counter()
+    X, T = S.make_windows(args.surr_windows, size=size, K=K, seed=5, instances=64,
+                          restart_every=16)
+    t_gen = time.perf_counter() - t0
+    net = S.Surrogate(size, size, max_batch=8, seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = S.train(net, X, T, steps=args.surr_train_steps, batch=8, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    target_var = float(T.pow(2).mean())
+    del X, T
+    rng = np.random.default_rng(20261203)
+    rows = []
+    for inst in range(4):
+        med, pk = inputs.surrogate_instance(rng, size)
+        n = inputs.ellipse_medium(size, size, 1.0, **med)
+        with qla.Grid(size, size, 1.0, "fp32", te_only=True) as g:
+            g.set_medium(n)
+            g.set_packet(**pk)
+            g.step(K)   # warm the kernels
+            g.set_packet(**pk)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.step(windows * K)
+            g.energy()
+            t_qla = time.perf_counter() - t0
+            ref = g.get_state()
+        with qla.Grid(size, size, 1.0, "fp32", te_only=True) as g:
+            # the network alone over one window, against QLA and against
+            # the zero-change predictor (the state left as it was)
+            g.set_medium(n)
+            g.set_packet(**pk)
+            f0 = S.features(g).unsqueeze(0).contiguous()
+            y = net.forward(f0)[0]
+            g.step(K)
+            d = S.features(g)[..., :3] - f0[0, ..., :3]
+            one = float((y - d).norm() / (f0[0, ..., :3] + d).norm())
+            zero = float(d.norm() / (f0[0, ..., :3] + d).norm())
+        for name, etol, dtol in (("checked", 2e-3, 3e-2), ("unchecked", 1e30, 1e30)):
+            with qla.Grid(size, size, 1.0, "fp32", te_only=True) as g:
+                g.set_medium(n)
+                g.set_packet(**pk)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                acc, _ = net.advance(g, windows, K, etol, dtol)
+                torch.cuda.synchronize()
+                t_s = time.perf_counter() - t0
+                got = g.get_state()
+            err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            rows.append(dict(instance=inst, mode=name, accepted=acc, rel_l2=err,
+                             one_window_rel_l2=one, zero_predictor_rel_l2=zero,
+                             t_qla_ms=1e3 * t_qla, t_surr_ms=1e3 * t_s, speedup=t_qla / t_s))
+    checked = [r for r in rows if r["mode"] == "checked"]
+    unchecked = [r for r in rows if r["mode"] == "unchecked"]
+    line = {
+        "metric": "surrogate speedup over plain GPU QLA at <=1e-2 relative L2 error",
+        "value": float(np.mean([r["speedup"] for r in checked])), "unit": "x",
+        "n_gpus": 1, "steps": windows, "warmup": 1, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32", "data": "synthetic",
+        "config": {"workload": "surrogate_256_K32_64_windows", "train_windows": args.surr_windows,
+                   "train_steps": args.surr_train_steps, "train_s": t_train, "gen_s": t_gen,
+                   "final_loss_over_target_var": float(np.mean(losses[-100:]) / target_var),
+                   "checks": "energy 2e-3, div B 3e-2"},
+        "checked": {"rel_l2": float(np.max([r["rel_l2"] for r in checked])),
+                    "accepted_windows": int(sum(r["accepted"] for r in checked)),
+                    "of_windows": windows * len(checked)},
+        "unchecked": {"rel_l2": float(np.max([r["rel_l2"] for r in unchecked])),
+                      "speedup": float(np.mean([r["speedup"] for r in unchecked]))},
+        "rows": rows,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "surrogate256":
+        return surrogate_arm(args)
     if args.impl == "reference":
         return reference_arm(args)
     if args.workload == "batch256":

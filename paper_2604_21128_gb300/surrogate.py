@@ -150,15 +150,18 @@ def make_windows(count, size=256, K=32, seed=5, instances=32, restart_every=16, 
     return X, T
 
 
-def train(net, X, T, steps, batch=8, lr=1e-3, lr_min=1e-5, seed=0, log_every=0):
-    """Adam with a cosine learning-rate schedule over ``steps`` minibatches
-    drawn (seeded) from the windows X, T; returns the losses."""
+def train(net, X, T, steps, batch=8, lr=1e-3, lr_min=1e-5, warmup=300, seed=0, log_every=0):
+    """Adam over ``steps`` minibatches drawn (seeded) from the windows X, T:
+    the rate rises linearly over the first ``warmup`` steps (without it this
+    normalisation-free U-Net diverges at rates above ~1e-3), then follows a
+    cosine schedule from ``lr`` to ``lr_min``.  Returns the losses."""
     rng = np.random.default_rng(seed)
     n = X.shape[0]
     losses = []
     for s in range(int(steps)):
         i = int(rng.integers(0, n - batch + 1))
         rate = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * s / max(1, steps)))
+        rate *= min(1.0, (s + 1) / max(1, warmup))
         losses.append(net.train_step(X[i:i + batch], T[i:i + batch], rate))
         if log_every and s % log_every == 0:
             print("step %d loss %.4e lr %.2e" % (s, losses[-1], rate), flush=True)

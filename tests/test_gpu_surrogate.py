@@ -157,3 +157,46 @@ def test_advance_rejecting_every_window_is_plain_qla():
     assert acc == 0
     assert np.array_equal(got, want)
     assert e[-1] == e_ref
+
+
+def test_trained_network_beats_the_zero_change_predictor_and_checks_hold():
+    """What training buys: over one K-step window on held-out lattices the
+    trained network's error is a small fraction of the error of leaving the
+    state unchanged (the best a method without the network can do without
+    running QLA).  With the energy / div B checks on, chained windows end
+    within the check-controlled error of plain QLA."""
+    import torch
+    size, K = 128, 16
+    X, T = S.make_windows(1024, size=size, K=K, seed=21, instances=64, restart_every=8)
+    net = S.Surrogate(size, size, max_batch=8, seed=4)
+    losses = S.train(net, X, T, steps=1500, batch=8, lr=1e-3)
+    var = float(T.pow(2).mean())
+    del X, T
+    print("loss / target variance: %.3e" % (np.mean(losses[-50:]) / var))
+    rng = np.random.default_rng(77)
+    for _ in range(2):
+        med, pk = inputs.surrogate_instance(rng, size)
+        n = inputs.ellipse_medium(size, size, 1.0, **med)
+        with qla.Grid(size, size, 1.0, "fp32", te_only=True) as g:
+            g.set_medium(n)
+            g.set_packet(**pk)
+            f0 = S.features(g).unsqueeze(0).contiguous()
+            y = net.forward(f0)[0]
+            g.step(K)
+            d = S.features(g)[..., :3] - f0[0, ..., :3]
+            state = (f0[0, ..., :3] + d).norm()
+            e_net, e_zero = float((y - d).norm() / state), float(d.norm() / state)
+            g.set_packet(**pk)
+            g.step(8 * K)
+            ref = g.get_state()
+        with qla.Grid(size, size, 1.0, "fp32", te_only=True) as g:
+            g.set_medium(n)
+            g.set_packet(**pk)
+            acc, _ = net.advance(g, 8, K, 2e-3, 3e-2)
+            got = g.get_state()
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        print("one window: network %.3e, zero change %.3e; 8 checked windows: %d accepted, "
+              "rel L2 %.3e" % (e_net, e_zero, acc, err))
+        assert e_net < 0.25 * e_zero
+        assert err <= 0.25
+        torch.cuda.synchronize()
