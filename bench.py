@@ -69,6 +69,55 @@ def peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+# Arithmetic roofline of the step kernel.  Per site-update the method needs
+# 16 collision rotations (8 layers of U_x, 8 of U_y) and 2 potential
+# rotations on each live pair (1 pair in E_z mode, 2 with six planes).  FP32:
+# a collision rotation with two-word coefficients is 8 FP32 instructions
+# (4 per output), a potential rotation 6; FP64: 4 per rotation either way.
+# Peaks from the unit counts and the maximum clock: 152 SMs x 128 FP32 lanes
+# x 2.07 GHz for FP32 instructions; the nominal 1.25 TFLOP/s FP64 rate
+# counted as FMA-class instructions (2 flops each) for FP64.
+FP32_INST_PEAK = 152 * 128 * 2.07e9
+FP64_INST_PEAK = 1.25e12 / 2
+
+
+def alu_ops_per_su(P, elt):
+    pairs = 1 if P == 3 else 2
+    if elt == 4:
+        return pairs * (16 * 8 + 2 * 6)
+    return pairs * (16 * 4 + 2 * 4)
+
+
+def roofline(P, elt, su_per_s, traffic, **extra):
+    """Roofline object for a step kernel that advances ``su_per_s`` site-updates
+    per second of its own run time.  The bound is the roof with the lower
+    ceiling in site-updates/s (HBM for FP32, the FP64 pipe for FP64); the
+    other roof's figures ride along under its name."""
+    ops = alu_ops_per_su(P, elt)
+    peak_ops = FP32_INST_PEAK if elt == 4 else FP64_INST_PEAK
+    hbm_peak, hbm_kind = peaks()
+    bytes_su = 2 * P * elt
+    hbm = {"achieved": bytes_su * su_per_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+           "frac": bytes_su * su_per_s / 1e9 / hbm_peak, "peak_kind": hbm_kind,
+           "bytes_per_site_update": bytes_su}
+    alu = {"achieved": ops * su_per_s / 1e12, "peak": peak_ops / 1e12,
+           "unit": "T%s-inst/s" % ("FP32" if elt == 4 else "FP64"),
+           "frac": ops * su_per_s / peak_ops,
+           "peak_kind": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2.07 GHz" if elt == 4
+                                         else "nominal 1.25 TFLOP/s FP64 / 2 flops per FMA"),
+           "ops_per_site_update": ops}
+    ceil = {"hbm": hbm_peak * 1e9 / bytes_su, "alu": peak_ops / ops}
+    bound = "hbm" if ceil["hbm"] <= ceil["alu"] else "alu"
+    other = "alu" if bound == "hbm" else "hbm"
+    r = {"bound": bound}
+    r.update(hbm if bound == "hbm" else alu)
+    r["traffic"] = traffic
+    r["ceilings_site_updates_per_s"] = ceil
+    r[other] = alu if other == "alu" else hbm
+    r.update(extra)
+    return r
+
+
 # ---------------------------------------------------------------------------
 # Clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -228,12 +277,14 @@ def kernel_traffic(k, sites):
             rec = json.load(f)
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_2604_21128_gb300", "csrc", rec["source"])
+    h = hashlib.sha256()
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
+        for name in rec["sources"]:
+            h.update(open(os.path.join(ROOT, "paper_2604_21128_gb300", "csrc", name), "rb").read())
+    except (OSError, KeyError):
         return None
-    if sha != rec.get("source_sha256") or rec.get("time_block") != k:
+    sha = h.hexdigest()
+    if sha != rec.get("sources_sha256") or rec.get("time_block") != k:
         return None
     return rec["dram_bytes_per_site_step"] * sites * k
 
@@ -304,14 +355,12 @@ def gpu_arm(args):
     value = su_total / elapsed
     drift = energies[-1] / e0 - 1 if e0 else float("nan")
 
-    # roofline of the dominant (step) kernel: algorithmic bytes per launch =
-    # 2 * P * element bytes per site-update x sites x steps per launch
+    # roofline of the dominant (step) kernel: algorithmic work per launch =
+    # per-site-update figure x sites x steps per launch, over the launch's
+    # mean duration (CUDA events on the launching stream)
     k_used = S * args.steps / max(step_launches, 1)
-    bytes_per_su = 2 * P * elt
     per_launch_s = step_time / max(step_launches, 1)
-    alg_bytes = bytes_per_su * sites * k_used
-    peak, peak_kind = peaks()
-    achieved = alg_bytes / per_launch_s / 1e9
+    kernel_su_per_s = sites * k_used / per_launch_s
     traffic = kernel_traffic(int(round(k_used)), sites)
     g.close()
 
@@ -321,7 +370,7 @@ def gpu_arm(args):
 
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
-        side, nst = 2048, 6
+        side, nst = 4096, 15
         v, dt, threads = oracle_sample(w, n_host.numpy(), side, nst)
         cpu = {"value": v, "unit": "site-updates/s", "cores": threads, "kind": "oracle",
                "sample": "%d x %d crop of the %s workload, %d steps (%.1f s), plain FP64 "
@@ -342,11 +391,8 @@ def gpu_arm(args):
                        "lane_cols": args.lane_cols or "auto", "rows": args.rows or "auto",
                        "energy_drift": drift,
                        "l2": "state %.0f MB > 129 MB L2, no flush" % (2 * P * elt * sites / 2e6)},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_kind": peak_kind,
-                         "bytes_per_site_update": bytes_per_su,
-                         "kernel_ms": 1e3 * per_launch_s},
+            "roofline": roofline(P, elt, kernel_su_per_s, traffic,
+                                 kernel_ms=1e3 * per_launch_s),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -440,9 +486,8 @@ def batch_arm(args):
     launches = b.launches - l0
     b.close()
     value = world * args.steps * S * sites / elapsed
-    peak, peak_kind = peaks()
-    bytes_per_su = 2 * 3 * (4 if args.precision == "fp32" else 8)
-    achieved = bytes_per_su * value / world / 1e9
+    elt = 4 if args.precision == "fp32" else 8
+    bytes_per_su = 2 * 3 * elt
     if rank == 0:
         drift = float(np.max(np.abs(energies[-1] / energies[0] - 1)))
         print(json.dumps({
@@ -459,10 +504,8 @@ def batch_arm(args):
                                  "captured as one CUDA graph",
                        "max_energy_drift": drift,
                        "l2": "state %.1f GB > 129 MB L2, no flush" % (bytes_per_su * sites / 1e9)},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "bytes_per_site_update": bytes_per_su,
-                         "note": "whole-run average (step kernels and energies)"},
+            "roofline": roofline(3, elt, value / world, None,
+                                 note="whole-run average (step kernels and energies)"),
             "cpu_baseline": None,
             "e2e": {"value": world * args.steps * S * sites / wall, "unit": "site-updates/s",
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8 * len(ws),
