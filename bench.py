@@ -39,7 +39,6 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--workload", default="ellipse_8192")
     ap.add_argument("--qla-steps", type=int, default=100)
-    ap.add_argument("--time-block", type=int, default=0)
     ap.add_argument("--lane-cols", type=int, default=0, help="marching kernel tuning")
     ap.add_argument("--rows", type=int, default=0, help="marching kernel tuning")
     ap.add_argument("--six-planes", action="store_true",
@@ -312,8 +311,6 @@ def gpu_arm(args):
 
     stream = torch.cuda.Stream(dev)
     g = qla.Grid(w.nx, w.ny, w.delta, args.precision, te_only=te, stream=stream)
-    if args.time_block:
-        g.set_time_block(args.time_block)
     g.set_march_tuning(args.lane_cols, args.rows)
     g.set_medium(n_host)
     g.set_packet(**pk)
@@ -414,8 +411,6 @@ def e2e_run(args, w, te, n_host, pk, world, dev):
     stream = torch.cuda.Stream(dev)
     ez = torch.empty((w.ny, w.nx), dtype=torch.float64).pin_memory()
     g = qla.Grid(w.nx, w.ny, w.delta, args.precision, te_only=te, stream=stream)
-    if args.time_block:
-        g.set_time_block(args.time_block)
     g.set_march_tuning(args.lane_cols, args.rows)
     S = args.qla_steps
     barrier(world)

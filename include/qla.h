@@ -142,12 +142,6 @@ qla_status qla_fields(qla_ctx *ctx, double *Ex, double *Ey, double *Ez,
  * index out of range or count outside 0..65536. */
 qla_status qla_probe(qla_ctx *ctx, int count, const int *i, const int *j, double *out);
 
-/* Number of time steps the library fuses into one kernel launch (temporal
- * blocking), 1..QLA_MAX_TIME_BLOCK; 0 restores the library's choice.
- * Results do not depend on it beyond FP rounding order (FP64: not at all). */
-#define QLA_MAX_TIME_BLOCK 8
-qla_status qla_set_time_block(qla_ctx *ctx, int k);
-
 /* Step kernel.  QLA_KERNEL_AUTO picks the register-resident marching
  * kernel when nx is a multiple of its per-lane column count (2 by default;
  * see qla_set_march_tuning), nx >= 32 times that count and ny >= 8, and the

@@ -361,16 +361,6 @@ qla_status qla_probe(qla_ctx *c, int count, const int *i, const int *j, double *
     return QLA_OK;
 }
 
-qla_status qla_set_time_block(qla_ctx *c, int k) {
-    qla_status s = usable(c);
-    if (s != QLA_OK) return s;
-    if (k < 0 || k > QLA_MAX_TIME_BLOCK)
-        return fail(c, QLA_EINVAL, "qla_set_time_block: k = %d outside 0..%d", k,
-                    QLA_MAX_TIME_BLOCK);
-    c->time_block = k;
-    return QLA_OK;
-}
-
 qla_status qla_set_step_kernel(qla_ctx *c, int kernel) {
     qla_status s = usable(c);
     if (s != QLA_OK) return s;

@@ -206,7 +206,6 @@ struct qla_ctx {
     // it (the step kernels apply that V to their input; read-outs apply it
     // on the fly with the same device code).
     bool pending_v = false;
-    int time_block = 0;
     int step_kernel = 0;            // qla_step_kernel
     long long launches = 0;
     qla_status sticky = QLA_OK;

@@ -22,7 +22,6 @@ QLA_FP64, QLA_FP32 = 0, 1
 QLA_TE_ONLY = 1
 QLA_POTENTIAL_LITERAL = 2
 QLA_POTENTIAL_NONE = 4
-QLA_MAX_TIME_BLOCK = 8
 QLA_KERNEL_AUTO, QLA_KERNEL_TILE, QLA_KERNEL_MARCH = 0, 1, 2
 
 STATUS = {0: "QLA_OK", 1: "QLA_EINVAL", 2: "QLA_ESTATE", 3: "QLA_ENOMEM",
@@ -65,7 +64,6 @@ def load():
                            ("qla_step", [c_vp, c_ll]),
                            ("qla_energy", [c_vp, _DP]),
                            ("qla_fields", [c_vp] + [c_vp] * 6),
-                           ("qla_set_time_block", [c_vp, c_int]),
                            ("qla_probe", [c_vp, c_int, c_vp, c_vp, c_vp]),
                            ("qla_set_step_kernel", [c_vp, c_int]),
                            ("qla_set_march_tuning", [c_vp, c_int, c_int])):
@@ -216,8 +214,6 @@ def qla_probe(ctx, i, j):
     return out
 
 
-def qla_set_time_block(ctx, k):
-    _check(ctx, load().qla_set_time_block(ctx, int(k)))
 
 
 def qla_set_step_kernel(ctx, kernel):
@@ -324,8 +320,6 @@ class Grid:
     def set_march_tuning(self, lane_cols=0, rows=0):
         qla_set_march_tuning(self._ctx, lane_cols, rows)
 
-    def set_time_block(self, k):
-        qla_set_time_block(self._ctx, k)
 
     @property
     def launches(self):

@@ -30,13 +30,11 @@ def rel_l2(a, b):
 
 
 def gpu_run(n, delta, steps, q0=None, packet=None, precision="fp64", te=False,
-            potential="rotation", time_block=0, kernel="auto", lane_cols=0, rows=0):
+            potential="rotation", kernel="auto", lane_cols=0, rows=0):
     ny, nx = n.shape
     with qla.Grid(nx, ny, delta, precision, te_only=te, potential=potential) as g:
         g.set_step_kernel(kernel)
         g.set_march_tuning(lane_cols, rows)
-        if time_block:
-            g.set_time_block(time_block)
         g.set_medium(n)
         if q0 is not None:
             g.set_state(q0)
