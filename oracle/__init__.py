@@ -55,6 +55,7 @@ def _load():
         lib.orc_energy.argtypes = [i, i, dp]
         lib.orc_energy.restype = d
         lib.orc_fields.argtypes = [i, i, dp, dp, dp]
+        lib.orc_divergence.argtypes = [i, i, d, dp, dp, dp]
         lib.orc_packet.argtypes = [i, i, d, i, i, i, i, dp, d, d, d, d, d, d, d, dp]
         lib.orc_set_threads.argtypes = [i]
         lib.orc_get_threads.restype = i
@@ -164,6 +165,20 @@ def fields(q, n):
     out = np.empty_like(q)
     _load().orc_fields(nx, ny, _ptr(n), _ptr(q), _ptr(out))
     return out
+
+
+def divergence(q, n, delta):
+    """Gauss-law monitors (Eqs. 3.1, 3.2) with centred periodic differences:
+    dict with div_b_sq = sum (div B)^2, grad_b_sq = sum (d_x B_x)^2 +
+    (d_y B_y)^2, div_d_sq, grad_d_sq (the same for D = (n q0, n q1)),
+    div_b_max, div_d_max."""
+    q = _state(q)
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    ny, nx = q.shape[1:]
+    out = np.empty(6)
+    _load().orc_divergence(nx, ny, float(delta), _ptr(n), _ptr(q), _ptr(out))
+    keys = ("div_b_sq", "grad_b_sq", "div_d_sq", "grad_d_sq", "div_b_max", "div_d_max")
+    return dict(zip(keys, (float(v) for v in out)))
 
 
 def packet(n, delta, x0, y0, angle, k0, width, transverse_width=0.0,

@@ -332,6 +332,50 @@ void orc_fields(int nx, int ny, const double *n, const double *q, double *out)
     }
 }
 
+/* Gauss laws, Eqs. 3.1 and 3.2, on the lattice.  Fields vary in x and y
+ * only, so div B = d_x B_x + d_y B_y and div D = d_x D_x + d_y D_y with
+ * B = (q3, q4) and D = eps E = n^2 E, i.e. D_x = n q0, D_y = n q1 (Dyson
+ * variables, Eq. 3b3, c = 1).  The paper does not state the discrete
+ * derivative; it is read as the centred periodic difference
+ * (f[i+1] - f[i-1]) / (2 delta), the same one the potential angles use.
+ * out[0] = sum (div B)^2, out[1] = sum (d_x B_x)^2 + (d_y B_y)^2 (the scale
+ * div B is measured against), out[2] = sum (div D)^2, out[3] the same scale
+ * for D, out[4] = max |div B|, out[5] = max |div D|. */
+void orc_divergence(int nx, int ny, double delta, const double *n, const double *q,
+                    double *out)
+{
+    size_t N = (size_t)nx * ny;
+    const double *q0 = q, *q1 = q + N, *q3 = q + 3 * N, *q4 = q + 4 * N;
+    double sb = 0.0, gb = 0.0, sd = 0.0, gd = 0.0, mb = 0.0, md = 0.0;
+    const double h = 0.5 / delta;
+    for (int j = 0; j < ny; ++j) {
+        const int jp = (j + 1) % ny, jm = (j + ny - 1) % ny;
+        for (int i = 0; i < nx; ++i) {
+            const int ip = (i + 1) % nx, im = (i + nx - 1) % nx;
+            const size_t k = (size_t)j * nx + i;
+            const size_t kxp = (size_t)j * nx + ip, kxm = (size_t)j * nx + im;
+            const size_t kyp = (size_t)jp * nx + i, kym = (size_t)jm * nx + i;
+            const double dbx = h * (q3[kxp] - q3[kxm]);
+            const double dby = h * (q4[kyp] - q4[kym]);
+            const double ddx = h * (n[kxp] * q0[kxp] - n[kxm] * q0[kxm]);
+            const double ddy = h * (n[kyp] * q1[kyp] - n[kym] * q1[kym]);
+            const double db = dbx + dby, dd = ddx + ddy;
+            sb += db * db;
+            gb += dbx * dbx + dby * dby;
+            sd += dd * dd;
+            gd += ddx * ddx + ddy * ddy;
+            if (fabs(db) > mb) mb = fabs(db);
+            if (fabs(dd) > md) md = fabs(dd);
+        }
+    }
+    out[0] = sb;
+    out[1] = gb;
+    out[2] = sd;
+    out[3] = gd;
+    out[4] = mb;
+    out[5] = md;
+}
+
 /* Minimum-image offset of coordinate x from x0 on a period L, in [-L/2, L/2). */
 static double min_image(double x, double x0, double L)
 {

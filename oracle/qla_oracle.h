@@ -32,6 +32,8 @@ int orc_run(int nx, int ny, double delta, const double *n, double *q,
             long long steps, int vmode);
 double orc_energy(int nx, int ny, const double *q);
 void orc_fields(int nx, int ny, const double *n, const double *q, double *out);
+void orc_divergence(int nx, int ny, double delta, const double *n, const double *q,
+                    double *out);
 void orc_packet(int nx, int ny, double delta, int i0, int j0, int nwx,
                 int nwy, const double *n_win, double x0, double y0,
                 double phi, double k0, double w, double wt, double amp,
