@@ -136,6 +136,21 @@ qla_status qla_energy(qla_ctx *ctx, double *out);
 qla_status qla_fields(qla_ctx *ctx, double *Ex, double *Ey, double *Ez,
                       double *Bx, double *By, double *Bz);
 
+/* Gauss-law monitors (Eqs. 3.1 and 3.2, which the paper tracks alongside the
+ * energy).  Fields vary in x and y only, so div B = d_x B_x + d_y B_y with
+ * B = (q3, q4), and div D = d_x D_x + d_y D_y with D = n^2 E = (n q0, n q1)
+ * (Eq. 3b3, c = 1).  d_x f = (f[i+1] - f[i-1]) / (2 delta), periodic (the
+ * paper does not state the discrete derivative).  The state is read with the
+ * pending potential step applied, like every read-out.  out[6] (host):
+ *   out[0] = sum (div B)^2        out[1] = sum (d_x B_x)^2 + (d_y B_y)^2
+ *   out[2] = sum (div D)^2        out[3] = sum (d_x D_x)^2 + (d_y D_y)^2
+ *   out[4] = max |div B|          out[5] = max |div D|
+ * sqrt(out[0] / out[1]) is the relative divergence; a QLA_TE_ONLY context
+ * has no in-plane D (out[2] = out[3] = out[5] = 0).  FP64 accumulation.
+ * Synchronises.  QLA_ESTATE without medium and state, QLA_ENONFINITE if a
+ * term is not finite. */
+qla_status qla_divergence(qla_ctx *ctx, double *out);
+
 /* Read the six amplitudes q0..q5 at `count` sites (i[k], j[k]), each
  * 0 <= i < nx, 0 <= j < ny, into out[6*k + c] (FP64; zeros for planes a
  * QLA_TE_ONLY context does not evolve).  Synchronises.  QLA_EINVAL for an

@@ -37,8 +37,9 @@ Layout layout_for(int nx, int ny, int prec, unsigned flags) {
     L.counter = off;  off += align256(4);
     L.n = off;        off += align256(L.plane_elems * 8);
     L.staging = off;  off += align256(sites * 8);
-    L.partials = off; off += align256(nb * 8);
-    L.result = off;   off += align256(8);
+    // partials: up to DIV_TERMS doubles per block (energy uses one)
+    L.partials = off; off += align256(nb * 8 * DIV_TERMS);
+    L.result = off;   off += align256(8 * DIV_TERMS);
     L.total = off;
     return L;
 }
@@ -303,6 +304,24 @@ qla_status qla_energy(qla_ctx *c, double *out) {
              "qla_energy: copy");
     QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_energy: sync");
     if (!std::isfinite(*out)) return fail(c, QLA_ENONFINITE, "qla_energy: energy is %g", *out);
+    return QLA_OK;
+}
+
+qla_status qla_divergence(qla_ctx *c, double *out) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (!out) return fail(c, QLA_EINVAL, "qla_divergence: null output");
+    if (!c->has_state || !c->has_medium)
+        return fail(c, QLA_ESTATE, "qla_divergence: needs medium and state");
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, QLA_ECUDA, "qla_divergence: cannot select device");
+    QLA_CUDA(c, launch_divergence(c), "qla_divergence: kernel");
+    QLA_CUDA(c, cudaMemcpyAsync(out, c->result, 8 * DIV_TERMS, cudaMemcpyDeviceToHost, c->stream),
+             "qla_divergence: copy");
+    QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_divergence: sync");
+    for (int k = 0; k < DIV_TERMS; ++k)
+        if (!std::isfinite(out[k]))
+            return fail(c, QLA_ENONFINITE, "qla_divergence: term %d is %g", k, out[k]);
     return QLA_OK;
 }
 

@@ -218,6 +218,7 @@ __device__ __forceinline__ double block_sum(double v) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     }
+    __syncthreads();  // warp_part is reused by the next call
     return v;  // valid in thread 0
 }
 
@@ -251,6 +252,78 @@ k_energy_final(const double *__restrict__ partials, int count, double *__restric
     for (int t = threadIdx.x; t < count; t += AUX_THREADS) acc += partials[t];
     acc = block_sum(acc);
     if (threadIdx.x == 0) *out = acc;
+}
+
+__device__ double block_max(double v) {
+    __shared__ double warp_part[AUX_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    if (lane == 0) warp_part[w] = v;
+    __syncthreads();
+    v = 0.0;
+    if (w == 0) {
+        v = lane < AUX_THREADS / 32 ? warp_part[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    }
+    __syncthreads();
+    return v;  // valid in thread 0
+}
+
+// Gauss laws (Eqs. 3.1, 3.2) with centred periodic differences: fields vary
+// in x and y only, B = (q3, q4), D = n^2 E = (n q0, n q1) (Dyson variables,
+// c = 1).  Each site reads its four neighbours' amplitudes (the pending
+// potential step applied) and medium.
+template <typename T, int P, int VM>
+__global__ void __launch_bounds__(AUX_THREADS)
+k_div_partial(const T *__restrict__ q, const double *__restrict__ n, int nx, int ny, int pitch,
+              size_t plane_elems, double inv2d, double *__restrict__ partials, bool vin,
+              const uint32_t *__restrict__ midx, const MedRec<T> *__restrict__ table) {
+    const size_t N = size_t(nx) * ny;
+    double sb = 0.0, gb = 0.0, sd = 0.0, gd = 0.0, mb = 0.0, md = 0.0;
+    for (size_t t = blockIdx.x * size_t(AUX_THREADS) + threadIdx.x; t < N;
+         t += size_t(gridDim.x) * AUX_THREADS) {
+        const int j = int(t / nx), i = int(t - size_t(j) * nx);
+        const size_t gxp = size_t(j) * pitch + wrap(i + 1, nx);
+        const size_t gxm = size_t(j) * pitch + wrap(i - 1, nx);
+        const size_t gyp = size_t(wrap(j + 1, ny)) * pitch + i;
+        const size_t gym = size_t(wrap(j - 1, ny)) * pitch + i;
+        T a[6], b[6], c[6], d[6];
+        load_site<T, P, VM>(q, plane_elems, gxp, vin, midx, table, a);
+        load_site<T, P, VM>(q, plane_elems, gxm, vin, midx, table, b);
+        load_site<T, P, VM>(q, plane_elems, gyp, vin, midx, table, c);
+        load_site<T, P, VM>(q, plane_elems, gym, vin, midx, table, d);
+        const double dbx = inv2d * (double(a[3]) - double(b[3]));
+        const double dby = inv2d * (double(c[4]) - double(d[4]));
+        const double ddx = inv2d * (n[gxp] * double(a[0]) - n[gxm] * double(b[0]));
+        const double ddy = inv2d * (n[gyp] * double(c[1]) - n[gym] * double(d[1]));
+        const double db = dbx + dby, dd = ddx + ddy;
+        sb = fma(db, db, sb);
+        gb = fma(dbx, dbx, fma(dby, dby, gb));
+        sd = fma(dd, dd, sd);
+        gd = fma(ddx, ddx, fma(ddy, ddy, gd));
+        mb = fmax(mb, fabs(db));
+        md = fmax(md, fabs(dd));
+    }
+    const double r[DIV_TERMS] = {block_sum(sb), block_sum(gb), block_sum(sd), block_sum(gd),
+                                 block_max(mb), block_max(md)};
+    if (threadIdx.x == 0)
+        for (int k = 0; k < DIV_TERMS; ++k) partials[size_t(blockIdx.x) * DIV_TERMS + k] = r[k];
+}
+
+__global__ void __launch_bounds__(AUX_THREADS)
+k_div_final(const double *__restrict__ partials, int count, double *__restrict__ out) {
+    double v[DIV_TERMS] = {0, 0, 0, 0, 0, 0};
+    for (int t = threadIdx.x; t < count; t += AUX_THREADS)
+        for (int k = 0; k < DIV_TERMS; ++k) {
+            const double p = partials[size_t(t) * DIV_TERMS + k];
+            v[k] = k < 4 ? v[k] + p : fmax(v[k], p);
+        }
+    double r[DIV_TERMS];
+    for (int k = 0; k < DIV_TERMS; ++k) r[k] = k < 4 ? block_sum(v[k]) : block_max(v[k]);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < DIV_TERMS; ++k) out[k] = r[k];
 }
 
 // Gather q at listed sites: ij holds i[0..count) then j[0..count).
@@ -382,6 +455,34 @@ cudaError_t launch_fields(qla_ctx *c, int comp, double *dst) {
 
 cudaError_t launch_probe(qla_ctx *c, int count, const int *ij_dev, double *out_dev) {
     return readout(c, 2, 0, nullptr, out_dev, count, ij_dev);
+}
+
+template <typename T, int P, int VM>
+static cudaError_t divergence_t(qla_ctx *c) {
+    k_div_partial<T, P, VM><<<c->energy_blocks, AUX_THREADS, 0, c->stream>>>(
+        static_cast<const T *>(c->state[c->cur]), c->n, c->nx, c->ny, c->pitch, c->plane_elems,
+        0.5 / c->delta, c->partials, c->pending_v, c->midx,
+        static_cast<const MedRec<T> *>(c->table));
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_div_final<<<1, AUX_THREADS, 0, c->stream>>>(c->partials, c->energy_blocks, c->result);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+template <typename T, int P>
+static cudaError_t divergence_p(qla_ctx *c) {
+    switch (c->vmode) {
+    case V_ROTATION: return divergence_t<T, P, V_ROTATION>(c);
+    case V_LITERAL:  return divergence_t<T, P, V_LITERAL>(c);
+    default:         return divergence_t<T, P, V_NONE>(c);
+    }
+}
+
+cudaError_t launch_divergence(qla_ctx *c) {
+    if (c->prec == QLA_FP64) return c->P == 6 ? divergence_p<double, 6>(c) : divergence_p<double, 3>(c);
+    return c->P == 6 ? divergence_p<float, 6>(c) : divergence_p<float, 3>(c);
 }
 
 cudaError_t launch_energy(qla_ctx *c) {

@@ -228,6 +228,10 @@ cudaError_t launch_from_f64(qla_ctx *c, int plane, const double *src);
 cudaError_t launch_to_f64(qla_ctx *c, int comp, double *dst);
 cudaError_t launch_fields(qla_ctx *c, int comp, double *dst);
 cudaError_t launch_energy(qla_ctx *c);
+// Gauss-law monitors (Eqs. 3.1, 3.2): sums of (div B)^2, (d_x B_x)^2 +
+// (d_y B_y)^2, (div D)^2, the D scale, then max |div B|, max |div D|.
+constexpr int DIV_TERMS = 6;
+cudaError_t launch_divergence(qla_ctx *c);
 cudaError_t launch_probe(qla_ctx *c, int count, const int *ij_dev, double *out_dev);
 cudaError_t launch_step_tile(qla_ctx *c, const void *in, void *out, bool vin);
 cudaError_t launch_step_march(qla_ctx *c, const void *in, void *out, bool vin);

@@ -63,6 +63,7 @@ def load():
                            ("qla_get_state", [c_vp, c_vp]),
                            ("qla_step", [c_vp, c_ll]),
                            ("qla_energy", [c_vp, _DP]),
+                           ("qla_divergence", [c_vp, c_vp]),
                            ("qla_fields", [c_vp] + [c_vp] * 6),
                            ("qla_probe", [c_vp, c_int, c_vp, c_vp, c_vp]),
                            ("qla_set_step_kernel", [c_vp, c_int]),
@@ -196,6 +197,15 @@ def qla_energy(ctx):
     return v.value
 
 
+DIV_KEYS = ("div_b_sq", "grad_b_sq", "div_d_sq", "grad_d_sq", "div_b_max", "div_d_max")
+
+
+def qla_divergence(ctx):
+    out = np.empty(6)
+    _check(ctx, load().qla_divergence(ctx, ctypes.c_void_p(out.ctypes.data)))
+    return dict(zip(DIV_KEYS, (float(v) for v in out)))
+
+
 def qla_fields(ctx, nx, ny, Ex=None, Ey=None, Ez=None, Bx=None, By=None, Bz=None):
     ptrs = [_host_ptr(a, nx * ny, writable=True) if a is not None else ctypes.c_void_p(0)
             for a in (Ex, Ey, Ez, Bx, By, Bz)]
@@ -301,6 +311,11 @@ class Grid:
     def energy(self):
         with self._dev():
             return qla_energy(self._ctx)
+
+    def divergence(self):
+        """Gauss-law monitors, a dict with the keys of DIV_KEYS."""
+        with self._dev():
+            return qla_divergence(self._ctx)
 
     def fields(self):
         out = {k: np.empty((self.ny, self.nx)) for k in ("Ex", "Ey", "Ez", "Bx", "By", "Bz")}
