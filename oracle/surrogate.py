@@ -96,4 +96,4 @@ def loss_grad(flat, feat, target):
     y = forward_t(unpack(theta), f)
     loss = ((y - t) ** 2).mean()
     loss.backward()
-    return float(loss), theta.grad.numpy().copy()
+    return float(loss.detach()), theta.grad.numpy().copy()

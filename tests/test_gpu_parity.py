@@ -281,3 +281,31 @@ def test_full_size_8192_sampled_sites():
         assert np.max(np.abs(got[k] - want)) <= 2e-5, (ii[k], jj[k], got[k], want)
     assert np.all(got[:, [0, 1, 5]] == 0)
     assert math.isfinite(e) and e > 0
+
+
+def test_full_size_16384_bubble_sampled_sites():
+    """The 16384^2 vacuum-bubble workload (268 M sites, FP32, E_z planes) for
+    16 steps in the default launch configuration; sampled sites in the
+    packet, on the bubble's tanh edge, at random and on the wrap-around
+    rows and columns, against the oracle on a periodic window around each
+    site (exact inside the dependence cone)."""
+    w = inputs.bubble_16384()
+    steps = 16
+    n = w.medium()
+    pk = w.packet.as_dict()
+    rng = np.random.default_rng(16384)
+    x0, xe, yc = int(pk["x0"]), w.nx // 2 - 2400, w.ny // 2
+    ii = np.concatenate([x0 + rng.integers(-900, 900, 6), xe + rng.integers(-12, 12, 6),
+                         rng.integers(0, w.nx, 3), [0, w.nx - 1]])
+    jj = np.concatenate([rng.integers(0, w.ny, 6), yc + rng.integers(-300, 300, 6),
+                         rng.integers(0, w.ny, 3), [w.ny - 1, 0]])
+    with qla.Grid(w.nx, w.ny, w.delta, "fp32", te_only=True) as g:
+        g.set_medium(n)
+        g.set_packet(**pk)
+        g.step(steps)
+        got = g.probe(ii, jj)
+    half = oracle.reach_per_step() * steps + 2
+    for k in range(len(ii)):
+        want = oracle.run_window(n, w.delta, pk, steps, (int(ii[k]), int(jj[k])), half)
+        assert np.max(np.abs(got[k] - want)) <= 2e-5, (ii[k], jj[k], got[k], want)
+    assert np.any(np.abs(got[:6, 2]) > 1e-3)      # the packet is in the sample
