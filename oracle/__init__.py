@@ -56,6 +56,11 @@ def _load():
         lib.orc_energy.restype = d
         lib.orc_fields.argtypes = [i, i, dp, dp, dp]
         lib.orc_divergence.argtypes = [i, i, d, dp, dp, dp]
+        lib.orc_divergence_aniso.argtypes = [i, i, d, dp, dp, dp, dp]
+        lib.orc_fields_aniso.argtypes = [i, i, dp, dp, dp, dp, dp]
+        lib.orc_angles_aniso.argtypes = [i, i, d, dp, dp, dp, dp]
+        lib.orc_run_aniso.argtypes = [i, i, d, dp, dp, dp, dp, ll, i]
+        lib.orc_run_aniso.restype = i
         lib.orc_packet.argtypes = [i, i, d, i, i, i, i, dp, d, d, d, d, d, d, d, dp]
         lib.orc_set_threads.argtypes = [i]
         lib.orc_get_threads.restype = i
@@ -137,17 +142,43 @@ def V(q, beta_x, beta_y, vmode="rotation"):
     return q
 
 
-def run(q, n, delta, steps, vmode="rotation"):
-    """Advance Q by ``steps`` full steps of Eq. 2e14; returns the new state."""
-    q = _state(q).copy()
+def _medium(n, ny, nx):
+    """The medium as (n_x, n_y, n_z) planes: a (ny, nx) array is isotropic,
+    a (3, ny, nx) array holds the diagonal of the index tensor."""
     n = np.ascontiguousarray(n, dtype=np.float64)
+    if n.shape == (ny, nx):
+        return n, n, n
+    if n.shape == (3, ny, nx):
+        return tuple(np.ascontiguousarray(n[c]) for c in range(3))
+    raise ValueError("medium shape mismatch")
+
+
+def run(q, n, delta, steps, vmode="rotation"):
+    """Advance Q by ``steps`` full steps of Eq. 2e14; returns the new state.
+    ``n`` is (ny, nx) (isotropic) or (3, ny, nx) = (n_x, n_y, n_z)."""
+    q = _state(q).copy()
     ny, nx = q.shape[1:]
-    if n.shape != (ny, nx):
-        raise ValueError("medium shape mismatch")
-    rc = _load().orc_run(nx, ny, float(delta), _ptr(n), _ptr(q), int(steps), _vmode(vmode))
+    nxx, nyy, nzz = _medium(n, ny, nx)
+    if nxx is nyy and nyy is nzz:
+        rc = _load().orc_run(nx, ny, float(delta), _ptr(nxx), _ptr(q), int(steps), _vmode(vmode))
+    else:
+        rc = _load().orc_run_aniso(nx, ny, float(delta), _ptr(nxx), _ptr(nyy), _ptr(nzz), _ptr(q),
+                                   int(steps), _vmode(vmode))
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return q
+
+
+def angles_aniso(n, delta):
+    """Per-pair angle planes (8, ny, nx) of a (3, ny, nx) index tensor, in the
+    order theta_1, theta_2 (C_x), theta_0, theta_2 (C_y), beta_0, beta_2
+    (V_x), beta_1, beta_3 (V_y) (Eqs. 2e4, 2e8, 2e13)."""
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    _, ny, nx = n.shape
+    nxx, nyy, nzz = _medium(n, ny, nx)
+    out = np.empty((8, ny, nx))
+    _load().orc_angles_aniso(nx, ny, float(delta), _ptr(nxx), _ptr(nyy), _ptr(nzz), _ptr(out))
+    return out
 
 
 def energy(q):
@@ -158,25 +189,26 @@ def energy(q):
 
 
 def fields(q, n):
-    """(E_x, E_y, E_z, B_x, B_y, B_z) = (q0/n, q1/n, q2/n, q3, q4, q5), Eq. 3b3."""
+    """(E_x, E_y, E_z, B_x, B_y, B_z) = (q0/n_x, q1/n_y, q2/n_z, q3, q4, q5),
+    Eq. 3b3; ``n`` isotropic (ny, nx) or (3, ny, nx)."""
     q = _state(q)
-    n = np.ascontiguousarray(n, dtype=np.float64)
     ny, nx = q.shape[1:]
+    nxx, nyy, nzz = _medium(n, ny, nx)
     out = np.empty_like(q)
-    _load().orc_fields(nx, ny, _ptr(n), _ptr(q), _ptr(out))
+    _load().orc_fields_aniso(nx, ny, _ptr(nxx), _ptr(nyy), _ptr(nzz), _ptr(q), _ptr(out))
     return out
 
 
 def divergence(q, n, delta):
     """Gauss-law monitors (Eqs. 3.1, 3.2) with centred periodic differences:
     dict with div_b_sq = sum (div B)^2, grad_b_sq = sum (d_x B_x)^2 +
-    (d_y B_y)^2, div_d_sq, grad_d_sq (the same for D = (n q0, n q1)),
+    (d_y B_y)^2, div_d_sq, grad_d_sq (the same for D = (n_x q0, n_y q1)),
     div_b_max, div_d_max."""
     q = _state(q)
-    n = np.ascontiguousarray(n, dtype=np.float64)
     ny, nx = q.shape[1:]
+    nxx, nyy, _ = _medium(n, ny, nx)
     out = np.empty(6)
-    _load().orc_divergence(nx, ny, float(delta), _ptr(n), _ptr(q), _ptr(out))
+    _load().orc_divergence_aniso(nx, ny, float(delta), _ptr(nxx), _ptr(nyy), _ptr(q), _ptr(out))
     keys = ("div_b_sq", "grad_b_sq", "div_d_sq", "grad_d_sq", "div_b_max", "div_d_max")
     return dict(zip(keys, (float(v) for v in out)))
 
@@ -190,6 +222,8 @@ def packet(n, delta, x0, y0, angle, k0, width, transverse_width=0.0,
     lattice whose first site is (i0, j0); the minimum-image distance to the
     packet centre is taken on the global lattice."""
     n = np.ascontiguousarray(n, dtype=np.float64)
+    if n.ndim == 3:                 # index tensor: the E_z packet sees n_z
+        n = np.ascontiguousarray(n[2])
     nwy, nwx = n.shape
     i0, j0 = (0, 0) if window is None else window
     gny, gnx = (nwy, nwx) if global_shape is None else global_shape

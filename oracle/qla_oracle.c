@@ -18,8 +18,11 @@
  *
  * Readings where the paper is garbled or silent (each also listed in the
  * design notes):
- *   - isotropic medium n_x = n_y = n_z = n (Sec. V-B), so
+ *   - the workloads are isotropic, n_x = n_y = n_z = n (Sec. V-B), so
  *     theta_0 = theta_1 = theta_2 = delta/(4n), beta_0 = beta_2, beta_1 = beta_3;
+ *     the *_aniso entry points take the three indices of a diagonal tensor
+ *     separately and give every pair its own angle as Eqs. 2e4, 2e8 and 2e13
+ *     print them;
  *   - streaming read literally: S^{+x} q(x) <- q(x + delta);
  *   - d n / d x by the centred periodic difference (n[i+1]-n[i-1])/(2 delta);
  *   - V: default "rotation" reading (rotation by beta/2 in the planes that
@@ -72,6 +75,45 @@ void orc_angles(int nx, int ny, double delta, const double *n,
     }
 }
 
+/* Per-pair angles of a diagonal index tensor (n_x, n_y, n_z), eight planes
+ * of N values in ang[], in this order:
+ *   0: theta_1 = delta / (4 n_y)   C_x pair (q1, q5)         Eq. 2e4
+ *   1: theta_2 = delta / (4 n_z)   C_x pair (q2, q4)         Eq. 2e4
+ *   2: theta_0 = delta / (4 n_x)   C_y pair (q0, q5)         Eq. 2e8
+ *   3: theta_2 = delta / (4 n_z)   C_y pair (q2, q3)         Eq. 2e8
+ *   4: beta_0 = (d_x n_y) / n_y^2 delta^2   V_x pair (q1, q5)   Eq. 2e13
+ *   5: beta_2 = (d_x n_z) / n_z^2 delta^2   V_x pair (q2, q4)
+ *   6: beta_1 = (d_y n_x) / n_x^2 delta^2   V_y pair (q0, q5)
+ *   7: beta_3 = (d_y n_z) / n_z^2 delta^2   V_y pair (q2, q3)
+ * with the centred periodic difference for the derivatives. */
+static double cdiff(const double *f, int nx, int ny, int i, int j, int axis, double delta)
+{
+    if (axis == 0)
+        return (f[SITE((i + 1) % nx, j)] - f[SITE((i - 1 + nx) % nx, j)]) / (2.0 * delta);
+    return (f[SITE(i, (j + 1) % ny)] - f[SITE(i, (j - 1 + ny) % ny)]) / (2.0 * delta);
+}
+
+void orc_angles_aniso(int nx, int ny, double delta, const double *n_x, const double *n_y,
+                      const double *n_z, double *ang)
+{
+    size_t N = (size_t)nx * ny;
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            size_t k = SITE(i, j);
+            double ax = n_x[k], ay = n_y[k], az = n_z[k];
+            ang[0 * N + k] = delta / (4.0 * ay);
+            ang[1 * N + k] = delta / (4.0 * az);
+            ang[2 * N + k] = delta / (4.0 * ax);
+            ang[3 * N + k] = delta / (4.0 * az);
+            ang[4 * N + k] = cdiff(n_y, nx, ny, i, j, 0, delta) / (ay * ay) * delta * delta;
+            ang[5 * N + k] = cdiff(n_z, nx, ny, i, j, 0, delta) / (az * az) * delta * delta;
+            ang[6 * N + k] = cdiff(n_x, nx, ny, i, j, 1, delta) / (ax * ax) * delta * delta;
+            ang[7 * N + k] = cdiff(n_z, nx, ny, i, j, 1, delta) / (az * az) * delta * delta;
+        }
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* Collision operators                                                */
 /* ------------------------------------------------------------------ */
@@ -100,22 +142,34 @@ static void pair_rotate(int nx, int ny, double *qa, double *qb,
 /* C_x of Eq. 2e3: rows q1 = cos q1 - sin q5, q5 = sin q1 + cos q5 (theta_1),
  * and q2 = cos q2 - sin q4, q4 = sin q2 + cos q4 (theta_2).  The adjoint is
  * the transpose (the sine signs swap). */
-void orc_collide_x(int nx, int ny, double *q, const double *theta, int dagger)
+static void collide_x_pairs(int nx, int ny, double *q, const double *th15,
+                            const double *th24, int dagger)
 {
     size_t N = (size_t)nx * ny;
     double sa = dagger ? +1.0 : -1.0, sb = -sa;
-    pair_rotate(nx, ny, q + 1 * N, q + 5 * N, theta, 1.0, sa, sb);
-    pair_rotate(nx, ny, q + 2 * N, q + 4 * N, theta, 1.0, sa, sb);
+    pair_rotate(nx, ny, q + 1 * N, q + 5 * N, th15, 1.0, sa, sb);
+    pair_rotate(nx, ny, q + 2 * N, q + 4 * N, th24, 1.0, sa, sb);
+}
+
+void orc_collide_x(int nx, int ny, double *q, const double *theta, int dagger)
+{
+    collide_x_pairs(nx, ny, q, theta, theta, dagger);
 }
 
 /* C_y of Eq. 2e8: rows q0 = cos q0 + sin q5, q5 = -sin q0 + cos q5
  * (theta_0), and q2 = cos q2 + sin q3, q3 = -sin q2 + cos q3 (theta_2). */
-void orc_collide_y(int nx, int ny, double *q, const double *theta, int dagger)
+static void collide_y_pairs(int nx, int ny, double *q, const double *th05,
+                            const double *th23, int dagger)
 {
     size_t N = (size_t)nx * ny;
     double sa = dagger ? -1.0 : +1.0, sb = -sa;
-    pair_rotate(nx, ny, q + 0 * N, q + 5 * N, theta, 1.0, sa, sb);
-    pair_rotate(nx, ny, q + 2 * N, q + 3 * N, theta, 1.0, sa, sb);
+    pair_rotate(nx, ny, q + 0 * N, q + 5 * N, th05, 1.0, sa, sb);
+    pair_rotate(nx, ny, q + 2 * N, q + 3 * N, th23, 1.0, sa, sb);
+}
+
+void orc_collide_y(int nx, int ny, double *q, const double *theta, int dagger)
+{
+    collide_y_pairs(nx, ny, q, theta, theta, dagger);
 }
 
 /* ------------------------------------------------------------------ */
@@ -170,8 +224,10 @@ static const int U_SEQUENCE[16] = {
     OP_C,    OP_S2M, OP_CDAG, OP_S2P,
 };
 
-void orc_U(int nx, int ny, double *q, const double *theta, int axis,
-           double *tmp)
+/* th5: angle of the pair with q5 ((q1, q5) along x, (q0, q5) along y);
+ * th2: angle of the pair with q2 ((q2, q4) along x, (q2, q3) along y). */
+static void U_pairs(int nx, int ny, double *q, const double *th5, const double *th2,
+                    int axis, double *tmp)
 {
     /* axis 0: pairs S14 = (q1, q4) and S25 = (q2, q5)   (Eq. 2e5)
      * axis 1: pairs S03 = (q0, q3) and S25 = (q2, q5)   (Eq. 2e9) */
@@ -181,8 +237,8 @@ void orc_U(int nx, int ny, double *q, const double *theta, int axis,
         case OP_C:
         case OP_CDAG: {
             int dag = (U_SEQUENCE[k] == OP_CDAG);
-            if (axis == 0) orc_collide_x(nx, ny, q, theta, dag);
-            else           orc_collide_y(nx, ny, q, theta, dag);
+            if (axis == 0) collide_x_pairs(nx, ny, q, th5, th2, dag);
+            else           collide_y_pairs(nx, ny, q, th5, th2, dag);
             break;
         }
         case OP_S1P: orc_stream(nx, ny, q, f_a, f_b, axis, +1, tmp); break;
@@ -193,6 +249,12 @@ void orc_U(int nx, int ny, double *q, const double *theta, int axis,
     }
 }
 
+void orc_U(int nx, int ny, double *q, const double *theta, int axis,
+           double *tmp)
+{
+    U_pairs(nx, ny, q, theta, theta, axis, tmp);
+}
+
 /* ------------------------------------------------------------------ */
 /* Potential operators V_x, V_y (Eqs. 2e11-2e13)                      */
 /* ------------------------------------------------------------------ */
@@ -200,7 +262,8 @@ void orc_U(int nx, int ny, double *q, const double *theta, int axis,
 /* Printed shear (Eq. 2e11) with the q5 row sign of the LCU sum: only the
  * rows q4 and q5 change,
  *   q4 <- -sin(b2) q2 + cos(b2) q4,   q5 <- +sin(b0) q1 + cos(b0) q5. */
-static void potential_x_literal(int nx, int ny, double *q, const double *bx)
+static void potential_x_literal(int nx, int ny, double *q, const double *b15,
+                                const double *b24)
 {
     size_t N = (size_t)nx * ny;
     double *q1 = q + N, *q2 = q + 2 * N, *q4 = q + 4 * N, *q5 = q + 5 * N;
@@ -208,16 +271,18 @@ static void potential_x_literal(int nx, int ny, double *q, const double *bx)
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             size_t k = SITE(i, j);
-            double b = bx[k], c = cos(b), s = sin(b);
-            q4[k] = -s * q2[k] + c * q4[k];
-            q5[k] = s * q1[k] + c * q5[k];
+            double c2 = cos(b24[k]), s2 = sin(b24[k]);
+            double c0 = cos(b15[k]), s0 = sin(b15[k]);
+            q4[k] = -s2 * q2[k] + c2 * q4[k];
+            q5[k] = s0 * q1[k] + c0 * q5[k];
         }
     }
 }
 
 /* Printed shear (Eq. 2e12) with the q3 row read as sin(b3) q2 + cos(b3) q3:
  *   q3 <- sin(b3) q2 + cos(b3) q3,   q5 <- -sin(b1) q0 + cos(b1) q5. */
-static void potential_y_literal(int nx, int ny, double *q, const double *by)
+static void potential_y_literal(int nx, int ny, double *q, const double *b05,
+                                const double *b23)
 {
     size_t N = (size_t)nx * ny;
     double *q0 = q, *q2 = q + 2 * N, *q3 = q + 3 * N, *q5 = q + 5 * N;
@@ -225,9 +290,10 @@ static void potential_y_literal(int nx, int ny, double *q, const double *by)
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             size_t k = SITE(i, j);
-            double b = by[k], c = cos(b), s = sin(b);
-            q3[k] = s * q2[k] + c * q3[k];
-            q5[k] = -s * q0[k] + c * q5[k];
+            double c3 = cos(b23[k]), s3 = sin(b23[k]);
+            double c1 = cos(b05[k]), s1 = sin(b05[k]);
+            q3[k] = s3 * q2[k] + c3 * q3[k];
+            q5[k] = -s1 * q0[k] + c1 * q5[k];
         }
     }
 }
@@ -238,34 +304,43 @@ static void potential_y_literal(int nx, int ny, double *q, const double *by)
  * planes, i.e. by the angle beta/2 over one step dt = delta^2:
  *   (q2, q4) <- [[c, s], [-s, c]] (q2, q4)     angle beta_2 / 2
  *   (q1, q5) <- [[c, -s], [s, c]] (q1, q5)     angle beta_0 / 2            */
-static void potential_x_rotation(int nx, int ny, double *q, const double *bx)
+static void potential_x_rotation(int nx, int ny, double *q, const double *b15,
+                                 const double *b24)
 {
     size_t N = (size_t)nx * ny;
-    pair_rotate(nx, ny, q + 2 * N, q + 4 * N, bx, 0.5, +1.0, -1.0);
-    pair_rotate(nx, ny, q + 1 * N, q + 5 * N, bx, 0.5, -1.0, +1.0);
+    pair_rotate(nx, ny, q + 2 * N, q + 4 * N, b24, 0.5, +1.0, -1.0);
+    pair_rotate(nx, ny, q + 1 * N, q + 5 * N, b15, 0.5, -1.0, +1.0);
 }
 
 /* Same along y (Eqs. 2d1, 2d3, 2d4, 2d6):
  *   (q2, q3) <- [[c, -s], [s, c]] (q2, q3)     angle beta_3 / 2
  *   (q0, q5) <- [[c, s], [-s, c]] (q0, q5)     angle beta_1 / 2            */
-static void potential_y_rotation(int nx, int ny, double *q, const double *by)
+static void potential_y_rotation(int nx, int ny, double *q, const double *b05,
+                                 const double *b23)
 {
     size_t N = (size_t)nx * ny;
-    pair_rotate(nx, ny, q + 2 * N, q + 3 * N, by, 0.5, -1.0, +1.0);
-    pair_rotate(nx, ny, q + 0 * N, q + 5 * N, by, 0.5, +1.0, -1.0);
+    pair_rotate(nx, ny, q + 2 * N, q + 3 * N, b23, 0.5, -1.0, +1.0);
+    pair_rotate(nx, ny, q + 0 * N, q + 5 * N, b05, 0.5, +1.0, -1.0);
+}
+
+/* V_x then V_y with the angle planes of orc_angles_aniso (slots 4..7). */
+static void V_pairs(int nx, int ny, double *q, const double *b15, const double *b24,
+                    const double *b05, const double *b23, int vmode)
+{
+    if (vmode == ORC_V_ROTATION) {
+        potential_x_rotation(nx, ny, q, b15, b24);
+        potential_y_rotation(nx, ny, q, b05, b23);
+    } else if (vmode == ORC_V_LITERAL) {
+        potential_x_literal(nx, ny, q, b15, b24);
+        potential_y_literal(nx, ny, q, b05, b23);
+    }
+    /* ORC_V_NONE: V = I, the homogeneous step of Eq. 2e10 */
 }
 
 void orc_V(int nx, int ny, double *q, const double *beta_x,
            const double *beta_y, int vmode)
 {
-    if (vmode == ORC_V_ROTATION) {
-        potential_x_rotation(nx, ny, q, beta_x);
-        potential_y_rotation(nx, ny, q, beta_y);
-    } else if (vmode == ORC_V_LITERAL) {
-        potential_x_literal(nx, ny, q, beta_x);
-        potential_y_literal(nx, ny, q, beta_y);
-    }
-    /* ORC_V_NONE: V = I, the homogeneous step of Eq. 2e10 */
+    V_pairs(nx, ny, q, beta_x, beta_x, beta_y, beta_y, vmode);
 }
 
 /* ------------------------------------------------------------------ */
@@ -279,6 +354,27 @@ void orc_step(int nx, int ny, double *q, const double *theta,
     orc_U(nx, ny, q, theta, 0, tmp);          /* U_x */
     orc_U(nx, ny, q, theta, 1, tmp);          /* U_y */
     orc_V(nx, ny, q, beta_x, beta_y, vmode);  /* V_x, then V_y */
+}
+
+/* Eq. 2e14 for a diagonal index tensor: every pair with its own angle. */
+int orc_run_aniso(int nx, int ny, double delta, const double *n_x, const double *n_y,
+                  const double *n_z, double *q, long long steps, int vmode)
+{
+    size_t N = (size_t)nx * ny;
+    double *ang = malloc(8 * N * sizeof(double));
+    double *tmp = malloc(N * sizeof(double));
+    if (!ang || !tmp) {
+        free(ang); free(tmp);
+        return -1;
+    }
+    orc_angles_aniso(nx, ny, delta, n_x, n_y, n_z, ang);
+    for (long long s = 0; s < steps; ++s) {
+        U_pairs(nx, ny, q, ang + 0 * N, ang + 1 * N, 0, tmp);     /* U_x */
+        U_pairs(nx, ny, q, ang + 2 * N, ang + 3 * N, 1, tmp);     /* U_y */
+        V_pairs(nx, ny, q, ang + 4 * N, ang + 5 * N, ang + 6 * N, ang + 7 * N, vmode);
+    }
+    free(ang); free(tmp);
+    return 0;
 }
 
 int orc_run(int nx, int ny, double delta, const double *n, double *q,
@@ -324,10 +420,18 @@ double orc_energy(int nx, int ny, const double *q)
  * planes in the order E_x, E_y, E_z, B_x, B_y, B_z. */
 void orc_fields(int nx, int ny, const double *n, const double *q, double *out)
 {
+    orc_fields_aniso(nx, ny, n, n, n, q, out);
+}
+
+/* The same with E_x = q0 / n_x, E_y = q1 / n_y, E_z = q2 / n_z (Eq. 3b3). */
+void orc_fields_aniso(int nx, int ny, const double *n_x, const double *n_y,
+                      const double *n_z, const double *q, double *out)
+{
     size_t N = (size_t)nx * ny;
+    const double *nc[3] = {n_x, n_y, n_z};
 #pragma omp parallel for schedule(static)
     for (long long k = 0; k < (long long)N; ++k) {
-        for (int c = 0; c < 3; ++c) out[c * N + k] = q[c * N + k] / n[k];
+        for (int c = 0; c < 3; ++c) out[c * N + k] = q[c * N + k] / nc[c][k];
         for (int c = 3; c < 6; ++c) out[c * N + k] = q[c * N + k];
     }
 }
@@ -344,6 +448,13 @@ void orc_fields(int nx, int ny, const double *n, const double *q, double *out)
 void orc_divergence(int nx, int ny, double delta, const double *n, const double *q,
                     double *out)
 {
+    orc_divergence_aniso(nx, ny, delta, n, n, q, out);
+}
+
+/* D_x = n_x q0 and D_y = n_y q1 for a diagonal index tensor. */
+void orc_divergence_aniso(int nx, int ny, double delta, const double *n_x,
+                          const double *n_y, const double *q, double *out)
+{
     size_t N = (size_t)nx * ny;
     const double *q0 = q, *q1 = q + N, *q3 = q + 3 * N, *q4 = q + 4 * N;
     double sb = 0.0, gb = 0.0, sd = 0.0, gd = 0.0, mb = 0.0, md = 0.0;
@@ -352,13 +463,12 @@ void orc_divergence(int nx, int ny, double delta, const double *n, const double 
         const int jp = (j + 1) % ny, jm = (j + ny - 1) % ny;
         for (int i = 0; i < nx; ++i) {
             const int ip = (i + 1) % nx, im = (i + nx - 1) % nx;
-            const size_t k = (size_t)j * nx + i;
             const size_t kxp = (size_t)j * nx + ip, kxm = (size_t)j * nx + im;
             const size_t kyp = (size_t)jp * nx + i, kym = (size_t)jm * nx + i;
             const double dbx = h * (q3[kxp] - q3[kxm]);
             const double dby = h * (q4[kyp] - q4[kym]);
-            const double ddx = h * (n[kxp] * q0[kxp] - n[kxm] * q0[kxm]);
-            const double ddy = h * (n[kyp] * q1[kyp] - n[kym] * q1[kym]);
+            const double ddx = h * (n_x[kxp] * q0[kxp] - n_x[kxm] * q0[kxm]);
+            const double ddy = h * (n_y[kyp] * q1[kyp] - n_y[kym] * q1[kym]);
             const double db = dbx + dby, dd = ddx + ddy;
             sb += db * db;
             gb += dbx * dbx + dby * dby;

@@ -34,6 +34,14 @@ double orc_energy(int nx, int ny, const double *q);
 void orc_fields(int nx, int ny, const double *n, const double *q, double *out);
 void orc_divergence(int nx, int ny, double delta, const double *n, const double *q,
                     double *out);
+void orc_divergence_aniso(int nx, int ny, double delta, const double *n_x,
+                          const double *n_y, const double *q, double *out);
+void orc_fields_aniso(int nx, int ny, const double *n_x, const double *n_y,
+                      const double *n_z, const double *q, double *out);
+void orc_angles_aniso(int nx, int ny, double delta, const double *n_x, const double *n_y,
+                      const double *n_z, double *ang);
+int orc_run_aniso(int nx, int ny, double delta, const double *n_x, const double *n_y,
+                  const double *n_z, double *q, long long steps, int vmode);
 void orc_packet(int nx, int ny, double delta, int i0, int j0, int nwx,
                 int nwy, const double *n_win, double x0, double y0,
                 double phi, double k0, double w, double wt, double amp,

@@ -113,11 +113,28 @@ def medium_angles(n, delta):
     return theta, delta ** 2 * dndx / n ** 2, delta ** 2 * dndy / n ** 2
 
 
+def tensor_angles(nxyz, delta):
+    """Per-pair angles of a diagonal index tensor as the paper prints them:
+    theta_1 = delta/(4 n_y), theta_2 = delta/(4 n_z) (Eq. 2e4),
+    theta_0 = delta/(4 n_x) (Eq. 2e8), beta_0 = delta^2 d_x n_y / n_y^2,
+    beta_1 = delta^2 d_y n_x / n_x^2, beta_2 = delta^2 d_x n_z / n_z^2,
+    beta_3 = delta^2 d_y n_z / n_z^2 (Eq. 2e13, centred differences)."""
+    ax, ay, az = nxyz
+    d_x = lambda f: (np.roll(f, -1, 1) - np.roll(f, 1, 1)) / (2 * delta)
+    d_y = lambda f: (np.roll(f, -1, 0) - np.roll(f, 1, 0)) / (2 * delta)
+    return dict(t0=delta / (4 * ax), t1=delta / (4 * ay), t2=delta / (4 * az),
+                b0=delta ** 2 * d_x(ay) / ay ** 2, b1=delta ** 2 * d_y(ax) / ax ** 2,
+                b2=delta ** 2 * d_x(az) / az ** 2, b3=delta ** 2 * d_y(az) / az ** 2)
+
+
 def assemble_step(n, delta, vmode):
-    theta, bx, by = medium_angles(n, delta)
-    th, bx, by = theta.ravel(), bx.ravel(), by.ravel()
-    Cx = local_op([Cx_matrix(th[k], th[k]) for k in range(N)])
-    Cy = local_op([Cy_matrix(th[k], th[k]) for k in range(N)])
+    return assemble_step_tensor((n, n, n), delta, vmode)
+
+
+def assemble_step_tensor(nxyz, delta, vmode):
+    a = {k: v.ravel() for k, v in tensor_angles(nxyz, delta).items()}
+    Cx = local_op([Cx_matrix(a["t1"][k], a["t2"][k]) for k in range(N)])
+    Cy = local_op([Cy_matrix(a["t0"][k], a["t2"][k]) for k in range(N)])
     Cxd, Cyd = Cx.T, Cy.T
     S14p, S14m = shift_op((1, 4), 0, +1), shift_op((1, 4), 0, -1)
     S25xp, S25xm = shift_op((2, 5), 0, +1), shift_op((2, 5), 0, -1)
@@ -131,12 +148,9 @@ def assemble_step(n, delta, vmode):
           @ S25ym @ Cy @ S25yp @ Cyd @ S03p @ Cy @ S03m @ Cyd)
     if vmode == "none":
         return Uy @ Ux
-    if vmode == "rotation":
-        Vx = local_op([Vx_rotation(bx[k], bx[k]) for k in range(N)])
-        Vy = local_op([Vy_rotation(by[k], by[k]) for k in range(N)])
-    else:
-        Vx = local_op([Vx_literal(bx[k], bx[k]) for k in range(N)])
-        Vy = local_op([Vy_literal(by[k], by[k]) for k in range(N)])
+    Vxf, Vyf = (Vx_rotation, Vy_rotation) if vmode == "rotation" else (Vx_literal, Vy_literal)
+    Vx = local_op([Vxf(a["b0"][k], a["b2"][k]) for k in range(N)])
+    Vy = local_op([Vyf(a["b1"][k], a["b3"][k]) for k in range(N)])
     # Eq. 2e14
     return Vy @ Vx @ Uy @ Ux
 
@@ -185,3 +199,28 @@ def test_U_alone_matches_product_and_reach():
     outw = oracle.U(qw, th, 0)
     cols = np.nonzero(np.abs(outw).sum(axis=(0, 1)) > 1e-300)[0]
     assert cols.min() == 12 and cols.max() == 20
+
+
+@pytest.mark.parametrize("vmode", ["rotation", "literal", "none"])
+def test_anisotropic_step_matches_assembled_matrix(vmode):
+    """Three different index fields n_x, n_y, n_z: every pair of C_x, C_y,
+    V_x and V_y must take its own angle (a pair given the wrong component's
+    angle fails here, which the isotropic case cannot see)."""
+    nxyz = np.stack([inputs.random_medium(NX, NY, seed=s, lo=1.0, hi=3.0, smooth=1)
+                     for s in (21, 22, 23)])
+    q = inputs.random_state(NX, NY, seed=24)
+    M = assemble_step_tensor(tuple(nxyz), 0.8, vmode)
+    want = (M @ q.ravel()).reshape(q.shape)
+    got = oracle.run(q, nxyz, 0.8, 1, vmode)
+    assert np.max(np.abs(got - want)) < 1e-13
+    want2 = (M @ (M @ q.ravel())).reshape(q.shape)
+    assert np.max(np.abs(oracle.run(q, nxyz, 0.8, 2, vmode) - want2)) < 1e-13
+
+
+def test_anisotropic_entry_with_equal_indices_is_the_isotropic_step():
+    n = inputs.random_medium(NX, NY, seed=31, lo=1.0, hi=3.0, smooth=1)
+    q = inputs.random_state(NX, NY, seed=32)
+    for vmode in ("rotation", "literal"):
+        iso = oracle.run(q, n, 1.0, 3, vmode)
+        ani = oracle.run(q, np.stack([n, n, n.copy()]), 1.0, 3, vmode)
+        assert np.array_equal(iso, ani)

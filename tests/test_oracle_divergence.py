@@ -111,3 +111,19 @@ def test_qla_keeps_div_b_zero_to_second_order():
     print("relative div B at delta 1/2, 1/4: %.3e %.3e (ratio %.2f)" % (rel[0], rel[1], rel[0] / rel[1]))
     assert rel[0] / rel[1] > 3.0
     assert rel[1] < 0.03
+
+
+def test_tensor_medium_uses_n_x_and_n_y_for_d():
+    """D = (n_x q0, n_y q1): with q0 = s / n_x and q1 = s / n_y the closed form
+    of the plane wave holds; dividing by the wrong components breaks it."""
+    nx, ny = 48, 30
+    kx, ky, s = _plane(nx, ny, 5, 2)
+    rng = np.random.default_rng(5)
+    nt = 1.0 + rng.random((3, ny, nx))
+    q = np.zeros((6, ny, nx))
+    q[0], q[1] = s / nt[0], s / nt[1]
+    d = oracle.divergence(q, nt, 1.0)
+    N = nx * ny
+    assert d["div_d_sq"] == pytest.approx(N / 2 * (math.sin(kx) + math.sin(ky)) ** 2, rel=1e-12)
+    q[0], q[1] = s / nt[1], s / nt[0]
+    assert oracle.divergence(q, nt, 1.0)["div_d_sq"] != pytest.approx(d["div_d_sq"], rel=1e-3)

@@ -53,6 +53,42 @@ def test_uniform_dielectric_phase_speed_is_one_over_n():
     assert e_right < 0.05 and e_wrong > 1.0
 
 
+@pytest.mark.parametrize("mode", ["te_x", "tm_x", "tm_y"])
+def test_anisotropic_medium_speeds(mode):
+    """Uniform diagonal index tensor (n_x, n_y, n_z) = (1.5, 2, 2.5).  The
+    1D reductions of Eqs. 2d1-2d6 give rigid translations:
+      E_z along x (Eq. 2e2):  q2 = n_z f, q4 = -q2, speed 1/n_z;
+      E_y along x (Eq. 2e1):  q1 = q5 = f, speed 1/n_y;
+      E_x along y (Eqs. 2d1, 2d6): q0 = f, q5 = -f, speed 1/n_x.
+    A pair driven by the wrong component's angle moves at the wrong speed."""
+    delta, L, T, w, k0, x0 = 0.25, 128.0, 32.0, 8.0, 0.5, 40.0
+    m = int(L / delta)
+    along_y = mode == "tm_y"
+    shape = (m, 2) if along_y else (2, m)
+    nt = np.stack([np.full(shape, v) for v in (1.5, 2.0, 2.5)])
+    x = np.arange(m) * delta
+    f0 = gaussian(x, x0, w, k0)
+    q = np.zeros((6,) + shape)
+    line = (lambda a: a[:, None] * np.ones((1, 2))) if along_y else (lambda a: a[None, :] * np.ones((2, 1)))
+    if mode == "te_x":
+        q[2], q[4] = 2.5 * line(f0), -2.5 * line(f0)
+        comp, amp, v = 2, 2.5, 1 / 2.5
+    elif mode == "tm_x":
+        q[1], q[5] = line(f0), line(f0)
+        comp, amp, v = 1, 1.0, 1 / 2.0
+    else:
+        q[0], q[5] = line(f0), -line(f0)
+        comp, amp, v = 0, 1.0, 1 / 1.5
+    qT = oracle.run(q, nt, delta, int(round(T / delta ** 2)))
+    got = qT[comp][:, 0] if along_y else qT[comp][0]
+    err = lambda speed: np.linalg.norm(got - amp * gaussian(x, x0 + speed * T, w, k0)) / np.linalg.norm(amp * f0)
+    e_right = err(v)
+    assert e_right < 0.08, (mode, e_right)   # O(delta^2) truncation: 0.02-0.05
+    for wrong in (1 / 1.5, 1 / 2.0, 1 / 2.5):
+        if wrong != v:
+            assert err(wrong) > 0.5, (mode, wrong)
+
+
 def _exact_te_vacuum(q, d, T):
     """Exact continuum solution of the vacuum TE equations (Eqs. 2d3-2d5 with
     n = 1): in Fourier space d/dt (q2, q3, q4) = i B(k) (q2, q3, q4) with B
@@ -209,6 +245,48 @@ def test_generator_literal_and_no_potential_do_not_converge():
     for vm in ("literal", "none"):
         e64, e128 = _generator_error(64, vm), _generator_error(128, vm)
         assert e128 > 0.05 and e64 / e128 < 2.0, (vm, e64, e128)
+
+
+def _aniso_generator_error(N, L=32.0):
+    """(step - I)/delta^2 against Eqs. 2d1-2d6 as printed for a diagonal
+    index tensor whose three components vary differently in x and y."""
+    k = 2 * math.pi / L
+    d = L / N
+    x = np.arange(N)[None, :] * d + np.zeros((N, 1))
+    y = np.arange(N)[:, None] * d + np.zeros((1, N))
+    nX = 1.4 + 0.2 * np.sin(k * x + 0.3) + 0.25 * np.cos(k * y)
+    nY = 1.7 + 0.3 * np.cos(k * x) + 0.15 * np.sin(k * y + 1.0)
+    nZ = 1.5 + 0.3 * np.sin(k * x) + 0.2 * np.cos(k * y)
+    dx_nY = -0.3 * k * np.sin(k * x)
+    dx_nZ = 0.3 * k * np.cos(k * x)
+    dy_nX = -0.25 * k * np.sin(k * y)
+    dy_nZ = -0.2 * k * np.sin(k * y)
+    spec = [(1, 2, 0.1), (2, -1, 0.7), (1, 1, 1.3), (-1, 2, 2.1), (2, 1, 0.4), (1, -2, 1.9)]
+    q, qx, qy = [], [], []
+    for m, p, ph in spec:
+        arg = k * (m * x + p * y) + ph
+        q.append(np.sin(arg))
+        qx.append(k * m * np.cos(arg))
+        qy.append(k * p * np.cos(arg))
+    q, qx, qy = np.array(q), np.array(qx), np.array(qy)
+    r = np.zeros_like(q)
+    r[0] = qy[5] / nX                                               # Eq. 2d1
+    r[1] = -qx[5] / nY                                              # Eq. 2d2
+    r[2] = -qy[3] / nZ + qx[4] / nZ                                 # Eq. 2d3
+    r[3] = -qy[2] / nZ + q[2] * dy_nZ / nZ ** 2                     # Eq. 2d4
+    r[4] = qx[2] / nZ - q[2] * dx_nZ / nZ ** 2                      # Eq. 2d5
+    r[5] = (qy[0] / nX - qx[1] / nY - q[0] * dy_nX / nX ** 2
+            + q[1] * dx_nY / nY ** 2)                               # Eq. 2d6
+    G = (oracle.run(q, np.stack([nX, nY, nZ]), d, 1) - q) / d ** 2
+    return max(np.linalg.norm(G[c] - r[c]) / np.linalg.norm(r[c]) for c in range(6))
+
+
+def test_anisotropic_generator_recovers_maxwell_equations_at_second_order():
+    """With each pair's collision and potential angle taken from its own
+    index component (Eqs. 2e4, 2e8, 2e13), the step recovers the anisotropic
+    Eqs. 2d1-2d6 at O(delta^2) in every component."""
+    e64, e128 = _aniso_generator_error(64), _aniso_generator_error(128)
+    assert e128 < 0.03 and 3.6 < e64 / e128 < 4.4, (e64, e128)
 
 
 def test_beta_follows_the_analytic_gradient():
