@@ -64,7 +64,13 @@ enum {
      * to O(delta^2) and the step exactly unitary. */
     QLA_POTENTIAL_LITERAL = 2u,
     /* V = I: the homogeneous-medium step of Eq. 2e10. */
-    QLA_POTENTIAL_NONE = 4u
+    QLA_POTENTIAL_NONE = 4u,
+    /* Diagonal index tensor (n_x, n_y, n_z) instead of a scalar n: the
+     * workspace gains the n_x and n_y planes (and, with six planes, a wider
+     * per-site record) so that qla_set_medium_tensor can give every pair its
+     * own angle.  E_z contexts (QLA_TE_ONLY) see n_z only and keep every step
+     * kernel; six-plane contexts step with the tile kernel. */
+    QLA_ANISOTROPIC = 8u
 };
 
 /* E_z-polarised Gaussian packet (Sec. V-B): with
@@ -104,6 +110,21 @@ qla_status qla_init_grid(qla_ctx **out, int nx, int ny, double delta,
  * part).  Returns QLA_EINVAL (and changes nothing) if any n is not finite
  * or not positive. */
 qla_status qla_set_medium(qla_ctx *ctx, const double *n_host);
+
+/* Set a diagonal index tensor n = diag(n_x, n_y, n_z)(x, y) (Sec. III, the
+ * form in which Eqs. 2d1-2d6, 2e3-2e13 are written); three nx*ny FP64 host
+ * arrays, every value finite and > 0, copied before return.  Each pair
+ * takes its own angle:
+ *   C_x (Eq. 2e3):  (q1, q5) theta_1 = delta/(4 n_y); (q2, q4) theta_2 = delta/(4 n_z)
+ *   C_y (Eq. 2e8):  (q0, q5) theta_0 = delta/(4 n_x); (q2, q3) theta_2
+ *   V_x (Eq. 2e13): (q1, q5) beta_0 = delta^2 d_x n_y / n_y^2; (q2, q4) beta_2 = delta^2 d_x n_z / n_z^2
+ *   V_y:            (q0, q5) beta_1 = delta^2 d_y n_x / n_x^2; (q2, q3) beta_3 = delta^2 d_y n_z / n_z^2
+ * and read-outs use E = (q0/n_x, q1/n_y, q2/n_z), D = (n_x q0, n_y q1), the
+ * packet q2 = n_z E_z.  Needs a context made with QLA_ANISOTROPIC (else
+ * QLA_EINVAL); on such a context qla_set_medium(n) equals
+ * qla_set_medium_tensor(n, n, n).  Synchronises. */
+qla_status qla_set_medium_tensor(qla_ctx *ctx, const double *n_x, const double *n_y,
+                                 const double *n_z);
 
 /* Fill the state with the packet described by *p (see qla_packet) on the
  * current medium.  QLA_ESTATE if no medium was set; QLA_EINVAL if width

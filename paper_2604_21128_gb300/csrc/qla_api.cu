@@ -40,6 +40,15 @@ Layout layout_for(int nx, int ny, int prec, unsigned flags) {
     // partials: up to DIV_TERMS doubles per block (energy uses one)
     L.partials = off; off += align256(nb * 8 * DIV_TERMS);
     L.result = off;   off += align256(8 * DIV_TERMS);
+    L.n_x = L.n_y = L.ttable = 0;
+    if (flags & QLA_ANISOTROPIC) {
+        L.n_x = off; off += align256(L.plane_elems * 8);
+        L.n_y = off; off += align256(L.plane_elems * 8);
+        if (P == 6) {
+            const size_t trec = prec == QLA_FP64 ? sizeof(MedRecT<double>) : sizeof(MedRecT<float>);
+            L.ttable = off; off += align256(L.plane_elems * trec);
+        }
+    }
     L.total = off;
     return L;
 }
@@ -108,7 +117,8 @@ qla_status qla_init_grid(qla_ctx **out, int nx, int ny, double delta, int precis
     *out = nullptr;
     if (nx < 1 || ny < 1 || !(delta > 0.0) || !std::isfinite(delta)) return QLA_EINVAL;
     if (precision != QLA_FP64 && precision != QLA_FP32) return QLA_EINVAL;
-    if (flags & ~(unsigned)(QLA_TE_ONLY | QLA_POTENTIAL_LITERAL | QLA_POTENTIAL_NONE))
+    if (flags & ~(unsigned)(QLA_TE_ONLY | QLA_POTENTIAL_LITERAL | QLA_POTENTIAL_NONE |
+                            QLA_ANISOTROPIC))
         return QLA_EINVAL;
     if ((flags & QLA_POTENTIAL_LITERAL) && (flags & QLA_POTENTIAL_NONE)) return QLA_EINVAL;
     if (size_t(nx) * size_t(ny) > (size_t(1) << 34)) return QLA_EINVAL;
@@ -158,6 +168,12 @@ qla_status qla_init_grid(qla_ctx **out, int nx, int ny, double delta, int precis
     c->partials = reinterpret_cast<double *>(c->ws + L.partials);
     c->result = reinterpret_cast<double *>(c->ws + L.result);
     c->energy_blocks = L.energy_blocks;
+    c->tensor = (flags & QLA_ANISOTROPIC) != 0;
+    if (c->tensor) {
+        c->n_x = reinterpret_cast<double *>(c->ws + L.n_x);
+        c->n_y = reinterpret_cast<double *>(c->ws + L.n_y);
+        if (c->P == 6) c->ttable = c->ws + L.ttable;
+    }
     // both state buffers start at zero (pad columns included)
     if (cudaMemsetAsync(c->ws + L.state[0], 0, L.midx - L.state[0], c->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -169,10 +185,55 @@ qla_status qla_init_grid(qla_ctx **out, int nx, int ny, double delta, int precis
     return QLA_OK;
 }
 
+static qla_status check_positive(qla_ctx *c, const double *a, const char *what) {
+    const size_t N = size_t(c->nx) * c->ny;
+    for (size_t k = 0; k < N; ++k) {
+        const double v = a[k];
+        if (!(v > 0.0) || !std::isfinite(v))
+            return fail(c, QLA_EINVAL, "%s[%zu] = %g is not finite and > 0", what, k, v);
+    }
+    return QLA_OK;
+}
+
+qla_status qla_set_medium_tensor(qla_ctx *c, const double *n_x, const double *n_y,
+                                 const double *n_z) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (!c->tensor)
+        return fail(c, QLA_EINVAL, "qla_set_medium_tensor: context made without QLA_ANISOTROPIC");
+    if (!n_x || !n_y || !n_z) return fail(c, QLA_EINVAL, "qla_set_medium_tensor: null array");
+    if ((s = check_positive(c, n_x, "qla_set_medium_tensor: n_x")) != QLA_OK) return s;
+    if ((s = check_positive(c, n_y, "qla_set_medium_tensor: n_y")) != QLA_OK) return s;
+    if ((s = check_positive(c, n_z, "qla_set_medium_tensor: n_z")) != QLA_OK) return s;
+    const size_t N = size_t(c->nx) * c->ny;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, QLA_ECUDA, "qla_set_medium_tensor: cannot select device");
+    // n_x and n_y through the staging plane into their pitched planes
+    const double *src[2] = {n_x, n_y};
+    double *dst[2] = {c->n_x, c->n_y};
+    for (int k = 0; k < 2; ++k) {
+        QLA_CUDA(c, cudaMemcpyAsync(c->staging, src[k], N * 8, cudaMemcpyHostToDevice, c->stream),
+                 "qla_set_medium_tensor: copy");
+        QLA_CUDA(c, launch_pitch_copy(c, dst[k]), "qla_set_medium_tensor: place");
+    }
+    // n_z is the scalar medium of the E_z triple: the shared-record table
+    QLA_CUDA(c, cudaMemcpyAsync(c->staging, n_z, N * 8, cudaMemcpyHostToDevice, c->stream),
+             "qla_set_medium_tensor: copy");
+    QLA_CUDA(c, cudaMemsetAsync(c->keys, 0, UNIFORM_SLOTS * 8, c->stream),
+             "qla_set_medium_tensor: clear");
+    QLA_CUDA(c, cudaMemsetAsync(c->counter, 0, 4, c->stream), "qla_set_medium_tensor: clear");
+    QLA_CUDA(c, launch_medium(c), "qla_set_medium_tensor: kernel");
+    if (c->P == 6) QLA_CUDA(c, launch_medium_tensor(c), "qla_set_medium_tensor: records");
+    QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_set_medium_tensor: sync");
+    c->has_medium = true;
+    return QLA_OK;
+}
+
 qla_status qla_set_medium(qla_ctx *c, const double *n_host) {
     qla_status s = usable(c);
     if (s != QLA_OK) return s;
     if (!n_host) return fail(c, QLA_EINVAL, "qla_set_medium: null n");
+    if (c->tensor) return qla_set_medium_tensor(c, n_host, n_host, n_host);
     const size_t N = size_t(c->nx) * c->ny;
     for (size_t k = 0; k < N; ++k) {
         const double v = n_host[k];
@@ -278,6 +339,17 @@ qla_status qla_step(qla_ctx *c, long long n_steps) {
         return fail(c, QLA_ESTATE, "qla_step: set a medium and a state first");
     DeviceGuard dg(c->device);
     if (!dg.ok) return fail(c, QLA_ECUDA, "qla_step: cannot select device");
+    if (c->tensor && c->P == 6) {
+        // every pair with its own angle; V applied in the same launch
+        for (long long k = 0; k < n_steps; ++k) {
+            QLA_CUDA(c, launch_step_tensor(c, c->state[c->cur], c->state[c->cur ^ 1]),
+                     "qla_step: kernel");
+            c->launches++;
+            c->cur ^= 1;
+        }
+        c->pending_v = false;
+        return QLA_OK;
+    }
     const bool march = c->step_kernel == QLA_KERNEL_MARCH ||
                        (c->step_kernel == QLA_KERNEL_AUTO && march_supported(c));
     for (long long k = 0; k < n_steps; ++k) {
@@ -385,6 +457,9 @@ qla_status qla_set_step_kernel(qla_ctx *c, int kernel) {
     if (s != QLA_OK) return s;
     if (kernel < QLA_KERNEL_AUTO || kernel > QLA_KERNEL_MARCH)
         return fail(c, QLA_EINVAL, "qla_set_step_kernel: unknown kernel %d", kernel);
+    if (kernel == QLA_KERNEL_MARCH && c->tensor && c->P == 6)
+        return fail(c, QLA_EINVAL, "qla_set_step_kernel: six-plane tensor media use the tile "
+                                   "kernel");
     if (kernel == QLA_KERNEL_MARCH && !march_supported(c))
         return fail(c, QLA_EINVAL, "qla_set_step_kernel: the marching kernel needs nx a multiple "
                                    "of its lane width, nx >= 32 lane widths and ny >= 8");

@@ -120,6 +120,42 @@ __global__ void k_medium(const double *__restrict__ n, int nx, int ny, int pitch
 }
 
 // Copy a contiguous FP64 host-layout plane into the pitched n plane.
+// Records of a diagonal index tensor, one per stored site: each pair's
+// collision angle from its own component (Eqs. 2e4, 2e8) and the potential
+// angles beta_0..beta_3 of Eq. 2e13 (centred periodic differences), times
+// vscale (1/2 for the rotation reading).  The same coefficient construction
+// as the scalar records (make_rec).
+template <typename T>
+__global__ void k_medium_tensor(const double *__restrict__ nX, const double *__restrict__ nY,
+                                const double *__restrict__ nZ, int nx, int ny, int pitch,
+                                double delta, double vscale, MedRecT<T> *__restrict__ table) {
+    const size_t N = size_t(nx) * ny;
+    for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < N;
+         t += size_t(gridDim.x) * blockDim.x) {
+        const int j = int(t / nx), i = int(t - size_t(j) * nx);
+        const size_t g = size_t(j) * pitch + i;
+        const size_t gxp = size_t(j) * pitch + wrap(i + 1, nx), gxm = size_t(j) * pitch + wrap(i - 1, nx);
+        const size_t gyp = size_t(wrap(j + 1, ny)) * pitch + i, gym = size_t(wrap(j - 1, ny)) * pitch + i;
+        const double ax = nX[g], ay = nY[g], az = nZ[g];
+        // the expression of k_medium, so equal components give equal records
+        const double b0 = (nY[gxp] - nY[gxm]) / (2.0 * delta) / (ay * ay) * delta * delta;
+        const double b2 = (nZ[gxp] - nZ[gxm]) / (2.0 * delta) / (az * az) * delta * delta;
+        const double b1 = (nX[gyp] - nX[gym]) / (2.0 * delta) / (ax * ax) * delta * delta;
+        const double b3 = (nZ[gyp] - nZ[gym]) / (2.0 * delta) / (az * az) * delta * delta;
+        MedRec<T> ry, rz, rx;
+        make_rec(ry, delta / (4.0 * ay), vscale * b0, vscale * b1);
+        make_rec(rz, delta / (4.0 * az), vscale * b2, vscale * b3);
+        make_rec(rx, delta / (4.0 * ax), 0.0, 0.0);
+        MedRecT<T> r;
+        r.c15 = ry.c;
+        r.c2 = rz.c;
+        r.c05 = rx.c;
+        r.vz = rz.v;
+        r.vt = ry.v;
+        table[g] = r;
+    }
+}
+
 __global__ void k_pitch_copy(const double *__restrict__ src, double *__restrict__ dst, int nx,
                              int ny, int pitch) {
     const size_t N = size_t(nx) * ny;
@@ -272,12 +308,13 @@ __device__ double block_max(double v) {
 }
 
 // Gauss laws (Eqs. 3.1, 3.2) with centred periodic differences: fields vary
-// in x and y only, B = (q3, q4), D = n^2 E = (n q0, n q1) (Dyson variables,
-// c = 1).  Each site reads its four neighbours' amplitudes (the pending
+// in x and y only, B = (q3, q4), D = (n_x q0, n_y q1) (Dyson variables,
+// c = 1; n_x = n_y = n for a scalar medium).  Each site reads its four neighbours' amplitudes (the pending
 // potential step applied) and medium.
 template <typename T, int P, int VM>
 __global__ void __launch_bounds__(AUX_THREADS)
-k_div_partial(const T *__restrict__ q, const double *__restrict__ n, int nx, int ny, int pitch,
+k_div_partial(const T *__restrict__ q, const double *__restrict__ nX,
+              const double *__restrict__ nY, int nx, int ny, int pitch,
               size_t plane_elems, double inv2d, double *__restrict__ partials, bool vin,
               const uint32_t *__restrict__ midx, const MedRec<T> *__restrict__ table) {
     const size_t N = size_t(nx) * ny;
@@ -296,8 +333,8 @@ k_div_partial(const T *__restrict__ q, const double *__restrict__ n, int nx, int
         load_site<T, P, VM>(q, plane_elems, gym, vin, midx, table, d);
         const double dbx = inv2d * (double(a[3]) - double(b[3]));
         const double dby = inv2d * (double(c[4]) - double(d[4]));
-        const double ddx = inv2d * (n[gxp] * double(a[0]) - n[gxm] * double(b[0]));
-        const double ddy = inv2d * (n[gyp] * double(c[1]) - n[gym] * double(d[1]));
+        const double ddx = inv2d * (nX[gxp] * double(a[0]) - nX[gxm] * double(b[0]));
+        const double ddy = inv2d * (nY[gyp] * double(c[1]) - nY[gym] * double(d[1]));
         const double db = dbx + dby, dd = ddx + ddy;
         sb = fma(db, db, sb);
         gb = fma(dbx, dbx, fma(dby, dby, gb));
@@ -359,6 +396,29 @@ cudaError_t launch_medium(qla_ctx *c) {
         k_medium<float><<<grid_for(N), AUX_THREADS, 0, c->stream>>>(
             c->n, c->nx, c->ny, c->pitch, c->delta, vscale, c->keys, c->counter, c->midx,
             static_cast<MedRec<float> *>(c->table));
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pitch_copy(qla_ctx *c, double *dst) {
+    const size_t N = size_t(c->nx) * c->ny;
+    k_pitch_copy<<<grid_for(N), AUX_THREADS, 0, c->stream>>>(c->staging, dst, c->nx, c->ny,
+                                                              c->pitch);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_medium_tensor(qla_ctx *c) {
+    const size_t N = size_t(c->nx) * c->ny;
+    const double vscale = c->vmode == V_ROTATION ? 0.5 : 1.0;
+    if (c->prec == QLA_FP64)
+        k_medium_tensor<double><<<grid_for(N), AUX_THREADS, 0, c->stream>>>(
+            c->n_x, c->n_y, c->n, c->nx, c->ny, c->pitch, c->delta, vscale,
+            static_cast<MedRecT<double> *>(c->ttable));
+    else
+        k_medium_tensor<float><<<grid_for(N), AUX_THREADS, 0, c->stream>>>(
+            c->n_x, c->n_y, c->n, c->nx, c->ny, c->pitch, c->delta, vscale,
+            static_cast<MedRecT<float> *>(c->ttable));
     c->launches++;
     return cudaGetLastError();
 }
@@ -450,7 +510,11 @@ cudaError_t launch_to_f64(qla_ctx *c, int comp, double *dst) {
 }
 
 cudaError_t launch_fields(qla_ctx *c, int comp, double *dst) {
-    return readout(c, 0, comp, comp < 3 ? c->n : nullptr, dst);
+    const double *n = comp == 0 && c->tensor ? c->n_x
+                    : comp == 1 && c->tensor ? c->n_y
+                    : comp < 3              ? c->n
+                                            : nullptr;
+    return readout(c, 0, comp, n, dst);
 }
 
 cudaError_t launch_probe(qla_ctx *c, int count, const int *ij_dev, double *out_dev) {
@@ -460,7 +524,8 @@ cudaError_t launch_probe(qla_ctx *c, int count, const int *ij_dev, double *out_d
 template <typename T, int P, int VM>
 static cudaError_t divergence_t(qla_ctx *c) {
     k_div_partial<T, P, VM><<<c->energy_blocks, AUX_THREADS, 0, c->stream>>>(
-        static_cast<const T *>(c->state[c->cur]), c->n, c->nx, c->ny, c->pitch, c->plane_elems,
+        static_cast<const T *>(c->state[c->cur]), c->tensor ? c->n_x : c->n,
+        c->tensor ? c->n_y : c->n, c->nx, c->ny, c->pitch, c->plane_elems,
         0.5 / c->delta, c->partials, c->pending_v, c->midx,
         static_cast<const MedRec<T> *>(c->table));
     c->launches++;

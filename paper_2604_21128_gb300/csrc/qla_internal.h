@@ -148,6 +148,35 @@ __device__ __forceinline__ void apply_potential(T (&q)[6], KV kv) {
     }
 }
 
+// Per-site record of a diagonal index tensor (six-plane contexts made with
+// QLA_ANISOTROPIC): a collision coefficient per pair class and the potential
+// coefficients of the E_z triple (from n_z) and of the (q0, q1, q5) triple
+// (V_x from n_y, V_y from n_x), in the layouts of Coef<T>.
+template <typename T> struct MedRecT {
+    typename Coef<T>::C c15;   // C_x (q1, q5): theta_1 = delta/(4 n_y)
+    typename Coef<T>::C c2;    // C_x (q2, q4) and C_y (q2, q3): theta_2 = delta/(4 n_z)
+    typename Coef<T>::C c05;   // C_y (q0, q5): theta_0 = delta/(4 n_x)
+    typename Coef<T>::V vz;    // V_x (q2, q4) from beta_2, V_y (q2, q3) from beta_3
+    typename Coef<T>::V vt;    // V_x (q1, q5) from beta_0, V_y (q0, q5) from beta_1
+};
+
+// apply_potential with each pair's own coefficients (same operations, same
+// order): kz for the pairs with q2, kt for the pairs with q5.
+template <typename T, int P, int VM, typename KV>
+__device__ __forceinline__ void apply_potential_tensor(T (&q)[6], KV kz, KV kt) {
+    if constexpr (VM == V_ROTATION) {
+        rotate1(q[2], q[4], kz.x, kz.y, T(-1));
+        if constexpr (P == 6) rotate1(q[1], q[5], kt.x, kt.y, T(1));
+        rotate1(q[2], q[3], kz.z, kz.w, T(1));
+        if constexpr (P == 6) rotate1(q[0], q[5], kt.z, kt.w, T(-1));
+    } else if constexpr (VM == V_LITERAL) {
+        shear1(q[2], q[4], kz.x, kz.y, T(-1));
+        if constexpr (P == 6) shear1(q[1], q[5], kt.x, kt.y, T(1));
+        shear1(q[2], q[3], kz.z, kz.w, T(1));
+        if constexpr (P == 6) shear1(q[0], q[5], kt.z, kt.w, T(-1));
+    }
+}
+
 // The six amplitudes of the state at site g (storage offset), with the
 // pending potential operator applied when vin (entries absent in E_z mode
 // are zero).
@@ -195,7 +224,12 @@ struct qla_ctx {
     unsigned long long *keys = nullptr;  // UNIFORM_SLOTS hash keys (n bits)
     unsigned *counter = nullptr;    // records handed to non-uniform sites
     int march_lx = 0, march_seg = 0;  // tuning (0 = automatic)
-    double *n = nullptr;            // ny * pitch
+    double *n = nullptr;            // ny * pitch (n_z of a tensor medium)
+    // QLA_ANISOTROPIC contexts: n_x, n_y planes (ny * pitch) and, with six
+    // planes, one MedRecT<T> per stored site (indexed like the state)
+    bool tensor = false;
+    double *n_x = nullptr, *n_y = nullptr;
+    void *ttable = nullptr;
     double *staging = nullptr;      // ny * nx
     double *partials = nullptr;     // energy partial sums
     double *result = nullptr;       // final energy (device)
@@ -216,6 +250,7 @@ namespace qla {
 // Workspace layout: offsets of each region (bytes, 256-aligned).
 struct Layout {
     size_t state[2], midx, table, keys, counter, n, staging, partials, result, total;
+    size_t n_x, n_y, ttable;  // QLA_ANISOTROPIC only (else 0)
     size_t plane_elems;
     int pitch, energy_blocks;
 };
@@ -223,6 +258,11 @@ Layout layout_for(int nx, int ny, int prec, unsigned flags);
 
 // Launchers (host), each returns the cudaError_t of its launch.
 cudaError_t launch_medium(qla_ctx *c);
+// Tensor media: stage one host plane (already in c->staging) into dst;
+// build the MedRecT table of a six-plane QLA_ANISOTROPIC context.
+cudaError_t launch_pitch_copy(qla_ctx *c, double *dst);
+cudaError_t launch_medium_tensor(qla_ctx *c);
+cudaError_t launch_step_tensor(qla_ctx *c, const void *in, void *out);
 cudaError_t launch_packet(qla_ctx *c, const qla_packet &p);
 cudaError_t launch_from_f64(qla_ctx *c, int plane, const double *src);
 cudaError_t launch_to_f64(qla_ctx *c, int comp, double *dst);

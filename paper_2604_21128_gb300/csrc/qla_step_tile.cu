@@ -10,6 +10,10 @@
 // leave the staged region are skipped, which only corrupts halo cells that
 // no output depends on.  The previous step's V_x, V_y (when pending) are
 // applied to every staged site on load; the buffer written holds U_y U_x Q.
+// For a diagonal index tensor (six planes) the kernel stages a coefficient
+// per pair class and applies this step's V before storing instead.
+#include <type_traits>
+
 #include "qla_internal.h"
 
 namespace qla {
@@ -22,11 +26,23 @@ template <typename T> struct TileShape;
 template <> struct TileShape<double> { static constexpr int TX = 32, TY = 16; };
 template <> struct TileShape<float>  { static constexpr int TX = 32, TY = 32; };
 
+// Staged collision coefficients of a diagonal index tensor: one per pair
+// class (see MedRecT).
+template <typename T> struct TriC { typename Coef<T>::C c15, c2, c05; };
+
+// The coefficient of pair pk (0: the pair with q5, 1: the pair with q2) of a
+// direction: a scalar medium has one for all pairs.
+template <bool XDIR, typename C>
+__device__ __forceinline__ C coef_of(C k, int) { return k; }
+template <bool XDIR, typename T>
+__device__ __forceinline__ typename Coef<T>::C coef_of(const TriC<T> &k, int pk) {
+    return pk == 1 ? k.c2 : XDIR ? k.c15 : k.c05;
+}
+
 // Apply one bond layer to all pairs of one direction at bond site `i` of a
 // line whose elements are `stride` apart in shared memory.
-template <typename T, int P, bool XDIR, int L>
-__device__ __forceinline__ void bond(T *s, size_t plane, int idx, int stride,
-                                     typename Coef<T>::C k) {
+template <typename T, int P, bool XDIR, int L, typename SC>
+__device__ __forceinline__ void bond(T *s, size_t plane, int idx, int stride, const SC &k) {
     constexpr Layer ly = layer_of(L);
     // collision sign: C_x rotates by +theta, C_y by -theta; adjoint flips
     constexpr int g0 = XDIR ? 1 : -1;
@@ -46,14 +62,14 @@ __device__ __forceinline__ void bond(T *s, size_t plane, int idx, int stride,
             if (pr.a_is_m1) ib += ly.shift * stride; else ia += ly.shift * stride;
         }
         T a = s[pa * plane + ia], b = s[pb * plane + ib];
-        rotate(a, b, k, g);
+        rotate(a, b, coef_of<XDIR>(k, pk), g);
         s[pa * plane + ia] = a;
         s[pb * plane + ib] = b;
     }
 }
 
-template <typename T, int P, bool XDIR, int L, int RX, int RY, int TX>
-__device__ __forceinline__ void layer_pass(T *s, const typename Coef<T>::C *sc) {
+template <typename T, int P, bool XDIR, int L, int RX, int RY, int TX, typename SC>
+__device__ __forceinline__ void layer_pass(T *s, const SC *sc) {
     constexpr Layer ly = layer_of(L);
     constexpr size_t plane = size_t(RX) * RY;
     if constexpr (XDIR) {
@@ -75,8 +91,8 @@ __device__ __forceinline__ void layer_pass(T *s, const typename Coef<T>::C *sc) 
     }
 }
 
-template <typename T, int P, bool XDIR, int RX, int RY, int TX>
-__device__ __forceinline__ void apply_U(T *s, const typename Coef<T>::C *sc) {
+template <typename T, int P, bool XDIR, int RX, int RY, int TX, typename SC>
+__device__ __forceinline__ void apply_U(T *s, const SC *sc) {
     layer_pass<T, P, XDIR, 0, RX, RY, TX>(s, sc); __syncthreads();
     layer_pass<T, P, XDIR, 1, RX, RY, TX>(s, sc); __syncthreads();
     layer_pass<T, P, XDIR, 2, RX, RY, TX>(s, sc); __syncthreads();
@@ -87,17 +103,22 @@ __device__ __forceinline__ void apply_U(T *s, const typename Coef<T>::C *sc) {
     layer_pass<T, P, XDIR, 7, RX, RY, TX>(s, sc); __syncthreads();
 }
 
-template <typename T, int P, int VM, bool VIN>
+// TS: a diagonal index tensor (QLA_ANISOTROPIC, six planes): per-site
+// records in ttable, each pair with its own coefficient, and this step's
+// potential operator applied to the outputs before they are stored (no
+// pending V; VIN is false).
+template <typename T, int P, int VM, bool VIN, bool TS>
 __global__ void __launch_bounds__(THREADS)
 k_step_tile(const T *__restrict__ in, T *__restrict__ out,
             const uint32_t *__restrict__ midx, const MedRec<T> *__restrict__ table,
-            int nx, int ny, int pitch, size_t plane_elems) {
-    using CC = typename Coef<T>::C;
+            const MedRecT<T> *__restrict__ ttable, int nx, int ny, int pitch,
+            size_t plane_elems) {
+    using SC = typename std::conditional<TS, TriC<T>, typename Coef<T>::C>::type;
     constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
     constexpr int RX = TX + 2 * HALO, RY = TY + 2 * HALO;
     constexpr size_t plane = size_t(RX) * RY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    CC *sc = reinterpret_cast<CC *>(smem_raw);
+    SC *sc = reinterpret_cast<SC *>(smem_raw);
     T *s = reinterpret_cast<T *>(sc + plane);
 
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -113,7 +134,12 @@ k_step_tile(const T *__restrict__ in, T *__restrict__ out,
             const int p = plane_of<P>(k);
             if (p >= 0) s[p * plane + t] = q[k];
         }
-        sc[t] = table[midx[g]].c;
+        if constexpr (TS) {
+            const MedRecT<T> &r = ttable[g];
+            sc[t] = SC{r.c15, r.c2, r.c05};
+        } else {
+            sc[t] = table[midx[g]].c;
+        }
     }
     __syncthreads();
     apply_U<T, P, true, RX, RY, TX>(s, sc);    // U_x (Eq. 2e6)
@@ -131,6 +157,10 @@ k_step_tile(const T *__restrict__ in, T *__restrict__ out,
             q[k] = p >= 0 ? s[p * plane + st] : T(0);
         }
         const size_t g = size_t(gy) * pitch + gx;
+        if constexpr (TS) {
+            const MedRecT<T> &r = ttable[g];
+            apply_potential_tensor<T, P, VM>(q, r.vz, r.vt);   // V_y V_x (Eq. 2e14)
+        }
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const int p = plane_of<P>(k);
@@ -139,12 +169,13 @@ k_step_tile(const T *__restrict__ in, T *__restrict__ out,
     }
 }
 
-template <typename T, int P, int VM, bool VIN>
+template <typename T, int P, int VM, bool VIN, bool TS = false>
 cudaError_t launch_tile_t(qla_ctx *c, const void *in, void *out) {
+    using SC = typename std::conditional<TS, TriC<T>, typename Coef<T>::C>::type;
     constexpr int TX = TileShape<T>::TX, TY = TileShape<T>::TY;
     constexpr int RX = TX + 2 * HALO, RY = TY + 2 * HALO;
-    const size_t smem = size_t(RX) * RY * (sizeof(typename Coef<T>::C) + P * sizeof(T));
-    auto kern = k_step_tile<T, P, VM, VIN>;
+    const size_t smem = size_t(RX) * RY * (sizeof(SC) + P * sizeof(T));
+    auto kern = k_step_tile<T, P, VM, VIN, TS>;
     static bool configured = false;  // per instantiation, per process
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -155,9 +186,18 @@ cudaError_t launch_tile_t(qla_ctx *c, const void *in, void *out) {
     dim3 grid((c->nx + TX - 1) / TX, (c->ny + TY - 1) / TY);
     kern<<<grid, THREADS, smem, c->stream>>>(
         static_cast<const T *>(in), static_cast<T *>(out),
-        c->midx, static_cast<const MedRec<T> *>(c->table), c->nx, c->ny, c->pitch,
-        c->plane_elems);
+        c->midx, static_cast<const MedRec<T> *>(c->table),
+        static_cast<const MedRecT<T> *>(c->ttable), c->nx, c->ny, c->pitch, c->plane_elems);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tensor_vm(qla_ctx *c, const void *in, void *out) {
+    switch (c->vmode) {
+    case V_ROTATION: return launch_tile_t<T, 6, V_ROTATION, false, true>(c, in, out);
+    case V_LITERAL:  return launch_tile_t<T, 6, V_LITERAL, false, true>(c, in, out);
+    default:         return launch_tile_t<T, 6, V_NONE, false, true>(c, in, out);
+    }
 }
 
 template <typename T, int P>
@@ -174,6 +214,11 @@ cudaError_t launch_tile_vm(qla_ctx *c, const void *in, void *out, bool vin) {
 }
 
 }  // namespace
+
+cudaError_t launch_step_tensor(qla_ctx *c, const void *in, void *out) {
+    return c->prec == QLA_FP64 ? launch_tensor_vm<double>(c, in, out)
+                               : launch_tensor_vm<float>(c, in, out);
+}
 
 cudaError_t launch_step_tile(qla_ctx *c, const void *in, void *out, bool vin) {
     if (c->prec == QLA_FP64)

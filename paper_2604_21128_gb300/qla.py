@@ -22,6 +22,7 @@ QLA_FP64, QLA_FP32 = 0, 1
 QLA_TE_ONLY = 1
 QLA_POTENTIAL_LITERAL = 2
 QLA_POTENTIAL_NONE = 4
+QLA_ANISOTROPIC = 8
 QLA_KERNEL_AUTO, QLA_KERNEL_TILE, QLA_KERNEL_MARCH = 0, 1, 2
 
 STATUS = {0: "QLA_OK", 1: "QLA_EINVAL", 2: "QLA_ESTATE", 3: "QLA_ENOMEM",
@@ -58,6 +59,7 @@ def load():
         lib.qla_init_grid.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, ctypes.c_double,
                                       c_int, c_u, c_vp, c_vp, c_sz]
         for name, args in (("qla_set_medium", [c_vp, c_vp]),
+                           ("qla_set_medium_tensor", [c_vp, c_vp, c_vp, c_vp]),
                            ("qla_set_packet", [c_vp, ctypes.POINTER(qla_packet)]),
                            ("qla_set_state", [c_vp, c_vp]),
                            ("qla_get_state", [c_vp, c_vp]),
@@ -173,6 +175,11 @@ def qla_set_medium(ctx, n, nx, ny):
     _check(ctx, load().qla_set_medium(ctx, _host_ptr(n, nx * ny)))
 
 
+def qla_set_medium_tensor(ctx, n_x, n_y, n_z, nx, ny):
+    _check(ctx, load().qla_set_medium_tensor(ctx, _host_ptr(n_x, nx * ny), _host_ptr(n_y, nx * ny),
+                                             _host_ptr(n_z, nx * ny)))
+
+
 def qla_set_packet(ctx, x0, y0, angle, k0, width, transverse_width=0.0, amplitude=1.0):
     p = qla_packet(float(x0), float(y0), float(angle), float(k0), float(width),
                    float(transverse_width), float(amplitude))
@@ -254,19 +261,20 @@ class Grid:
     """One QLA lattice on a CUDA device.
 
     precision: "fp64" or "fp32"; te_only: evolve only q2, q3, q4;
-    potential: "rotation" (default reading), "literal" or "none".
+    potential: "rotation" (default reading), "literal" or "none";
+    tensor: a diagonal index tensor (set_medium with a (3, ny, nx) array).
     The device workspace is a torch uint8 tensor; work is enqueued on
     ``stream`` (default: torch's current stream on the device)."""
 
     def __init__(self, nx, ny, delta=1.0, precision="fp64", te_only=False,
-                 potential="rotation", device=None, stream=None):
+                 potential="rotation", device=None, stream=None, tensor=False):
         import torch
         load()
         if not torch.cuda.is_available():
             raise RuntimeError("libqla needs a CUDA device; none is available")
         self.nx, self.ny, self.delta = int(nx), int(ny), float(delta)
         self.precision = {"fp64": QLA_FP64, "fp32": QLA_FP32}[precision]
-        flags = (QLA_TE_ONLY if te_only else 0) | {
+        flags = (QLA_TE_ONLY if te_only else 0) | (QLA_ANISOTROPIC if tensor else 0) | {
             "rotation": 0, "literal": QLA_POTENTIAL_LITERAL, "none": QLA_POTENTIAL_NONE}[potential]
         self.flags = flags
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
@@ -286,8 +294,14 @@ class Grid:
         return torch.cuda.device(self.device)
 
     def set_medium(self, n):
+        """n: (ny, nx) scalar index, or (3, ny, nx) = (n_x, n_y, n_z) for a
+        context made with tensor=True."""
         with self._dev():
-            qla_set_medium(self._ctx, n, self.nx, self.ny)
+            if getattr(n, "ndim", 2) == 3:
+                a = [np.ascontiguousarray(n[c], dtype=np.float64) for c in range(3)]
+                qla_set_medium_tensor(self._ctx, a[0], a[1], a[2], self.nx, self.ny)
+            else:
+                qla_set_medium(self._ctx, n, self.nx, self.ny)
 
     def set_packet(self, x0, y0, angle, k0, width, transverse_width=0.0, amplitude=1.0):
         with self._dev():
