@@ -30,8 +30,9 @@ from . import build as _build
 V_ROTATION = 0   # default reading: rotation by beta/2 (exactly unitary step)
 V_LITERAL = 1    # printed shear of Eqs. 2e11-2e12 with the two row fixes
 V_NONE = 2       # homogeneous step of Eq. 2e10 (V = I)
+V_LCU = 3        # Eqs. 2f1-2f7: (1/2) sum of the printed unitaries, branch by branch
 
-_VMODES = {"rotation": V_ROTATION, "literal": V_LITERAL, "none": V_NONE}
+_VMODES = {"rotation": V_ROTATION, "literal": V_LITERAL, "none": V_NONE, "lcu": V_LCU}
 
 _lib = None
 

@@ -28,7 +28,9 @@
  *   - V: default "rotation" reading (rotation by beta/2 in the planes that
  *     Eqs. 2d1-2d6 couple), or the printed shear with the q5 row sign taken
  *     from the LCU sum (Eqs. 2f1-2f4) and the q3 row of Eq. 2e12 read as
- *     sin(beta_3) q2 + cos(beta_3) q3, or no V at all (Eq. 2e10).
+ *     sin(beta_3) q2 + cos(beta_3) q3, or no V at all (Eq. 2e10), or the
+ *     linear combination of unitaries of Eqs. 2f1-2f7 emulated branch by
+ *     branch exactly as printed.
  *
  * State layout: six planes q[c][j*nx + i], c = 0..5, i = x index (fastest),
  * j = y index; site (i, j) sits at (i*delta, j*delta); periodic in both axes.
@@ -323,6 +325,76 @@ static void potential_y_rotation(int nx, int ny, double *q, const double *b05,
     pair_rotate(nx, ny, q + 0 * N, q + 5 * N, b05, 0.5, +1.0, -1.0);
 }
 
+/* The linear combination of unitaries of Eqs. 2f1-2f7, emulated branch by
+ * branch: V = (1/2)(L1 + L2 + L3 + L4) with each L applied to the site's
+ * six amplitudes as printed (full angles beta, not halved).  Its sum is the
+ * printed V_x with +sin(beta_0) q1 in the q5 row, and the printed V_y with
+ * the q3 row cos(beta_3) q2 + sin(beta_3) q3 (the printed L_y3, L_y4 carry
+ * that row); no reading is applied here. */
+static void lcu_x_site(double *v, double b0, double b2)
+{
+    const double c0 = cos(b0), s0 = sin(b0), c2 = cos(b2), s2 = sin(b2);
+    double o[6];
+    /* L_x1 = I */
+    for (int r = 0; r < 6; ++r) o[r] = v[r];
+    /* L_x2 (Eq. 2f2) = diag(-1, 1, 1, -1, -1, -1) */
+    o[0] += -v[0]; o[1] += v[1]; o[2] += v[2]; o[3] += -v[3]; o[4] += -v[4]; o[5] += -v[5];
+    /* L_x3 (Eq. 2f3) */
+    o[0] += v[0];
+    o[1] += c0 * v[1] - s0 * v[5];
+    o[2] += c2 * v[2] + s2 * v[4];
+    o[3] += v[3];
+    o[4] += -s2 * v[2] + c2 * v[4];
+    o[5] += s0 * v[1] + c0 * v[5];
+    /* L_x4 (Eq. 2f4) */
+    o[0] += v[0];
+    o[1] += -c0 * v[1] + s0 * v[5];
+    o[2] += -c2 * v[2] - s2 * v[4];
+    o[3] += v[3];
+    o[4] += -s2 * v[2] + c2 * v[4];
+    o[5] += s0 * v[1] + c0 * v[5];
+    for (int r = 0; r < 6; ++r) v[r] = 0.5 * o[r];
+}
+
+static void lcu_y_site(double *v, double b1, double b3)
+{
+    const double c1 = cos(b1), s1 = sin(b1), c3 = cos(b3), s3 = sin(b3);
+    double o[6];
+    /* L_y1 = I */
+    for (int r = 0; r < 6; ++r) o[r] = v[r];
+    /* L_y2 (Eq. 2f5) = diag(1, -1, 1, -1, -1, -1) */
+    o[0] += v[0]; o[1] += -v[1]; o[2] += v[2]; o[3] += -v[3]; o[4] += -v[4]; o[5] += -v[5];
+    /* L_y3 (Eq. 2f6) */
+    o[0] += c1 * v[0] + s1 * v[5];
+    o[1] += v[1];
+    o[2] += -s3 * v[2] + c3 * v[3];
+    o[3] += c3 * v[2] + s3 * v[3];
+    o[4] += v[4];
+    o[5] += -s1 * v[0] + c1 * v[5];
+    /* L_y4 (Eq. 2f7) */
+    o[0] += -c1 * v[0] - s1 * v[5];
+    o[1] += v[1];
+    o[2] += s3 * v[2] - c3 * v[3];
+    o[3] += c3 * v[2] + s3 * v[3];
+    o[4] += v[4];
+    o[5] += -s1 * v[0] + c1 * v[5];
+    for (int r = 0; r < 6; ++r) v[r] = 0.5 * o[r];
+}
+
+static void potential_lcu(int nx, int ny, double *q, const double *b15, const double *b24,
+                          const double *b05, const double *b23)
+{
+    size_t N = (size_t)nx * ny;
+#pragma omp parallel for schedule(static)
+    for (long long k = 0; k < (long long)N; ++k) {
+        double v[6];
+        for (int c = 0; c < 6; ++c) v[c] = q[(size_t)c * N + k];
+        lcu_x_site(v, b15[k], b24[k]);
+        lcu_y_site(v, b05[k], b23[k]);
+        for (int c = 0; c < 6; ++c) q[(size_t)c * N + k] = v[c];
+    }
+}
+
 /* V_x then V_y with the angle planes of orc_angles_aniso (slots 4..7). */
 static void V_pairs(int nx, int ny, double *q, const double *b15, const double *b24,
                     const double *b05, const double *b23, int vmode)
@@ -333,6 +405,8 @@ static void V_pairs(int nx, int ny, double *q, const double *b15, const double *
     } else if (vmode == ORC_V_LITERAL) {
         potential_x_literal(nx, ny, q, b15, b24);
         potential_y_literal(nx, ny, q, b05, b23);
+    } else if (vmode == ORC_V_LCU) {
+        potential_lcu(nx, ny, q, b15, b24, b05, b23);
     }
     /* ORC_V_NONE: V = I, the homogeneous step of Eq. 2e10 */
 }

@@ -13,7 +13,7 @@
 extern "C" {
 #endif
 
-enum { ORC_V_ROTATION = 0, ORC_V_LITERAL = 1, ORC_V_NONE = 2 };
+enum { ORC_V_ROTATION = 0, ORC_V_LITERAL = 1, ORC_V_NONE = 2, ORC_V_LCU = 3 };
 
 void orc_angles(int nx, int ny, double delta, const double *n,
                 double *theta, double *beta_x, double *beta_y);

@@ -105,6 +105,14 @@ def Vy_literal(b1, b3):
     return M
 
 
+def Vy_printed(b1, b3):
+    """Eq. 2e12 exactly as printed, q3 row cos(b3) q2 + sin(b3) q3 included."""
+    M = np.eye(6)
+    M[3, 2], M[3, 3] = np.cos(b3), np.sin(b3)
+    M[5, 0], M[5, 5] = -np.sin(b1), np.cos(b1)
+    return M
+
+
 def medium_angles(n, delta):
     """Eq. 2e4 and Eq. 2e13 with the centred periodic difference."""
     theta = delta / (4 * n)
@@ -148,14 +156,17 @@ def assemble_step_tensor(nxyz, delta, vmode):
           @ S25ym @ Cy @ S25yp @ Cyd @ S03p @ Cy @ S03m @ Cyd)
     if vmode == "none":
         return Uy @ Ux
-    Vxf, Vyf = (Vx_rotation, Vy_rotation) if vmode == "rotation" else (Vx_literal, Vy_literal)
+    # the LCU sum of Eqs. 2f1-2f7 equals the printed V_x (q5 row with
+    # +sin(beta_0), which the literal reading adopts) and the printed V_y
+    Vxf, Vyf = {"rotation": (Vx_rotation, Vy_rotation), "literal": (Vx_literal, Vy_literal),
+                "lcu": (Vx_literal, Vy_printed)}[vmode]
     Vx = local_op([Vxf(a["b0"][k], a["b2"][k]) for k in range(N)])
     Vy = local_op([Vyf(a["b1"][k], a["b3"][k]) for k in range(N)])
     # Eq. 2e14
     return Vy @ Vx @ Uy @ Ux
 
 
-@pytest.mark.parametrize("vmode", ["rotation", "literal", "none"])
+@pytest.mark.parametrize("vmode", ["rotation", "literal", "none", "lcu"])
 @pytest.mark.parametrize("delta", [1.0, 0.5])
 def test_step_matches_assembled_matrix(vmode, delta):
     n = inputs.random_medium(NX, NY, seed=7, lo=1.0, hi=3.0, smooth=1)
@@ -224,3 +235,22 @@ def test_anisotropic_entry_with_equal_indices_is_the_isotropic_step():
         iso = oracle.run(q, n, 1.0, 3, vmode)
         ani = oracle.run(q, np.stack([n, n, n.copy()]), 1.0, 3, vmode)
         assert np.array_equal(iso, ani)
+
+
+def test_lcu_branches_sum_to_the_printed_potentials():
+    """Eq. 2f1: (1/2)(L1 + L2 + L3 + L4) = V.  The oracle's branch-by-branch
+    emulation of Eqs. 2f2-2f7 against Eq. 2e11 (with the +sin(beta_0) q5
+    row the LCU implies) and Eq. 2e12 as printed, site by site, on random
+    states and large angles (so that a wrong entry in any branch shows)."""
+    rng = np.random.default_rng(41)
+    q = rng.standard_normal((6, 5, 7))
+    bx, by = rng.uniform(-1.2, 1.2, (5, 7)), rng.uniform(-1.2, 1.2, (5, 7))
+    got = oracle.V(q, bx, by, "lcu")
+    for j in range(5):
+        for i in range(7):
+            want = Vy_printed(by[j, i], by[j, i]) @ Vx_literal(bx[j, i], bx[j, i]) @ q[:, j, i]
+            assert np.max(np.abs(got[:, j, i] - want)) < 1e-14
+    # the printed q3 row makes the (q2, q3) block singular where beta_3 = 0:
+    # wherever d_y n = 0 it overwrites B_x with n E_z
+    assert np.linalg.det(Vy_printed(0.3, 0.0)[2:4, 2:4]) == 0.0
+    assert np.allclose(oracle.V(q, 0 * bx, 0 * by, "lcu")[3], q[2])
