@@ -70,7 +70,18 @@ enum {
      * per-site record) so that qla_set_medium_tensor can give every pair its
      * own angle.  E_z contexts (QLA_TE_ONLY) see n_z only and keep every step
      * kernel; six-plane contexts step with the tile kernel. */
-    QLA_ANISOTROPIC = 8u
+    QLA_ANISOTROPIC = 8u,
+    /* Potential operators as the paper's linear combination of unitaries
+     * (Eqs. 2f1-2f7), emulated branch by branch: each site's amplitudes are
+     * sent through the four printed matrices L_1..L_4 (full angles beta) and
+     * the results summed and halved.  The sum is the printed V_x (with the
+     * +sin(beta_0) q5 row) and the printed V_y, whose q3 row
+     * cos(beta_3) q2 + sin(beta_3) q3 overwrites B_x with n E_z wherever
+     * d_y n = 0: the scheme is then unstable (the oracle's energy grows by
+     * ~1e87 over 400 steps of the 256^2 ellipse workload).  For measuring
+     * that, not for physics.  Excludes the two flags above; stepped by the
+     * tile kernel with V applied within each launch. */
+    QLA_POTENTIAL_LCU = 16u
 };
 
 /* E_z-polarised Gaussian packet (Sec. V-B): with

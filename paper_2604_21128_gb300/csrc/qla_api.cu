@@ -118,9 +118,12 @@ qla_status qla_init_grid(qla_ctx **out, int nx, int ny, double delta, int precis
     if (nx < 1 || ny < 1 || !(delta > 0.0) || !std::isfinite(delta)) return QLA_EINVAL;
     if (precision != QLA_FP64 && precision != QLA_FP32) return QLA_EINVAL;
     if (flags & ~(unsigned)(QLA_TE_ONLY | QLA_POTENTIAL_LITERAL | QLA_POTENTIAL_NONE |
-                            QLA_ANISOTROPIC))
+                            QLA_ANISOTROPIC | QLA_POTENTIAL_LCU))
         return QLA_EINVAL;
-    if ((flags & QLA_POTENTIAL_LITERAL) && (flags & QLA_POTENTIAL_NONE)) return QLA_EINVAL;
+    {
+        const unsigned v = flags & (QLA_POTENTIAL_LITERAL | QLA_POTENTIAL_NONE | QLA_POTENTIAL_LCU);
+        if (v & (v - 1)) return QLA_EINVAL;  // at most one potential reading
+    }
     if (size_t(nx) * size_t(ny) > (size_t(1) << 34)) return QLA_EINVAL;
     if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255)) return QLA_EINVAL;
 
@@ -134,6 +137,7 @@ qla_status qla_init_grid(qla_ctx **out, int nx, int ny, double delta, int precis
     c->P = (flags & QLA_TE_ONLY) ? 3 : 6;
     c->vmode = (flags & QLA_POTENTIAL_LITERAL) ? V_LITERAL
              : (flags & QLA_POTENTIAL_NONE)    ? V_NONE
+             : (flags & QLA_POTENTIAL_LCU)     ? V_LCU
                                                : V_ROTATION;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return QLA_ECUDA; }
@@ -339,10 +343,13 @@ qla_status qla_step(qla_ctx *c, long long n_steps) {
         return fail(c, QLA_ESTATE, "qla_step: set a medium and a state first");
     DeviceGuard dg(c->device);
     if (!dg.ok) return fail(c, QLA_ECUDA, "qla_step: cannot select device");
-    if (c->tensor && c->P == 6) {
-        // every pair with its own angle; V applied in the same launch
+    if ((c->tensor && c->P == 6) || c->vmode == V_LCU) {
+        // the tile kernel with this step's V applied in the same launch:
+        // every pair with its own angle, or the LCU branches
         for (long long k = 0; k < n_steps; ++k) {
-            QLA_CUDA(c, launch_step_tensor(c, c->state[c->cur], c->state[c->cur ^ 1]),
+            QLA_CUDA(c, c->tensor && c->P == 6
+                            ? launch_step_tensor(c, c->state[c->cur], c->state[c->cur ^ 1])
+                            : launch_step_tile(c, c->state[c->cur], c->state[c->cur ^ 1], false),
                      "qla_step: kernel");
             c->launches++;
             c->cur ^= 1;
@@ -457,9 +464,9 @@ qla_status qla_set_step_kernel(qla_ctx *c, int kernel) {
     if (s != QLA_OK) return s;
     if (kernel < QLA_KERNEL_AUTO || kernel > QLA_KERNEL_MARCH)
         return fail(c, QLA_EINVAL, "qla_set_step_kernel: unknown kernel %d", kernel);
-    if (kernel == QLA_KERNEL_MARCH && c->tensor && c->P == 6)
-        return fail(c, QLA_EINVAL, "qla_set_step_kernel: six-plane tensor media use the tile "
-                                   "kernel");
+    if (kernel == QLA_KERNEL_MARCH && ((c->tensor && c->P == 6) || c->vmode == V_LCU))
+        return fail(c, QLA_EINVAL, "qla_set_step_kernel: six-plane tensor media and the LCU "
+                                   "potential use the tile kernel");
     if (kernel == QLA_KERNEL_MARCH && !march_supported(c))
         return fail(c, QLA_EINVAL, "qla_set_step_kernel: the marching kernel needs nx a multiple "
                                    "of its lane width, nx >= 32 lane widths and ny >= 8");

@@ -427,6 +427,7 @@ extern "C" {
 size_t qla_batch_workspace_bytes(int count, const int *nx, const int *ny, int precision,
                                  unsigned flags) {
     if (count < 1 || !nx || !ny) return 0;
+    if (flags & (QLA_ANISOTROPIC | QLA_POTENTIAL_LCU)) return 0;  // single contexts only
     size_t total = 0;
     for (int k = 0; k < count; ++k) {
         if (!lattice_ok(nx[k], ny[k])) return 0;

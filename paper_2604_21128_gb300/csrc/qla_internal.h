@@ -125,7 +125,41 @@ __device__ __forceinline__ void shear1(double x, double &y, double c, double s, 
     y = fma(c, y, g * s * x);
 }
 
-enum VMode { V_ROTATION = 0, V_LITERAL = 1, V_NONE = 2 };
+enum VMode { V_ROTATION = 0, V_LITERAL = 1, V_NONE = 2, V_LCU = 3 };
+
+// Cosine and sine of a potential angle from a CoefV entry pair: FP64 stores
+// (cos, sin), FP32 (gamma = 1 - cos, sin).
+__device__ __forceinline__ void cos_sin(double a, double b, double &c, double &s) { c = a; s = b; }
+__device__ __forceinline__ void cos_sin(float a, float b, float &c, float &s) { c = 1.0f - a; s = b; }
+
+// Eqs. 2f1-2f7: V = (1/2)(L1 + L2 + L3 + L4), each printed L applied to the
+// six amplitudes and the four results summed row by row, then halved.
+// (c0, s0), (c2, s2): V_x angles beta_0 (q1, q5) and beta_2 (q2, q4);
+// (c1, s1), (c3, s3): V_y angles beta_1 (q0, q5) and beta_3 (q2, q3).
+template <typename T>
+__device__ __forceinline__ void lcu_x(T (&v)[6], T c0, T s0, T c2, T s2) {
+    T o[6];
+    o[0] = v[0] - v[0] + v[0] + v[0];
+    o[1] = v[1] + v[1] + (c0 * v[1] - s0 * v[5]) + (-c0 * v[1] + s0 * v[5]);
+    o[2] = v[2] + v[2] + (c2 * v[2] + s2 * v[4]) + (-c2 * v[2] - s2 * v[4]);
+    o[3] = v[3] - v[3] + v[3] + v[3];
+    o[4] = v[4] - v[4] + (-s2 * v[2] + c2 * v[4]) + (-s2 * v[2] + c2 * v[4]);
+    o[5] = v[5] - v[5] + (s0 * v[1] + c0 * v[5]) + (s0 * v[1] + c0 * v[5]);
+#pragma unroll
+    for (int r = 0; r < 6; ++r) v[r] = T(0.5) * o[r];
+}
+template <typename T>
+__device__ __forceinline__ void lcu_y(T (&v)[6], T c1, T s1, T c3, T s3) {
+    T o[6];
+    o[0] = v[0] + v[0] + (c1 * v[0] + s1 * v[5]) + (-c1 * v[0] - s1 * v[5]);
+    o[1] = v[1] - v[1] + v[1] + v[1];
+    o[2] = v[2] + v[2] + (-s3 * v[2] + c3 * v[3]) + (s3 * v[2] - c3 * v[3]);
+    o[3] = v[3] - v[3] + (c3 * v[2] + s3 * v[3]) + (c3 * v[2] + s3 * v[3]);
+    o[4] = v[4] - v[4] + v[4] + v[4];
+    o[5] = v[5] - v[5] + (-s1 * v[0] + c1 * v[5]) + (-s1 * v[0] + c1 * v[5]);
+#pragma unroll
+    for (int r = 0; r < 6; ++r) v[r] = T(0.5) * o[r];
+}
 
 // Potential operators at one site: V_x then V_y (Eq. 2e14).  q[] holds the
 // six amplitudes (entries absent in E_z mode are ignored).  kv = CoefV.
@@ -145,6 +179,12 @@ __device__ __forceinline__ void apply_potential(T (&q)[6], KV kv) {
         // V_y: q3 <- sin q2 + cos q3; q5 <- -sin q0 + cos q5
         shear1(q[2], q[3], kv.z, kv.w, T(1));
         if constexpr (P == 6) shear1(q[0], q[5], kv.z, kv.w, T(-1));
+    } else if constexpr (VM == V_LCU) {
+        T cx, sx, cy, sy;
+        cos_sin(kv.x, kv.y, cx, sx);
+        cos_sin(kv.z, kv.w, cy, sy);
+        lcu_x(q, cx, sx, cx, sx);
+        lcu_y(q, cy, sy, cy, sy);
     }
 }
 
@@ -174,6 +214,14 @@ __device__ __forceinline__ void apply_potential_tensor(T (&q)[6], KV kz, KV kt) 
         if constexpr (P == 6) shear1(q[1], q[5], kt.x, kt.y, T(1));
         shear1(q[2], q[3], kz.z, kz.w, T(1));
         if constexpr (P == 6) shear1(q[0], q[5], kt.z, kt.w, T(-1));
+    } else if constexpr (VM == V_LCU) {
+        T c0, s0, c1, s1, c2, s2, c3, s3;
+        cos_sin(kt.x, kt.y, c0, s0);
+        cos_sin(kz.x, kz.y, c2, s2);
+        cos_sin(kt.z, kt.w, c1, s1);
+        cos_sin(kz.z, kz.w, c3, s3);
+        lcu_x(q, c0, s0, c2, s2);
+        lcu_y(q, c1, s1, c3, s3);
     }
 }
 

@@ -154,7 +154,8 @@ int march_lane_cols(const qla_ctx *c) {
 bool march_supported(const qla_ctx *c) {
     const int lx = march_lane_cols(c);
     return c->nx % lx == 0 && c->nx >= 32 * lx && c->ny >= 8 &&
-           c->plane_elems < (size_t(1) << 31) && !(c->tensor && c->P == 6);
+           c->plane_elems < (size_t(1) << 31) && !(c->tensor && c->P == 6) &&
+           c->vmode != V_LCU;
 }
 
 cudaError_t launch_step_march(qla_ctx *c, const void *in, void *out, bool vin) {

@@ -11,7 +11,8 @@
 // no output depends on.  The previous step's V_x, V_y (when pending) are
 // applied to every staged site on load; the buffer written holds U_y U_x Q.
 // For a diagonal index tensor (six planes) the kernel stages a coefficient
-// per pair class and applies this step's V before storing instead.
+// per pair class and applies this step's V before storing instead; so it
+// does for the LCU form of V (Eqs. 2f1-2f7).
 #include <type_traits>
 
 #include "qla_internal.h"
@@ -160,6 +161,8 @@ k_step_tile(const T *__restrict__ in, T *__restrict__ out,
         if constexpr (TS) {
             const MedRecT<T> &r = ttable[g];
             apply_potential_tensor<T, P, VM>(q, r.vz, r.vt);   // V_y V_x (Eq. 2e14)
+        } else if constexpr (VM == V_LCU) {
+            apply_potential<T, P, VM>(q, table[midx[g]].v);     // Eqs. 2f1-2f7
         }
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
@@ -196,6 +199,7 @@ cudaError_t launch_tensor_vm(qla_ctx *c, const void *in, void *out) {
     switch (c->vmode) {
     case V_ROTATION: return launch_tile_t<T, 6, V_ROTATION, false, true>(c, in, out);
     case V_LITERAL:  return launch_tile_t<T, 6, V_LITERAL, false, true>(c, in, out);
+    case V_LCU:      return launch_tile_t<T, 6, V_LCU, false, true>(c, in, out);
     default:         return launch_tile_t<T, 6, V_NONE, false, true>(c, in, out);
     }
 }
@@ -209,6 +213,7 @@ cudaError_t launch_tile_vm(qla_ctx *c, const void *in, void *out, bool vin) {
     case V_LITERAL:
         return vin ? launch_tile_t<T, P, V_LITERAL, true>(c, in, out)
                    : launch_tile_t<T, P, V_LITERAL, false>(c, in, out);
+    case V_LCU: return launch_tile_t<T, P, V_LCU, false>(c, in, out);   // V applied at the end
     default: return launch_tile_t<T, P, V_NONE, false>(c, in, out);
     }
 }

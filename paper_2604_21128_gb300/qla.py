@@ -23,6 +23,7 @@ QLA_TE_ONLY = 1
 QLA_POTENTIAL_LITERAL = 2
 QLA_POTENTIAL_NONE = 4
 QLA_ANISOTROPIC = 8
+QLA_POTENTIAL_LCU = 16
 QLA_KERNEL_AUTO, QLA_KERNEL_TILE, QLA_KERNEL_MARCH = 0, 1, 2
 
 STATUS = {0: "QLA_OK", 1: "QLA_EINVAL", 2: "QLA_ESTATE", 3: "QLA_ENOMEM",
@@ -261,7 +262,7 @@ class Grid:
     """One QLA lattice on a CUDA device.
 
     precision: "fp64" or "fp32"; te_only: evolve only q2, q3, q4;
-    potential: "rotation" (default reading), "literal" or "none";
+    potential: "rotation" (default reading), "literal", "none" or "lcu";
     tensor: a diagonal index tensor (set_medium with a (3, ny, nx) array).
     The device workspace is a torch uint8 tensor; work is enqueued on
     ``stream`` (default: torch's current stream on the device)."""
@@ -275,7 +276,8 @@ class Grid:
         self.nx, self.ny, self.delta = int(nx), int(ny), float(delta)
         self.precision = {"fp64": QLA_FP64, "fp32": QLA_FP32}[precision]
         flags = (QLA_TE_ONLY if te_only else 0) | (QLA_ANISOTROPIC if tensor else 0) | {
-            "rotation": 0, "literal": QLA_POTENTIAL_LITERAL, "none": QLA_POTENTIAL_NONE}[potential]
+            "rotation": 0, "literal": QLA_POTENTIAL_LITERAL, "none": QLA_POTENTIAL_NONE,
+            "lcu": QLA_POTENTIAL_LCU}[potential]
         self.flags = flags
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
                                    else (device if isinstance(device, int) else device.index or 0))
