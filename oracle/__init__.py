@@ -62,6 +62,8 @@ def _load():
         lib.orc_angles_aniso.argtypes = [i, i, d, dp, dp, dp, dp]
         lib.orc_run_aniso.argtypes = [i, i, d, dp, dp, dp, dp, ll, i]
         lib.orc_run_aniso.restype = i
+        lib.orc3_run.argtypes = [i, i, i, d, dp, dp, ll, i]
+        lib.orc3_run.restype = i
         lib.orc_packet.argtypes = [i, i, d, i, i, i, i, dp, d, d, d, d, d, d, d, dp]
         lib.orc_set_threads.argtypes = [i]
         lib.orc_get_threads.restype = i
@@ -167,6 +169,21 @@ def run(q, n, delta, steps, vmode="rotation"):
                                    int(steps), _vmode(vmode))
     if rc != 0:
         raise MemoryError("oracle allocation failed")
+    return q
+
+
+def run3(q, n, delta, steps, vmode="rotation"):
+    """Three dimensions: q (6, nz, ny, nx), n (nz, ny, nx); the step
+    V_z V_y V_x U_z U_y U_x (Eq. 2e14 extended along z with the couplings of
+    Eq. 3b4).  Readings "rotation" and "none" only."""
+    q = np.ascontiguousarray(q, dtype=np.float64).copy()
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    if q.ndim != 4 or q.shape[0] != 6 or n.shape != q.shape[1:]:
+        raise ValueError("q must be (6, nz, ny, nx) and n (nz, ny, nx)")
+    nz, ny, nx = n.shape
+    rc = _load().orc3_run(nx, ny, nz, float(delta), _ptr(n), _ptr(q), int(steps), _vmode(vmode))
+    if rc != 0:
+        raise ValueError("orc3_run failed (reading not available in 3D, or no memory)")
     return q
 
 

@@ -471,6 +471,119 @@ int orc_run(int nx, int ny, double delta, const double *n, double *q,
 }
 
 /* ------------------------------------------------------------------ */
+/* Three dimensions (Sec. III, Eq. 3b4)                                */
+/* ------------------------------------------------------------------ */
+
+/* The paper runs its scaling tests in 3D but prints only the x and y
+ * sequences.  Eq. 3b4 (with i dQ/dt = W^-1/2 M W^-1/2 Q) gives the z
+ * couplings of an isotropic n:
+ *   dq0/dt = -(1/n) d_z q4,   dq4/dt = -d_z (q0/n)    (like (q1, q5) along x)
+ *   dq1/dt = +(1/n) d_z q3,   dq3/dt = +d_z (q1/n)    (like (q2, q4) along x)
+ * so the z step is the x construction with q1 -> q0, q5 -> q4, q2 -> q1,
+ * q4 -> q3: C_z rotates (q0, q4) and (q1, q3) with the sign pattern of C_x,
+ * the first streamed pair is S03 (q0 and q3), the second S14 (q1 and q4),
+ * in the order of Eq. 2e6; V_z rotates (q1, q3) like (q2, q4) and (q0, q4)
+ * like (q1, q5) by beta_z / 2, beta_z = delta^2 (d_z n) / n^2.  The full
+ * step extends Eq. 2e14: Q <- V_z V_y V_x U_z U_y U_x Q.  (A reading; the
+ * tests pin it to Eq. 3b4 through the generator fit.)
+ * Layout: q[c][(k * ny + j) * nx + i], k = z index; periodic in all axes. */
+
+#define SITE3(i, j, k) (((size_t)(k) * (size_t)ny + (size_t)(j)) * (size_t)nx + (size_t)(i))
+
+static void shift3(int nx, int ny, int nz, double *p, int axis, int sign, double *tmp)
+{
+    size_t N = (size_t)nx * ny * nz;
+    memcpy(tmp, p, N * sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int si = i, sj = j, sk = k;
+                if (axis == 0)      si = ((i + sign) % nx + nx) % nx;
+                else if (axis == 1) sj = ((j + sign) % ny + ny) % ny;
+                else                sk = ((k + sign) % nz + nz) % nz;
+                p[SITE3(i, j, k)] = tmp[SITE3(si, sj, sk)];
+            }
+}
+
+static void collide3(int nx, int ny, int nz, double *q, const double *theta, int axis,
+                     int dagger)
+{
+    size_t N = (size_t)nx * ny * nz;
+    /* all three collisions are site-local: a 2D pass over N sites */
+    if (axis == 0) {
+        collide_x_pairs((int)N, 1, q, theta, theta, dagger);
+    } else if (axis == 1) {
+        collide_y_pairs((int)N, 1, q, theta, theta, dagger);
+    } else {
+        double sa = dagger ? +1.0 : -1.0, sb = -sa;     /* the sign pattern of C_x */
+        pair_rotate((int)N, 1, q + 0 * N, q + 4 * N, theta, 1.0, sa, sb);
+        pair_rotate((int)N, 1, q + 1 * N, q + 3 * N, theta, 1.0, sa, sb);
+    }
+}
+
+static void U3(int nx, int ny, int nz, double *q, const double *theta, int axis, double *tmp)
+{
+    size_t N = (size_t)nx * ny * nz;
+    /* first and second streamed pairs: x (q1,q4),(q2,q5); y (q0,q3),(q2,q5);
+     * z (q0,q3),(q1,q4) */
+    int f_a = axis == 0 ? 1 : 0, f_b = axis == 0 ? 4 : 3;
+    int s_a = axis == 2 ? 1 : 2, s_b = axis == 2 ? 4 : 5;
+    for (int k = 0; k < 16; ++k) {
+        int op = U_SEQUENCE[k];
+        if (op == OP_C || op == OP_CDAG) {
+            collide3(nx, ny, nz, q, theta, axis, op == OP_CDAG);
+            continue;
+        }
+        int first = op == OP_S1P || op == OP_S1M;
+        int sign = (op == OP_S1P || op == OP_S2P) ? +1 : -1;
+        int a = first ? f_a : s_a, b = first ? f_b : s_b;
+        shift3(nx, ny, nz, q + (size_t)a * N, axis, sign, tmp);
+        shift3(nx, ny, nz, q + (size_t)b * N, axis, sign, tmp);
+    }
+}
+
+int orc3_run(int nx, int ny, int nz, double delta, const double *n, double *q,
+             long long steps, int vmode)
+{
+    size_t N = (size_t)nx * ny * nz;
+    double *theta = malloc(N * sizeof(double));
+    double *b = malloc(3 * N * sizeof(double));
+    double *tmp = malloc(N * sizeof(double));
+    if (!theta || !b || !tmp || (vmode != ORC_V_ROTATION && vmode != ORC_V_NONE)) {
+        free(theta); free(b); free(tmp);
+        return -1;
+    }
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t s = SITE3(i, j, k);
+                double nn = n[s];
+                double dx = (n[SITE3((i + 1) % nx, j, k)] - n[SITE3((i + nx - 1) % nx, j, k)]) / (2.0 * delta);
+                double dy = (n[SITE3(i, (j + 1) % ny, k)] - n[SITE3(i, (j + ny - 1) % ny, k)]) / (2.0 * delta);
+                double dz = (n[SITE3(i, j, (k + 1) % nz)] - n[SITE3(i, j, (k + nz - 1) % nz)]) / (2.0 * delta);
+                theta[s] = delta / (4.0 * nn);
+                b[s] = dx / (nn * nn) * delta * delta;
+                b[N + s] = dy / (nn * nn) * delta * delta;
+                b[2 * N + s] = dz / (nn * nn) * delta * delta;
+            }
+    for (long long t = 0; t < steps; ++t) {
+        U3(nx, ny, nz, q, theta, 0, tmp);
+        U3(nx, ny, nz, q, theta, 1, tmp);
+        U3(nx, ny, nz, q, theta, 2, tmp);
+        if (vmode == ORC_V_ROTATION) {
+            potential_x_rotation((int)N, 1, q, b, b);
+            potential_y_rotation((int)N, 1, q, b + N, b + N);
+            pair_rotate((int)N, 1, q + 1 * N, q + 3 * N, b + 2 * N, 0.5, +1.0, -1.0);
+            pair_rotate((int)N, 1, q + 0 * N, q + 4 * N, b + 2 * N, 0.5, -1.0, +1.0);
+        }
+    }
+    free(theta); free(b); free(tmp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Energy (Eq. A13), fields (inverse of Eq. 3b3), initial packet       */
 /* ------------------------------------------------------------------ */
 
