@@ -391,6 +391,58 @@ qla_status surr_weight_grad_raw(const void *dz_bf16, const void *in_bf16, int B,
                                 int cout, int cin, int splits, float *part, float *dw_f32,
                                 void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Three dimensions.  The paper runs its scaling tests with a 3D code whose z
+ * sequence it does not print; Eq. 3b4 (i dQ/dt = W^-1/2 M W^-1/2 Q) fixes
+ * the z couplings of an isotropic n:
+ *   dq0/dt = -(1/n) d_z q4,  dq4/dt = -d_z(q0/n);  dq1/dt = (1/n) d_z q3,
+ *   dq3/dt = d_z(q1/n)
+ * so U_z is the construction of Eq. 2e6 with C_z rotating (q0, q4) and
+ * (q1, q3) by +theta (the sign pattern of C_x), S03 (q0, q3) as the first
+ * and S14 (q1, q4) as the second streamed pair; V_z rotates (q1, q3) and
+ * (q0, q4) by beta_z / 2 (beta_z = delta^2 d_z n / n^2) as V_x rotates
+ * (q2, q4) and (q1, q5); the step is Q <- V_z V_y V_x U_z U_y U_x Q.
+ * All six planes evolve (the E_z triple does not decouple in 3D).
+ * Lattice nx x ny x nz, periodic, site (i, j, k) at host index
+ * (k * ny + j) * nx + i; ny, nz <= 65535.  Flags: 0 (rotation reading) or
+ * QLA_POTENTIAL_NONE; others give QLA_EINVAL.  Same status conventions and
+ * stream semantics as the 2D context.
+ * ------------------------------------------------------------------------ */
+typedef struct qla3_ctx qla3_ctx;
+
+/* Device workspace bytes for a 3D context; 0 for invalid arguments. */
+size_t qla3_workspace_bytes(int nx, int ny, int nz, int precision, unsigned flags);
+
+/* Create a 3D context; workspace as for qla_init_grid (256-byte aligned,
+ * caller-owned, or NULL to let the library allocate it). */
+qla_status qla3_init(qla3_ctx **out, int nx, int ny, int nz, double delta, int precision,
+                     unsigned flags, void *cuda_stream, void *workspace,
+                     size_t workspace_bytes);
+
+/* Medium n(x, y, z): nx*ny*nz FP64 host values, finite and > 0, copied
+ * before return; theta = delta/(4n) and beta_x, beta_y, beta_z by centred
+ * periodic differences (Eqs. 2e4, 2e13 extended to z).  Synchronises. */
+qla_status qla3_set_medium(qla3_ctx *ctx, const double *n_host);
+
+/* Raw Dyson amplitudes in or out: one host array of 6 * nx*ny*nz FP64
+ * values, plane c at offset c * nx*ny*nz (caller-owned; finite on input).
+ * Synchronise. */
+qla_status qla3_set_state(qla3_ctx *ctx, const double *q_host);
+qla_status qla3_get_state(qla3_ctx *ctx, double *q_host);
+
+/* Advance n_steps steps (each three passes: U_x, U_y, then U_z followed by
+ * V_x V_y V_z); asynchronous on the context's stream.  QLA_ESTATE without
+ * medium and state. */
+qla_status qla3_step(qla3_ctx *ctx, long long n_steps);
+
+/* Sum of q^2 over sites and planes (Eq. A13 without the cell volume),
+ * FP64.  Synchronises; QLA_ENONFINITE if not finite. */
+qla_status qla3_energy(qla3_ctx *ctx, double *out);
+
+long long qla3_launch_count(const qla3_ctx *ctx);
+const char *qla3_last_error(const qla3_ctx *ctx);
+void qla3_destroy(qla3_ctx *ctx);
+
 /* Kernel launches enqueued by this context since creation (diagnostics). */
 long long qla_launch_count(const qla_ctx *ctx);
 

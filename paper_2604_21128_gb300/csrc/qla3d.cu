@@ -1,0 +1,496 @@
+// Three-dimensional QLA step: Q <- V_z V_y V_x U_z U_y U_x Q, with U_z and
+// V_z read off Eq. 3b4 (see include/qla.h).  One step is three launches,
+// one per axis: a CTA stages 32 lines x 40 cells along the active axis (32
+// outputs and a 4-cell periodic halo on each side, the reach of U) of all
+// six planes and of the collision coefficients in shared memory, applies
+// the eight bond layers of that axis's U (the layer form of Eq. 2e6, see
+// layer_of), and writes the 32 inner cells of each line; the z pass then
+// applies V_x, V_y, V_z to its outputs.  Three passes read and write the
+// state three times per step: the simple form of the 3D path.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "qla_internal.h"
+
+namespace qla {
+namespace {
+
+constexpr int SEG = 32, HALO3 = 4, AX = SEG + 2 * HALO3, TB = 32, THREADS3 = 256;
+
+// Pairs rotated by the collision of each axis: (a, b, a is the first-type
+// mover).  x: Eq. 2e3, y: Eq. 2e8, z: the reading of Eq. 3b4.
+__host__ __device__ constexpr Pair pair3_of(int axis, int k) {
+    return axis == 0 ? (k == 0 ? Pair{1, 5, true} : Pair{2, 4, false})
+         : axis == 1 ? (k == 0 ? Pair{0, 5, true} : Pair{2, 3, false})
+                     : (k == 0 ? Pair{0, 4, true} : Pair{1, 3, false});
+}
+
+// Potential coefficients of one site for x, y, z, in the CoefV convention
+// (FP64 (cos, sin), FP32 (gamma = 1 - cos, sin)).
+template <typename T> struct V3 { T gx, sx, gy, sy, gz, sz; };
+
+__device__ __forceinline__ void coef_c(double th, double2 &k) {
+    double s, c;
+    sincos(th, &s, &c);
+    k = make_double2(c, s);
+}
+__device__ __forceinline__ void split2(double v, float &hi, float &lo) {
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(v - double(hi));
+}
+__device__ __forceinline__ void coef_c(double th, float4 &k) {
+    double s, c;
+    sincos(th, &s, &c);
+    split2(c, k.x, k.z);
+    split2(s, k.y, k.w);
+}
+__device__ __forceinline__ void coef_v(double ph, double &g, double &s) {
+    g = cos(ph);
+    s = sin(ph);
+}
+__device__ __forceinline__ void coef_v(double ph, float &g, float &s) {
+    const double h = sin(0.5 * ph);
+    g = __double2float_rn(2.0 * h * h);
+    s = __double2float_rn(sin(ph));
+}
+
+__host__ __device__ inline size_t at3(int x, int y, int z, int ny, int pitch) {
+    return (size_t(z) * ny + y) * size_t(pitch) + x;
+}
+
+template <typename T>
+__global__ void k3_medium(const double *__restrict__ n, int nx, int ny, int nz, int pitch,
+                          double delta, double vscale, typename Coef<T>::C *__restrict__ kc,
+                          V3<T> *__restrict__ kv) {
+    const size_t N = size_t(nx) * ny * nz;
+    for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < N;
+         t += size_t(gridDim.x) * blockDim.x) {
+        const int x = int(t % nx), y = int((t / nx) % ny), z = int(t / (size_t(nx) * ny));
+        const size_t g = at3(x, y, z, ny, pitch);
+        const double nn = n[g];
+        const double bx = (n[at3(wrap(x + 1, nx), y, z, ny, pitch)] -
+                           n[at3(wrap(x - 1, nx), y, z, ny, pitch)]) /
+                          (2.0 * delta) / (nn * nn) * delta * delta;
+        const double by = (n[at3(x, wrap(y + 1, ny), z, ny, pitch)] -
+                           n[at3(x, wrap(y - 1, ny), z, ny, pitch)]) /
+                          (2.0 * delta) / (nn * nn) * delta * delta;
+        const double bz = (n[at3(x, y, wrap(z + 1, nz), ny, pitch)] -
+                           n[at3(x, y, wrap(z - 1, nz), ny, pitch)]) /
+                          (2.0 * delta) / (nn * nn) * delta * delta;
+        typename Coef<T>::C c;
+        coef_c(delta / (4.0 * nn), c);
+        kc[g] = c;
+        V3<T> v;
+        coef_v(vscale * bx, v.gx, v.sx);
+        coef_v(vscale * by, v.gy, v.sy);
+        coef_v(vscale * bz, v.gz, v.sz);
+        kv[g] = v;
+    }
+}
+
+// Global coordinates of staged cell (a along the axis, b across it) of the
+// CTA's tile; false if the line lies outside the lattice.
+template <int AXIS>
+__device__ __forceinline__ bool cell(int a, int b, int nx, int ny, int nz, int &x, int &y,
+                                     int &z) {
+    if constexpr (AXIS == 0) {
+        x = wrap(int(blockIdx.x) * SEG - HALO3 + a, nx);
+        y = int(blockIdx.y) * TB + b;
+        z = int(blockIdx.z);
+        return y < ny;
+    } else if constexpr (AXIS == 1) {
+        x = int(blockIdx.x) * TB + b;
+        y = wrap(int(blockIdx.y) * SEG - HALO3 + a, ny);
+        z = int(blockIdx.z);
+        return x < nx;
+    } else {
+        x = int(blockIdx.x) * TB + b;
+        y = int(blockIdx.z);
+        z = wrap(int(blockIdx.y) * SEG - HALO3 + a, nz);
+        return x < nx;
+    }
+}
+
+// Shared-memory row stride: the x pass stages lines along x, and one
+// padding column keeps its column-wise accesses off a single bank.
+template <int AXIS> constexpr int LD = AXIS == 0 ? TB + 1 : TB;
+
+template <typename T, int AXIS, bool VEND, int VM>
+__global__ void __launch_bounds__(THREADS3)
+k3_pass(const T *__restrict__ in, T *__restrict__ out, const typename Coef<T>::C *__restrict__ kc,
+        const V3<T> *__restrict__ kv, int nx, int ny, int nz, int pitch, size_t plane_elems) {
+    using CC = typename Coef<T>::C;
+    constexpr int ld = LD<AXIS>, cells = AX * ld;
+    extern __shared__ __align__(16) unsigned char smem3[];
+    CC *sc = reinterpret_cast<CC *>(smem3);
+    T *s = reinterpret_cast<T *>(sc + cells);
+    // stage: consecutive threads take consecutive x
+    for (int t = threadIdx.x; t < AX * TB; t += THREADS3) {
+        const int a = AXIS == 0 ? t % AX : t / TB, b = AXIS == 0 ? t / AX : t % TB;
+        int x, y, z;
+        if (!cell<AXIS>(a, b, nx, ny, nz, x, y, z)) continue;
+        const size_t g = at3(x, y, z, ny, pitch);
+        const int i = a * ld + b;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) s[c * cells + i] = in[c * plane_elems + g];
+        sc[i] = kc[g];
+    }
+    __syncthreads();
+    // the eight bond layers of this axis (Eq. 2e6 / 2e9 / their z analogue)
+#pragma unroll
+    for (int L = 0; L < 8; ++L) {
+        const Layer ly = layer_of(L);
+        const T g0 = T(AXIS == 1 ? -1 : 1);
+        const T g = ly.dag ? -g0 : g0;
+        for (int t = threadIdx.x; t < AX * TB; t += THREADS3) {
+            const int a = t / TB, b = t % TB;
+            const int a2 = a + ly.shift;
+            if (a2 < 0 || a2 >= AX) continue;
+            const int i = a * ld + b, i2 = a2 * ld + b;
+#pragma unroll
+            for (int pk = 0; pk < 2; ++pk) {
+                const Pair pr = pair3_of(AXIS, pk);
+                int ia = i, ib = i;
+                if (ly.mover == 1) {
+                    if (pr.a_is_m1) ia = i2; else ib = i2;
+                } else if (ly.mover == 2) {
+                    if (pr.a_is_m1) ib = i2; else ia = i2;
+                }
+                T va = s[pr.a * cells + ia], vb = s[pr.b * cells + ib];
+                rotate(va, vb, sc[i], g);
+                s[pr.a * cells + ia] = va;
+                s[pr.b * cells + ib] = vb;
+            }
+        }
+        __syncthreads();
+    }
+    // write the 32 inner cells of each line
+    const int seg0 = int(AXIS == 0 ? blockIdx.x : blockIdx.y) * SEG;
+    const int n_along = AXIS == 0 ? nx : AXIS == 1 ? ny : nz;
+    for (int t = threadIdx.x; t < SEG * TB; t += THREADS3) {
+        const int a = HALO3 + (AXIS == 0 ? t % SEG : t / TB), b = AXIS == 0 ? t / SEG : t % TB;
+        if (seg0 + a - HALO3 >= n_along) continue;
+        int x, y, z;
+        if (!cell<AXIS>(a, b, nx, ny, nz, x, y, z)) continue;
+        const size_t g = at3(x, y, z, ny, pitch);
+        const int i = a * ld + b;
+        T q[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) q[c] = s[c * cells + i];
+        if constexpr (VEND && VM == V_ROTATION) {
+            // V_x (Eq. 2e11, rotation reading), V_y (Eq. 2e12), V_z (Eq. 3b4)
+            const V3<T> v = kv[g];
+            rotate1(q[2], q[4], v.gx, v.sx, T(-1));
+            rotate1(q[1], q[5], v.gx, v.sx, T(1));
+            rotate1(q[2], q[3], v.gy, v.sy, T(1));
+            rotate1(q[0], q[5], v.gy, v.sy, T(-1));
+            rotate1(q[1], q[3], v.gz, v.sz, T(-1));
+            rotate1(q[0], q[4], v.gz, v.sz, T(1));
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) out[c * plane_elems + g] = q[c];
+    }
+}
+
+template <typename T, int AXIS, bool VEND, int VM>
+cudaError_t pass_t(const void *in, void *out, const void *kc, const void *kv, int nx, int ny,
+                   int nz, int pitch, size_t plane_elems, cudaStream_t st) {
+    constexpr int cells = AX * LD<AXIS>;
+    const size_t smem = size_t(cells) * (sizeof(typename Coef<T>::C) + 6 * sizeof(T));
+    auto kern = k3_pass<T, AXIS, VEND, VM>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [&] {
+        attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    });
+    if (attr != cudaSuccess) return attr;
+    dim3 grid;
+    if (AXIS == 0) grid = dim3((nx + SEG - 1) / SEG, (ny + TB - 1) / TB, nz);
+    else if (AXIS == 1) grid = dim3((nx + TB - 1) / TB, (ny + SEG - 1) / SEG, nz);
+    else grid = dim3((nx + TB - 1) / TB, (nz + SEG - 1) / SEG, ny);
+    kern<<<grid, THREADS3, smem, st>>>(static_cast<const T *>(in), static_cast<T *>(out),
+                                       static_cast<const typename Coef<T>::C *>(kc),
+                                       static_cast<const V3<T> *>(kv), nx, ny, nz, pitch,
+                                       plane_elems);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace qla
+
+using namespace qla;
+
+struct qla3_ctx {
+    int nx = 0, ny = 0, nz = 0, pitch = 0, prec = 0, vmode = V_ROTATION, device = 0;
+    double delta = 1.0;
+    size_t plane_elems = 0;
+    cudaStream_t stream = nullptr;
+    char *ws = nullptr;
+    bool owns_ws = false;
+    void *state[2] = {nullptr, nullptr};
+    int cur = 0;
+    double *n = nullptr, *staging = nullptr, *partials = nullptr, *result = nullptr;
+    void *kc = nullptr, *kv = nullptr;
+    int eblocks = 1;
+    bool has_medium = false, has_state = false;
+    long long launches = 0;
+    qla_status sticky = QLA_OK;
+    std::string err;
+};
+
+namespace {
+
+struct Layout3 {
+    size_t state[2], n, staging, kc, kv, partials, result, total, plane_elems;
+    int pitch, eblocks;
+};
+
+size_t al256(size_t v) { return (v + 255) / 256 * 256; }
+
+bool dims_ok(int nx, int ny, int nz) {
+    return nx >= 1 && ny >= 1 && nz >= 1 && ny <= 65535 && nz <= 65535 &&
+           size_t(nx) * ny * nz <= (size_t(1) << 31);
+}
+
+Layout3 layout3(int nx, int ny, int nz, int prec) {
+    Layout3 L{};
+    const size_t elt = prec == QLA_FP64 ? 8 : 4;
+    L.pitch = (nx + 31) / 32 * 32;
+    L.plane_elems = size_t(nz) * ny * L.pitch;
+    const size_t sites = size_t(nx) * ny * nz;
+    size_t nb = (sites + 2047) / 2048;
+    nb = nb > 4096 ? 4096 : (nb < 1 ? 1 : nb);
+    L.eblocks = int(nb);
+    const size_t kcb = prec == QLA_FP64 ? sizeof(double2) : sizeof(float4);
+    const size_t kvb = prec == QLA_FP64 ? sizeof(V3<double>) : sizeof(V3<float>);
+    size_t off = 0;
+    L.state[0] = off; off += al256(L.plane_elems * elt * 6);
+    L.state[1] = off; off += al256(L.plane_elems * elt * 6);
+    L.n = off;        off += al256(L.plane_elems * 8);
+    L.staging = off;  off += al256(sites * 8);
+    L.kc = off;       off += al256(L.plane_elems * kcb);
+    L.kv = off;       off += al256(L.plane_elems * kvb);
+    L.partials = off; off += al256(nb * 8);
+    L.result = off;   off += al256(8);
+    L.total = off;
+    return L;
+}
+
+qla_status fail3(qla3_ctx *c, qla_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+    if (s == QLA_ECUDA) c->sticky = s;
+    return s;
+}
+
+#define CUDA3(c, call, what)                                                                \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail3(c, QLA_ECUDA, "%s: %s", what, cudaGetErrorString(e_));             \
+    } while (0)
+
+qla_status usable3(qla3_ctx *c) {
+    if (!c) return QLA_EINVAL;
+    if (c->sticky != QLA_OK) return c->sticky;
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail3(c, QLA_ECUDA, "cannot select device");
+    return QLA_OK;
+}
+
+template <typename T>
+cudaError_t step3_t(qla3_ctx *c) {
+    const int nx = c->nx, ny = c->ny, nz = c->nz, pitch = c->pitch;
+    const size_t pe = c->plane_elems;
+    void *a = c->state[c->cur], *b = c->state[c->cur ^ 1];
+    cudaError_t e = pass_t<T, 0, false, V_NONE>(a, b, c->kc, c->kv, nx, ny, nz, pitch, pe, c->stream);
+    if (e != cudaSuccess) return e;
+    e = pass_t<T, 1, false, V_NONE>(b, a, c->kc, c->kv, nx, ny, nz, pitch, pe, c->stream);
+    if (e != cudaSuccess) return e;
+    e = c->vmode == V_ROTATION
+            ? pass_t<T, 2, true, V_ROTATION>(a, b, c->kc, c->kv, nx, ny, nz, pitch, pe, c->stream)
+            : pass_t<T, 2, true, V_NONE>(a, b, c->kc, c->kv, nx, ny, nz, pitch, pe, c->stream);
+    c->launches += 3;
+    c->cur ^= 1;
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t qla3_workspace_bytes(int nx, int ny, int nz, int precision, unsigned flags) {
+    if (!dims_ok(nx, ny, nz) || (precision != QLA_FP64 && precision != QLA_FP32)) return 0;
+    if (flags & ~(unsigned)QLA_POTENTIAL_NONE) return 0;
+    return layout3(nx, ny, nz, precision).total;
+}
+
+qla_status qla3_init(qla3_ctx **out, int nx, int ny, int nz, double delta, int precision,
+                     unsigned flags, void *cuda_stream, void *workspace, size_t workspace_bytes) {
+    if (!out) return QLA_EINVAL;
+    *out = nullptr;
+    const size_t need = qla3_workspace_bytes(nx, ny, nz, precision, flags);
+    if (need == 0 || !(delta > 0.0) || !std::isfinite(delta)) return QLA_EINVAL;
+    if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255)) return QLA_EINVAL;
+    if (workspace && workspace_bytes < need) return QLA_ENOMEM;
+    qla3_ctx *c = new (std::nothrow) qla3_ctx();
+    if (!c) return QLA_ENOMEM;
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->delta = delta;
+    c->prec = precision;
+    c->vmode = (flags & QLA_POTENTIAL_NONE) ? V_NONE : V_ROTATION;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return QLA_ECUDA; }
+    const Layout3 L = layout3(nx, ny, nz, precision);
+    if (workspace) {
+        c->ws = static_cast<char *>(workspace);
+    } else {
+        void *p = nullptr;
+        if (cudaMalloc(&p, L.total) != cudaSuccess) { cudaGetLastError(); delete c; return QLA_ENOMEM; }
+        c->ws = static_cast<char *>(p);
+        c->owns_ws = true;
+    }
+    c->pitch = L.pitch;
+    c->plane_elems = L.plane_elems;
+    c->state[0] = c->ws + L.state[0];
+    c->state[1] = c->ws + L.state[1];
+    c->n = reinterpret_cast<double *>(c->ws + L.n);
+    c->staging = reinterpret_cast<double *>(c->ws + L.staging);
+    c->kc = c->ws + L.kc;
+    c->kv = c->ws + L.kv;
+    c->partials = reinterpret_cast<double *>(c->ws + L.partials);
+    c->result = reinterpret_cast<double *>(c->ws + L.result);
+    c->eblocks = L.eblocks;
+    // both state buffers start at zero (pad columns included)
+    if (cudaMemsetAsync(c->ws, 0, L.n, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->owns_ws) cudaFree(c->ws);
+        delete c;
+        return QLA_ECUDA;
+    }
+    *out = c;
+    return QLA_OK;
+}
+
+qla_status qla3_set_medium(qla3_ctx *c, const double *n_host) {
+    qla_status s = usable3(c);
+    if (s != QLA_OK) return s;
+    if (!n_host) return fail3(c, QLA_EINVAL, "qla3_set_medium: null n");
+    const size_t N = size_t(c->nx) * c->ny * c->nz;
+    for (size_t k = 0; k < N; ++k)
+        if (!(n_host[k] > 0.0) || !std::isfinite(n_host[k]))
+            return fail3(c, QLA_EINVAL, "qla3_set_medium: n[%zu] = %g is not finite and > 0", k,
+                         n_host[k]);
+    const int rows = c->ny * c->nz;
+    CUDA3(c, cudaMemcpyAsync(c->staging, n_host, N * 8, cudaMemcpyHostToDevice, c->stream),
+          "qla3_set_medium: copy");
+    CUDA3(c, raw_pitch_copy(c->staging, c->n, c->nx, rows, c->pitch, c->stream),
+          "qla3_set_medium: place");
+    const double vscale = 0.5;   // rotation reading: V rotates by beta / 2
+    const int blocks = int(std::min<size_t>((N + 255) / 256, size_t(65535) * 16));
+    if (c->prec == QLA_FP64)
+        k3_medium<double><<<blocks, 256, 0, c->stream>>>(
+            c->n, c->nx, c->ny, c->nz, c->pitch, c->delta, vscale,
+            static_cast<double2 *>(c->kc), static_cast<V3<double> *>(c->kv));
+    else
+        k3_medium<float><<<blocks, 256, 0, c->stream>>>(
+            c->n, c->nx, c->ny, c->nz, c->pitch, c->delta, vscale,
+            static_cast<float4 *>(c->kc), static_cast<V3<float> *>(c->kv));
+    CUDA3(c, cudaGetLastError(), "qla3_set_medium: kernel");
+    c->launches += 2;
+    CUDA3(c, cudaStreamSynchronize(c->stream), "qla3_set_medium: sync");
+    c->has_medium = true;
+    return QLA_OK;
+}
+
+qla_status qla3_set_state(qla3_ctx *c, const double *q_host) {
+    qla_status s = usable3(c);
+    if (s != QLA_OK) return s;
+    if (!q_host) return fail3(c, QLA_EINVAL, "qla3_set_state: null state");
+    const size_t N = size_t(c->nx) * c->ny * c->nz;
+    for (size_t k = 0; k < 6 * N; ++k)
+        if (!std::isfinite(q_host[k]))
+            return fail3(c, QLA_EINVAL, "qla3_set_state: non-finite value at %zu", k);
+    const size_t elt = c->prec == QLA_FP64 ? 8 : 4;
+    for (int comp = 0; comp < 6; ++comp) {
+        CUDA3(c, cudaMemcpyAsync(c->staging, q_host + size_t(comp) * N, N * 8,
+                                 cudaMemcpyHostToDevice, c->stream), "qla3_set_state: copy");
+        CUDA3(c, raw_from_f64(c->prec, c->staging,
+                              static_cast<char *>(c->state[c->cur]) + comp * c->plane_elems * elt,
+                              c->nx, c->ny * c->nz, c->pitch, c->stream),
+              "qla3_set_state: convert");
+        c->launches++;
+    }
+    // the staging plane is reused per component and the host buffer may
+    // change after return
+    CUDA3(c, cudaStreamSynchronize(c->stream), "qla3_set_state: sync");
+    c->has_state = true;
+    return QLA_OK;
+}
+
+qla_status qla3_get_state(qla3_ctx *c, double *q_host) {
+    qla_status s = usable3(c);
+    if (s != QLA_OK) return s;
+    if (!q_host) return fail3(c, QLA_EINVAL, "qla3_get_state: null output");
+    if (!c->has_state) return fail3(c, QLA_ESTATE, "qla3_get_state: no state");
+    const size_t N = size_t(c->nx) * c->ny * c->nz;
+    for (int comp = 0; comp < 6; ++comp) {
+        CUDA3(c, raw_to_f64(c->prec, c->state[c->cur], c->plane_elems, comp, c->staging, c->nx,
+                            c->ny * c->nz, c->pitch, c->stream), "qla3_get_state: convert");
+        c->launches++;
+        CUDA3(c, cudaMemcpyAsync(q_host + size_t(comp) * N, c->staging, N * 8,
+                                 cudaMemcpyDeviceToHost, c->stream), "qla3_get_state: copy");
+        CUDA3(c, cudaStreamSynchronize(c->stream), "qla3_get_state: sync");
+    }
+    return QLA_OK;
+}
+
+qla_status qla3_step(qla3_ctx *c, long long n_steps) {
+    qla_status s = usable3(c);
+    if (s != QLA_OK) return s;
+    if (n_steps < 0) return fail3(c, QLA_EINVAL, "qla3_step: n_steps < 0");
+    if (n_steps == 0) return QLA_OK;
+    if (!c->has_medium || !c->has_state)
+        return fail3(c, QLA_ESTATE, "qla3_step: set a medium and a state first");
+    for (long long k = 0; k < n_steps; ++k)
+        CUDA3(c, c->prec == QLA_FP64 ? step3_t<double>(c) : step3_t<float>(c), "qla3_step: kernel");
+    return QLA_OK;
+}
+
+qla_status qla3_energy(qla3_ctx *c, double *out) {
+    qla_status s = usable3(c);
+    if (s != QLA_OK) return s;
+    if (!out) return fail3(c, QLA_EINVAL, "qla3_energy: null output");
+    if (!c->has_state) return fail3(c, QLA_ESTATE, "qla3_energy: no state");
+    CUDA3(c, raw_energy(c->prec, c->state[c->cur], c->plane_elems, c->nx, c->ny * c->nz, c->pitch,
+                        c->partials, c->eblocks, c->result, c->stream), "qla3_energy: kernel");
+    c->launches += 2;
+    CUDA3(c, cudaMemcpyAsync(out, c->result, 8, cudaMemcpyDeviceToHost, c->stream),
+          "qla3_energy: copy");
+    CUDA3(c, cudaStreamSynchronize(c->stream), "qla3_energy: sync");
+    if (!std::isfinite(*out)) return fail3(c, QLA_ENONFINITE, "qla3_energy: energy is %g", *out);
+    return QLA_OK;
+}
+
+long long qla3_launch_count(const qla3_ctx *c) { return c ? c->launches : 0; }
+
+const char *qla3_last_error(const qla3_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+void qla3_destroy(qla3_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    if (c->owns_ws) cudaFree(c->ws);
+    delete c;
+}
+
+}  // extern "C"

@@ -400,6 +400,57 @@ cudaError_t launch_medium(qla_ctx *c) {
     return cudaGetLastError();
 }
 
+// Raw-pointer forms of the conversions and the energy for a six-plane state
+// with no pending potential step (the three-dimensional path, whose
+// lattice is nx x rows with rows = ny * nz).
+cudaError_t raw_pitch_copy(const double *src, double *dst, int nx, int rows, int pitch,
+                           cudaStream_t st) {
+    k_pitch_copy<<<grid_for(size_t(nx) * rows), AUX_THREADS, 0, st>>>(src, dst, nx, rows, pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t raw_from_f64(int prec, const double *src, void *plane, int nx, int rows, int pitch,
+                         cudaStream_t st) {
+    const size_t N = size_t(nx) * rows;
+    if (prec == QLA_FP64)
+        k_from_f64<double><<<grid_for(N), AUX_THREADS, 0, st>>>(src, static_cast<double *>(plane),
+                                                                 nx, rows, pitch);
+    else
+        k_from_f64<float><<<grid_for(N), AUX_THREADS, 0, st>>>(src, static_cast<float *>(plane),
+                                                                nx, rows, pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t raw_to_f64(int prec, const void *state, size_t plane_elems, int comp, double *dst,
+                       int nx, int rows, int pitch, cudaStream_t st) {
+    const size_t N = size_t(nx) * rows;
+    if (prec == QLA_FP64)
+        k_to_f64<double, 6, V_NONE><<<grid_for(N), AUX_THREADS, 0, st>>>(
+            static_cast<const double *>(state), plane_elems, comp, nullptr, dst, nx, rows, pitch,
+            false, nullptr, nullptr);
+    else
+        k_to_f64<float, 6, V_NONE><<<grid_for(N), AUX_THREADS, 0, st>>>(
+            static_cast<const float *>(state), plane_elems, comp, nullptr, dst, nx, rows, pitch,
+            false, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t raw_energy(int prec, const void *state, size_t plane_elems, int nx, int rows,
+                       int pitch, double *partials, int nblocks, double *result, cudaStream_t st) {
+    if (prec == QLA_FP64)
+        k_energy_partial<double, 6, V_NONE><<<nblocks, AUX_THREADS, 0, st>>>(
+            static_cast<const double *>(state), nx, rows, pitch, plane_elems, partials, false,
+            nullptr, nullptr);
+    else
+        k_energy_partial<float, 6, V_NONE><<<nblocks, AUX_THREADS, 0, st>>>(
+            static_cast<const float *>(state), nx, rows, pitch, plane_elems, partials, false,
+            nullptr, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_energy_final<<<1, AUX_THREADS, 0, st>>>(partials, nblocks, result);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pitch_copy(qla_ctx *c, double *dst) {
     const size_t N = size_t(c->nx) * c->ny;
     k_pitch_copy<<<grid_for(N), AUX_THREADS, 0, c->stream>>>(c->staging, dst, c->nx, c->ny,

@@ -309,6 +309,16 @@ cudaError_t launch_medium(qla_ctx *c);
 // Tensor media: stage one host plane (already in c->staging) into dst;
 // build the MedRecT table of a six-plane QLA_ANISOTROPIC context.
 cudaError_t launch_pitch_copy(qla_ctx *c, double *dst);
+// Raw forms for a six-plane state without a pending V (three dimensions:
+// rows = ny * nz).  Each returns the cudaError_t of its launches.
+cudaError_t raw_pitch_copy(const double *src, double *dst, int nx, int rows, int pitch,
+                           cudaStream_t st);
+cudaError_t raw_from_f64(int prec, const double *src, void *plane, int nx, int rows, int pitch,
+                         cudaStream_t st);
+cudaError_t raw_to_f64(int prec, const void *state, size_t plane_elems, int comp, double *dst,
+                       int nx, int rows, int pitch, cudaStream_t st);
+cudaError_t raw_energy(int prec, const void *state, size_t plane_elems, int nx, int rows,
+                       int pitch, double *partials, int nblocks, double *result, cudaStream_t st);
 cudaError_t launch_medium_tensor(qla_ctx *c);
 cudaError_t launch_step_tensor(qla_ctx *c, const void *in, void *out);
 cudaError_t launch_packet(qla_ctx *c, const qla_packet &p);

@@ -74,6 +74,22 @@ def load():
             getattr(lib, name).argtypes = args
             getattr(lib, name).restype = c_int
         lib.qla_init_grid.restype = c_int
+        lib.qla3_workspace_bytes.argtypes = [c_int, c_int, c_int, c_int, c_u]
+        lib.qla3_workspace_bytes.restype = c_sz
+        lib.qla3_init.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, c_int, ctypes.c_double,
+                                  c_int, c_u, c_vp, c_vp, c_sz]
+        lib.qla3_init.restype = c_int
+        for name, args in (("qla3_set_medium", [c_vp, c_vp]), ("qla3_set_state", [c_vp, c_vp]),
+                           ("qla3_get_state", [c_vp, c_vp]), ("qla3_step", [c_vp, c_ll]),
+                           ("qla3_energy", [c_vp, _DP])):
+            getattr(lib, name).argtypes = args
+            getattr(lib, name).restype = c_int
+        lib.qla3_launch_count.argtypes = [c_vp]
+        lib.qla3_launch_count.restype = c_ll
+        lib.qla3_last_error.argtypes = [c_vp]
+        lib.qla3_last_error.restype = ctypes.c_char_p
+        lib.qla3_destroy.argtypes = [c_vp]
+        lib.qla3_destroy.restype = None
         lib.qla_batch_workspace_bytes.argtypes = [c_int, c_vp, c_vp, c_int, c_u]
         lib.qla_batch_workspace_bytes.restype = c_sz
         lib.qla_batch_create.argtypes = [ctypes.POINTER(c_vp), c_int, c_vp, c_vp,
@@ -492,3 +508,85 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Grid3:
+    """A three-dimensional context (qla3_* in the C ABI): nx x ny x nz
+    periodic lattice, six planes, precision "fp64" or "fp32", potential
+    "rotation" or "none".  Arrays are (6, nz, ny, nx) states and (nz, ny, nx)
+    media; the workspace is a torch uint8 tensor, work runs on ``stream``."""
+
+    def __init__(self, nx, ny, nz, delta=1.0, precision="fp64", potential="rotation",
+                 stream=None):
+        import torch
+        lib = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libqla needs a CUDA device; none is available")
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        prec = {"fp64": QLA_FP64, "fp32": QLA_FP32}[precision]
+        flags = {"rotation": 0, "none": QLA_POTENTIAL_NONE}[potential]
+        nbytes = int(lib.qla3_workspace_bytes(self.nx, self.ny, self.nz, prec, flags))
+        if nbytes == 0:
+            raise QLAError(1, "invalid 3D lattice or flags")
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        ctx = ctypes.c_void_p()
+        st = lib.qla3_init(ctypes.byref(ctx), self.nx, self.ny, self.nz, float(delta), prec, flags,
+                           ctypes.c_void_p(self.stream.cuda_stream),
+                           ctypes.c_void_p(self.workspace.data_ptr()), nbytes)
+        if st != 0:
+            raise QLAError(st, "qla3_init")
+        self._ctx = ctx
+
+    def _check(self, st):
+        if st != 0:
+            raise QLAError(st, load().qla3_last_error(self._ctx).decode())
+
+    @property
+    def sites(self):
+        return self.nx * self.ny * self.nz
+
+    def set_medium(self, n):
+        a = np.ascontiguousarray(n, dtype=np.float64)
+        assert a.size == self.sites
+        self._check(load().qla3_set_medium(self._ctx, ctypes.c_void_p(a.ctypes.data)))
+
+    def set_state(self, q):
+        a = np.ascontiguousarray(q, dtype=np.float64)
+        assert a.size == 6 * self.sites
+        self._check(load().qla3_set_state(self._ctx, ctypes.c_void_p(a.ctypes.data)))
+
+    def get_state(self):
+        out = np.empty((6, self.nz, self.ny, self.nx))
+        self._check(load().qla3_get_state(self._ctx, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def step(self, n=1):
+        self._check(load().qla3_step(self._ctx, int(n)))
+
+    def energy(self):
+        v = ctypes.c_double()
+        self._check(load().qla3_energy(self._ctx, ctypes.byref(v)))
+        return v.value
+
+    @property
+    def launches(self):
+        return int(load().qla3_launch_count(self._ctx))
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            load().qla3_destroy(self._ctx)
+            self._ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
