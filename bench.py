@@ -87,12 +87,18 @@ def alu_ops_per_su(P, elt):
     return pairs * (16 * 4 + 2 * 4)
 
 
-def roofline(P, elt, su_per_s, traffic, **extra):
+def alu_ops_per_su_3d(elt):
+    """3D: per axis 8 layers x 2 pairs of collision rotations, then six
+    potential rotations (two per axis)."""
+    return 3 * 16 * (8 if elt == 4 else 4) + 6 * (6 if elt == 4 else 4)
+
+
+def roofline(P, elt, su_per_s, traffic, ops=None, **extra):
     """Roofline object for a step kernel that advances ``su_per_s`` site-updates
     per second of its own run time.  The bound is the roof with the lower
     ceiling in site-updates/s (HBM for FP32, the FP64 pipe for FP64); the
     other roof's figures ride along under its name."""
-    ops = alu_ops_per_su(P, elt)
+    ops = alu_ops_per_su(P, elt) if ops is None else ops
     peak_ops = FP32_INST_PEAK if elt == 4 else FP64_INST_PEAK
     hbm_peak, hbm_kind = peaks()
     bytes_su = 2 * P * elt
@@ -599,8 +605,115 @@ def surrogate_arm(args):
     return 0
 
 
+def cube_arm(args):
+    """3D workload (qla3_*): an E_z packet into a dielectric ellipsoid on a
+    256^3 lattice; a bench step is --qla-steps steps (three launches each)
+    and one energy read.  The packet state is built here on the host (the
+    Dyson map q2 = n E_z and the plane-wave B of a +x wave, q4 = -q2) and
+    handed to both arms as input data."""
+    import numpy as np
+    import torch
+
+    from paper_2604_21128_gb300 import build as qbuild
+    from paper_2604_21128_gb300 import inputs, qla
+
+    world, rank, local = dist_setup()
+    if world == 1:
+        torch.cuda.set_device(0)
+    qbuild.build()
+    w = inputs.cube_256()
+    N, d = w["n"], w["delta"]
+    n3 = inputs.ellipsoid_medium3(N, N, N, d, **w["medium"])
+    x = np.arange(N) * d
+    pk = w["packet"]
+    f = np.exp(-(x - pk["x0"]) ** 2 / pk["width"] ** 2) * np.cos(pk["k0"] * (x - pk["x0"]))
+    q = np.zeros((6, N, N, N))
+    q[2] = n3 * f[None, None, :]
+    q[4] = -q[2]
+    elt = 4 if args.precision == "fp32" else 8
+    S = max(1, args.qla_steps // 5)
+    sites = N ** 3
+    stream = torch.cuda.Stream()
+    g = qla.Grid3(N, N, N, d, args.precision, stream=stream)
+    t_e2e = time.perf_counter()
+    g.set_medium(n3)
+    g.set_state(q)
+    e0 = g.energy()
+    for _ in range(args.warmup):
+        g.step(S)
+        g.energy()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sampler = ClockSampler(local if world > 1 else 0)
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = g.launches
+    sampler.start()
+    time.sleep(0.3)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        g.step(S)
+        ev[k][1].record(stream)
+        e = g.energy()
+    stop.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = g.launches - l0
+    elapsed = max_over_ranks(world, start.elapsed_time(stop) / 1e3)
+    step_time = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    final = g.get_state()
+    t_e2e = time.perf_counter() - t_e2e
+    g.close()
+    value = world * args.steps * S * sites / elapsed
+    kernel_su = args.steps * S * sites / step_time
+    total_steps = (args.warmup + args.steps) * S
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        import oracle
+        side, nst = 96, 3
+        nw = np.ascontiguousarray(n3[:side, :side, :side])
+        qw = np.ascontiguousarray(q[:, :side, :side, :side])
+        threads = os.cpu_count() or 1
+        oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        oracle.run3(qw, nw, d, nst)
+        dt = time.perf_counter() - t0
+        cpu = {"value": side ** 3 * nst / dt, "unit": "site-updates/s", "cores": threads,
+               "kind": "oracle",
+               "sample": "%d^3 corner of the cube_256 workload (periodic), %d steps (%.1f s), "
+                         "plain FP64 CPU oracle" % (side, nst, dt)}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if elt == 4 else "f64", "data": "synthetic",
+            "config": {"workload": "cube_256_%s_3d" % args.precision, "n": N, "delta": d,
+                       "qla_steps_per_bench_step": S, "planes": 6,
+                       "launches_per_qla_step": 3, "energy_drift": e / e0 - 1,
+                       "l2": "state %.0f MB > 129 MB L2, no flush" % (12 * elt * sites / 1e6)},
+            "roofline": roofline(6, elt, kernel_su, None, ops=alu_ops_per_su_3d(elt),
+                                 kernel_ms_per_qla_step=1e3 * step_time / (args.steps * S),
+                                 note="three passes per step: U_x, U_y, U_z + V"),
+            "cpu_baseline": cpu,
+            "e2e": {"value": total_steps * sites / t_e2e, "unit": "site-updates/s",
+                    "h2d_bytes_per_step": (q.nbytes + n3.nbytes) / (args.steps + args.warmup),
+                    "d2h_bytes_per_step": (final.nbytes + 8 * (args.steps + args.warmup + 1))
+                                          / (args.steps + args.warmup),
+                    "note": "host wall clock: medium and state in, all steps, energies, "
+                            "state out"},
+            "gpu_launches": launches, "clocks": clocks}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "cube_256" and args.impl != "reference":
+        return cube_arm(args)
     if args.workload == "surrogate256":
         return surrogate_arm(args)
     if args.impl == "reference":

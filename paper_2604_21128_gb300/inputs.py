@@ -187,6 +187,35 @@ def batch_instances(count: int = 256, seed: int = BATCH_SEED,
     return out
 
 
+def ellipsoid_medium3(nx: int, ny: int, nz: int, delta: float, a: float, b: float, c: float,
+                      n_in: float, n_out: float, edge: float, centre=None) -> np.ndarray:
+    """Index map (nz, ny, nx) of a smooth ellipsoid (semi-axes a, b, c along
+    x, y, z, lengths in physical units): rho = |(X/a, Y/b, Z/c)|, signed
+    distance s = (rho - 1)/|grad rho|, n = n_out + (n_in - n_out)(1 - tanh(s/edge))/2,
+    built plane by plane along z."""
+    cx, cy, cz = (nx * delta / 2, ny * delta / 2, nz * delta / 2) if centre is None else centre
+    X = np.arange(nx)[None, :] * delta - cx
+    Y = np.arange(ny)[:, None] * delta - cy
+    out = np.empty((nz, ny, nx))
+    for k in range(nz):
+        Z = k * delta - cz
+        rho = np.sqrt((X / a) ** 2 + (Y / b) ** 2 + (Z / c) ** 2)
+        rs = np.maximum(rho, 1e-12)
+        grad = np.sqrt((X / a ** 2) ** 2 + (Y / b ** 2) ** 2 + (Z / c ** 2) ** 2) / rs
+        sdist = (rho - 1.0) / np.maximum(grad, 1e-12)
+        out[k] = n_out + (n_in - n_out) * 0.5 * (1.0 - np.tanh(sdist / edge))
+    return out
+
+
+def cube_256():
+    """3D workload: 256^3, delta = 1, a dielectric ellipsoid (semi-axes 60,
+    40, 30 cells, n = 2, tanh edge 3) in vacuum at the box centre; a planar
+    E_z packet (k0 = 0.3, width 16 cells) moving along +x from x = 40."""
+    return dict(name="cube_256", n=256, delta=1.0,
+                medium=dict(a=60.0, b=40.0, c=30.0, n_in=2.0, n_out=1.0, edge=3.0),
+                packet=dict(x0=40.0, k0=0.3, width=16.0))
+
+
 def random_state(nx: int, ny: int, seed: int, planes=6) -> np.ndarray:
     """Seeded N(0,1) amplitudes of shape (6, ny, nx); planes beyond ``planes``
     of the TE set are zero when planes == 3 (q2, q3, q4 live)."""
