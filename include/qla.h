@@ -430,14 +430,22 @@ qla_status qla3_set_medium(qla3_ctx *ctx, const double *n_host);
 qla_status qla3_set_state(qla3_ctx *ctx, const double *q_host);
 qla_status qla3_get_state(qla3_ctx *ctx, double *q_host);
 
-/* Advance n_steps steps (each three passes: U_x, U_y, then U_z followed by
- * V_x V_y V_z); asynchronous on the context's stream.  QLA_ESTATE without
+/* Advance n_steps steps (see qla3_set_step_kernel for the launches);
+ * asynchronous on the context's stream.  QLA_ESTATE without
  * medium and state. */
 qla_status qla3_step(qla3_ctx *ctx, long long n_steps);
 
 /* Sum of q^2 over sites and planes (Eq. A13 without the cell volume),
  * FP64.  Synchronises; QLA_ENONFINITE if not finite. */
 qla_status qla3_energy(qla3_ctx *ctx, double *out);
+
+/* Step kernel: 0 (default) runs one launch per axis (U_x; U_y; U_z then
+ * V); 1 fuses the step into one launch that marches along z (U_x, U_y in
+ * shared memory per plane, U_z as a register pipeline, then V), which moves
+ * a third of the data but is slower on the GPUs measured (its per-plane
+ * barriers dominate).  Both apply the same operations in the same order per
+ * site: results agree bit for bit.  QLA_EINVAL for other values. */
+qla_status qla3_set_step_kernel(qla3_ctx *ctx, int kernel);
 
 long long qla3_launch_count(const qla3_ctx *ctx);
 const char *qla3_last_error(const qla3_ctx *ctx);

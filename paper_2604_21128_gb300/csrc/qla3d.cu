@@ -1,6 +1,8 @@
 // Three-dimensional QLA step: Q <- V_z V_y V_x U_z U_y U_x Q, with U_z and
-// V_z read off Eq. 3b4 (see include/qla.h).  One step is three launches,
-// one per axis: a CTA stages 32 lines x 40 cells along the active axis (32
+// V_z read off Eq. 3b4 (see include/qla.h).  Two step kernels: three
+// launches, one per axis (default), and the fused march along z further
+// below (one launch; measured slower on 256^3: its per-plane barriers
+// dominate).  The per-axis form: a CTA stages 32 lines x 40 cells along the active axis (32
 // outputs and a 4-cell periodic halo on each side, the reach of U) of all
 // six planes and of the collision coefficients in shared memory, applies
 // the eight bond layers of that axis's U (the layer form of Eq. 2e6, see
@@ -28,6 +30,12 @@ __host__ __device__ constexpr Pair pair3_of(int axis, int k) {
     return axis == 0 ? (k == 0 ? Pair{1, 5, true} : Pair{2, 4, false})
          : axis == 1 ? (k == 0 ? Pair{0, 5, true} : Pair{2, 3, false})
                      : (k == 0 ? Pair{0, 4, true} : Pair{1, 3, false});
+}
+
+// Collision sign of layer L of U_z: C_z rotates by +theta (the sign pattern
+// of C_x); the adjoint flips it.
+template <int L> __host__ __device__ constexpr int layer_sign_z() {
+    return layer_of(L).dag ? -1 : 1;
 }
 
 // Potential coefficients of one site for x, y, z, in the CoefV convention
@@ -220,6 +228,269 @@ cudaError_t pass_t(const void *in, void *out, const void *kc, const void *kv, in
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Fused step: a CTA owns a TX x TY tile of (x, y) sites and marches along z
+// over a segment of planes.  Per input plane: stage the tile and a 4-cell
+// halo in x and y (all six planes and the collision coefficients), apply
+// U_x to every staged row and U_y to the tile's columns in shared memory;
+// U_z then runs as a software pipeline along z in registers, per site (the
+// pipeline of the 2D march kernel along y: each neighbour layer delays its
+// output by one plane and carries two values per pair), so the output plane
+// is four planes behind the input plane.  q2 and q5, which no z pair
+// touches, wait in a four-plane register ring so that V_x V_y V_z see all
+// six amplitudes of the output plane; then it is stored.  A segment reads
+// four planes on each side that it does not store.
+// ---------------------------------------------------------------------------
+template <typename T> struct MTile;
+template <> struct MTile<float>  { static constexpr int TX = 32, TY = 16; };
+template <> struct MTile<double> { static constexpr int TX = 32, TY = 8; };
+
+// One on-site U_z layer on a site's six amplitudes (pairs (q0, q4), (q1, q3)).
+template <typename T, int L>
+__device__ __forceinline__ void uz_local(T (&q)[6], typename Coef<T>::C k) {
+    const T g = T(layer_sign_z<L>());
+#pragma unroll
+    for (int pk = 0; pk < 2; ++pk) {
+        const Pair pr = pair3_of(2, pk);
+        rotate(q[pr.a], q[pr.b], k, g);
+    }
+}
+
+// One neighbour U_z layer: q holds the plane entering the stage and on
+// return the plane leaving it (one plane earlier); c[pk][0..1] carry the
+// values the layer keeps between planes (as uy_neighbour in the 2D march).
+template <typename T, int L>
+__device__ __forceinline__ void uz_neighbour(T (&q)[6], T (&c)[2][2], typename Coef<T>::C k) {
+    constexpr Layer ly = layer_of(L);
+    const T g = T(layer_sign_z<L>());
+#pragma unroll
+    for (int pk = 0; pk < 2; ++pk) {
+        const Pair pr = pair3_of(2, pk);
+        const bool a_moved = (ly.mover == 1) == pr.a_is_m1;
+        const int cm = a_moved ? pr.a : pr.b, cu = a_moved ? pr.b : pr.a;
+        const T u = q[cu], m = q[cm];
+        if (ly.shift < 0) {
+            // bond at this plane r: (u_r, m_{r-1}); c0 = m_{r-1} before the
+            // layer, c1 = u_{r-1} after it
+            T uu = u, mm = c[pk][0];
+            if (a_moved) rotate(mm, uu, k, g); else rotate(uu, mm, k, g);
+            q[cu] = c[pk][1];
+            q[cm] = mm;
+            c[pk][0] = m;
+            c[pk][1] = uu;
+        } else {
+            // bond at plane r-1: (u_{r-1}, m_r); c0 = u_{r-1} before the
+            // layer, c1 = m_{r-1} after it
+            T uu = c[pk][0], mm = m;
+            if (a_moved) rotate(mm, uu, k, g); else rotate(uu, mm, k, g);
+            q[cu] = uu;
+            q[cm] = c[pk][1];
+            c[pk][0] = u;
+            c[pk][1] = mm;
+        }
+    }
+}
+
+template <typename T, int VM>
+struct March3 {
+    using CC = typename Coef<T>::C;
+    static constexpr int TX = MTile<T>::TX, TY = MTile<T>::TY;
+    static constexpr int RX = TX + 2 * HALO3, RY = TY + 2 * HALO3, CELLS = RX * RY;
+    static constexpr int SPT = TX * TY / THREADS3;   // inner sites per thread
+
+    const T *in;
+    T *out;
+    const CC *kc;
+    const V3<T> *kv;
+    int nx, ny, nz, pitch;
+    size_t plane_elems;
+    int x0, y0, z_lo, z_hi;
+    T *s;
+    CC *sc;
+    T carry[SPT][4][2][2];   // [site][neighbour layer][pair][value]
+    CC kring[SPT][4];        // coefficients of the four planes in the U_z pipeline
+    T dring[SPT][4][2];      // q2, q5 of the four planes in flight
+
+    // One bond of layer L of axis AXIS between staged cells a (the bond
+    // site) and b (its partner at a + shift), both pairs.
+    template <int AXIS>
+    __device__ __forceinline__ void bond3(int L, int a, int b, T g) {
+        const Layer ly = layer_of(L);
+#pragma unroll
+        for (int pk = 0; pk < 2; ++pk) {
+            const Pair pr = pair3_of(AXIS, pk);
+            int ia = a, ib = a;
+            if (ly.mover == 1) { if (pr.a_is_m1) ia = b; else ib = b; }
+            else if (ly.mover == 2) { if (pr.a_is_m1) ib = b; else ia = b; }
+            T va = s[pr.a * CELLS + ia], vb = s[pr.b * CELLS + ib];
+            rotate(va, vb, sc[a], g);
+            s[pr.a * CELLS + ia] = va;
+            s[pr.b * CELLS + ib] = vb;
+        }
+    }
+
+    // Input plane J; PH = (J - first plane) mod 4 selects the ring slots
+    // (slot S0 holds plane J, and held plane J - 4 until this iteration).
+    template <int PH>
+    __device__ __forceinline__ void plane(int J) {
+        constexpr int S0 = PH, S1 = (PH + 3) & 3, S2 = (PH + 2) & 3, S3 = (PH + 1) & 3;
+        const int zJ = wrap(J, nz);
+        __syncthreads();   // the previous plane's readers are done with s
+        for (int t = threadIdx.x; t < CELLS; t += THREADS3) {
+            const int r = t / RX, c = t - r * RX;
+            const int gx = wrap(x0 - HALO3 + c, nx), gy = wrap(y0 - HALO3 + r, ny);
+            const size_t g = at3(gx, gy, zJ, ny, pitch);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s[k * CELLS + t] = in[k * plane_elems + g];
+            sc[t] = kc[g];
+        }
+        __syncthreads();
+        // U_x on every staged row (Eq. 2e6)
+#pragma unroll
+        for (int L = 0; L < 8; ++L) {
+            const Layer ly = layer_of(L);
+            const T g = ly.dag ? T(-1) : T(1);
+            for (int t = threadIdx.x; t < CELLS; t += THREADS3) {
+                const int r = t / RX, i = t - r * RX, i2 = i + ly.shift;
+                if (i2 < 0 || i2 >= RX) continue;
+                bond3<0>(L, r * RX + i, r * RX + i2, g);
+            }
+            __syncthreads();
+        }
+        // U_y on the tile's columns (Eq. 2e9)
+#pragma unroll
+        for (int L = 0; L < 8; ++L) {
+            const Layer ly = layer_of(L);
+            const T g = ly.dag ? T(1) : T(-1);
+            for (int t = threadIdx.x; t < TX * RY; t += THREADS3) {
+                const int r = t / TX, i = HALO3 + (t - r * TX), r2 = r + ly.shift;
+                if (r2 < 0 || r2 >= RY) continue;
+                bond3<1>(L, r * RX + i, r2 * RX + i, g);
+            }
+            __syncthreads();
+        }
+        // U_z along the march, per inner site; the output is plane J - 4
+        const bool store = J - HALO3 >= z_lo && J - HALO3 < z_hi;
+        const int zo = wrap(J - HALO3, nz);
+#pragma unroll
+        for (int p = 0; p < SPT; ++p) {
+            const int site = int(threadIdx.x) + p * THREADS3;
+            const int ix = site % TX, iy = site / TX;
+            const int sm = (iy + HALO3) * RX + ix + HALO3;
+            T q[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) q[k] = s[k * CELLS + sm];
+            kring[p][S0] = sc[sm];
+            uz_local<T, 0>(q, kring[p][S0]);
+            uz_neighbour<T, 1>(q, carry[p][0], kring[p][S0]);
+            uz_local<T, 2>(q, kring[p][S1]);
+            uz_neighbour<T, 3>(q, carry[p][1], kring[p][S2]);
+            uz_local<T, 4>(q, kring[p][S2]);
+            uz_neighbour<T, 5>(q, carry[p][2], kring[p][S3]);
+            uz_local<T, 6>(q, kring[p][S3]);
+            uz_neighbour<T, 7>(q, carry[p][3], kring[p][S3]);
+            // q2, q5 of the output plane J - 4 come out of the ring; those of
+            // plane J go in (the same slot)
+            const T q2 = dring[p][S0][0], q5 = dring[p][S0][1];
+            dring[p][S0][0] = q[2];
+            dring[p][S0][1] = q[5];
+            q[2] = q2;
+            q[5] = q5;
+            const int gx = x0 + ix, gy = y0 + iy;
+            if (store && gx < nx && gy < ny) {
+                const size_t g = at3(gx, gy, zo, ny, pitch);
+                if constexpr (VM == V_ROTATION) {
+                    // V_x (Eq. 2e11, rotation reading), V_y (Eq. 2e12), V_z (Eq. 3b4)
+                    const V3<T> v = kv[g];
+                    rotate1(q[2], q[4], v.gx, v.sx, T(-1));
+                    rotate1(q[1], q[5], v.gx, v.sx, T(1));
+                    rotate1(q[2], q[3], v.gy, v.sy, T(1));
+                    rotate1(q[0], q[5], v.gy, v.sy, T(-1));
+                    rotate1(q[1], q[3], v.gz, v.sz, T(-1));
+                    rotate1(q[0], q[4], v.gz, v.sz, T(1));
+                }
+#pragma unroll
+                for (int k = 0; k < 6; ++k) out[k * plane_elems + g] = q[k];
+            }
+        }
+    }
+};
+
+template <typename T, int VM>
+__global__ void __launch_bounds__(THREADS3)
+k3_march(const T *__restrict__ in, T *__restrict__ out, const typename Coef<T>::C *__restrict__ kc,
+         const V3<T> *__restrict__ kv, int nx, int ny, int nz, int pitch, size_t plane_elems,
+         int seg) {
+    using M = March3<T, VM>;
+    extern __shared__ __align__(16) unsigned char smem3[];
+    M m;
+    m.in = in;
+    m.out = out;
+    m.kc = kc;
+    m.kv = kv;
+    m.nx = nx;
+    m.ny = ny;
+    m.nz = nz;
+    m.pitch = pitch;
+    m.plane_elems = plane_elems;
+    m.x0 = int(blockIdx.x) * M::TX;
+    m.y0 = int(blockIdx.y) * M::TY;
+    m.z_lo = int(blockIdx.z) * seg;
+    m.z_hi = min(nz, m.z_lo + seg);
+    m.sc = reinterpret_cast<typename M::CC *>(smem3);
+    m.s = reinterpret_cast<T *>(m.sc + M::CELLS);
+#pragma unroll
+    for (int p = 0; p < M::SPT; ++p)
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            m.dring[p][l][0] = m.dring[p][l][1] = T(0);
+#pragma unroll
+            for (int a = 0; a < 2; ++a) m.carry[p][l][a][0] = m.carry[p][l][a][1] = T(0);
+        }
+    // input planes z_lo - 4 .. z_hi + 3 (rounded up to a multiple of 4; the
+    // extra planes are computed and not stored); output plane J - 4
+    const int J0 = m.z_lo - HALO3, J1 = m.z_hi + HALO3;
+    for (int J = J0; J < J1; J += 4) {
+        m.template plane<0>(J);
+        m.template plane<1>(J + 1);
+        m.template plane<2>(J + 2);
+        m.template plane<3>(J + 3);
+    }
+}
+
+template <typename T, int VM>
+cudaError_t march3_t(const void *in, void *out, const void *kc, const void *kv, int nx, int ny,
+                     int nz, int pitch, size_t plane_elems, int num_sms, cudaStream_t st) {
+    using M = March3<T, VM>;
+    const size_t smem = size_t(M::CELLS) * (sizeof(typename Coef<T>::C) + 6 * sizeof(T));
+    auto kern = k3_march<T, VM>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    static int per_sm = 1;
+    std::call_once(once, [&] {
+        attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (attr == cudaSuccess)
+            attr = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS3, smem);
+        if (per_sm < 1) per_sm = 1;
+    });
+    if (attr != cudaSuccess) return attr;
+    const int tiles = ((nx + M::TX - 1) / M::TX) * ((ny + M::TY - 1) / M::TY);
+    // about two waves of CTAs; at least 16 planes per segment so that the
+    // 8 planes a segment reads but does not store stay a modest overhead
+    const long long want = 2LL * per_sm * num_sms;
+    int nseg = int((want + tiles - 1) / tiles);
+    if (nseg < 1) nseg = 1;
+    int seg = (nz + nseg - 1) / nseg;
+    if (seg < 16) seg = 16;
+    nseg = (nz + seg - 1) / seg;
+    dim3 grid((nx + M::TX - 1) / M::TX, (ny + M::TY - 1) / M::TY, nseg);
+    kern<<<grid, THREADS3, smem, st>>>(static_cast<const T *>(in), static_cast<T *>(out),
+                                       static_cast<const typename Coef<T>::C *>(kc),
+                                       static_cast<const V3<T> *>(kv), nx, ny, nz, pitch,
+                                       plane_elems, seg);
+    return cudaGetLastError();
+}
+
 }  // namespace
 }  // namespace qla
 
@@ -237,6 +508,8 @@ struct qla3_ctx {
     double *n = nullptr, *staging = nullptr, *partials = nullptr, *result = nullptr;
     void *kc = nullptr, *kv = nullptr;
     int eblocks = 1;
+    int num_sms = 1;
+    int kernel = 0;   // 0: one pass per axis (default), 1: fused march along z
     bool has_medium = false, has_state = false;
     long long launches = 0;
     qla_status sticky = QLA_OK;
@@ -311,6 +584,14 @@ cudaError_t step3_t(qla3_ctx *c) {
     const int nx = c->nx, ny = c->ny, nz = c->nz, pitch = c->pitch;
     const size_t pe = c->plane_elems;
     void *a = c->state[c->cur], *b = c->state[c->cur ^ 1];
+    if (c->kernel == 1) {
+        cudaError_t e = c->vmode == V_ROTATION
+            ? march3_t<T, V_ROTATION>(a, b, c->kc, c->kv, nx, ny, nz, pitch, pe, c->num_sms, c->stream)
+            : march3_t<T, V_NONE>(a, b, c->kc, c->kv, nx, ny, nz, pitch, pe, c->num_sms, c->stream);
+        c->launches += 1;
+        c->cur ^= 1;
+        return e;
+    }
     cudaError_t e = pass_t<T, 0, false, V_NONE>(a, b, c->kc, c->kv, nx, ny, nz, pitch, pe, c->stream);
     if (e != cudaSuccess) return e;
     e = pass_t<T, 1, false, V_NONE>(b, a, c->kc, c->kv, nx, ny, nz, pitch, pe, c->stream);
@@ -351,6 +632,8 @@ qla_status qla3_init(qla3_ctx **out, int nx, int ny, int nz, double delta, int p
     c->vmode = (flags & QLA_POTENTIAL_NONE) ? V_NONE : V_ROTATION;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return QLA_ECUDA; }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (c->num_sms < 1) c->num_sms = 1;
     const Layout3 L = layout3(nx, ny, nz, precision);
     if (workspace) {
         c->ws = static_cast<char *>(workspace);
@@ -479,6 +762,15 @@ qla_status qla3_energy(qla3_ctx *c, double *out) {
           "qla3_energy: copy");
     CUDA3(c, cudaStreamSynchronize(c->stream), "qla3_energy: sync");
     if (!std::isfinite(*out)) return fail3(c, QLA_ENONFINITE, "qla3_energy: energy is %g", *out);
+    return QLA_OK;
+}
+
+qla_status qla3_set_step_kernel(qla3_ctx *c, int kernel) {
+    qla_status s = usable3(c);
+    if (s != QLA_OK) return s;
+    if (kernel != 0 && kernel != 1)
+        return fail3(c, QLA_EINVAL, "qla3_set_step_kernel: kernel must be 0 or 1, got %d", kernel);
+    c->kernel = kernel;
     return QLA_OK;
 }
 

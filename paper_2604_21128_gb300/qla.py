@@ -81,7 +81,7 @@ def load():
         lib.qla3_init.restype = c_int
         for name, args in (("qla3_set_medium", [c_vp, c_vp]), ("qla3_set_state", [c_vp, c_vp]),
                            ("qla3_get_state", [c_vp, c_vp]), ("qla3_step", [c_vp, c_ll]),
-                           ("qla3_energy", [c_vp, _DP])):
+                           ("qla3_energy", [c_vp, _DP]), ("qla3_set_step_kernel", [c_vp, c_int])):
             getattr(lib, name).argtypes = args
             getattr(lib, name).restype = c_int
         lib.qla3_launch_count.argtypes = [c_vp]
@@ -564,6 +564,10 @@ class Grid3:
 
     def step(self, n=1):
         self._check(load().qla3_step(self._ctx, int(n)))
+
+    def set_step_kernel(self, kernel):
+        """"passes" (one launch per axis, default) or "march" (fused)."""
+        self._check(load().qla3_set_step_kernel(self._ctx, {"passes": 0, "march": 1}[kernel]))
 
     def energy(self):
         v = ctypes.c_double()

@@ -34,20 +34,23 @@ def medium3(nx, ny, nz, seed):
     return 1.0 + 2.5 * raw
 
 
+@pytest.mark.parametrize("kernel", ["march", "passes"])
 @pytest.mark.parametrize("potential", ["rotation", "none"])
-@pytest.mark.parametrize("shape", [(24, 20, 6), (33, 17, 9), (70, 40, 36), (5, 3, 2)])
-def test_fp64_matches_oracle(shape, potential):
+@pytest.mark.parametrize("shape", [(24, 20, 6), (33, 17, 9), (70, 40, 36), (5, 3, 2),
+                                   (40, 26, 70)])
+def test_fp64_matches_oracle(shape, potential, kernel):
     nx, ny, nz = shape
     n = medium3(nx, ny, nz, seed=nx + ny + nz)
     q0 = np.random.default_rng(nx * ny + nz).standard_normal((6, nz, ny, nx))
     want = oracle.run3(q0, n, 0.7, 3, potential)
     with qla.Grid3(nx, ny, nz, 0.7, "fp64", potential) as g:
+        g.set_step_kernel(kernel)
         g.set_medium(n)
         g.set_state(q0)
         g.step(3)
         got = g.get_state()
         e = g.energy()
-        assert g.launches >= 9
+        assert g.launches >= 3
     assert rel_l2(got, want) <= 1e-12, rel_l2(got, want)
     assert e == pytest.approx(float(np.sum(want ** 2)), rel=1e-12)
 
@@ -63,6 +66,25 @@ def test_fp32_matches_oracle():
         g.step(8)
         got = g.get_state()
     assert rel_l2(got, want) <= 1e-5, rel_l2(got, want)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("shape", [(64, 48, 40), (37, 19, 53)])
+def test_march_and_passes_agree_bitwise(shape, precision):
+    """The fused kernel and the per-axis passes apply the same operations in
+    the same order at every site."""
+    nx, ny, nz = shape
+    n = medium3(nx, ny, nz, seed=11)
+    q0 = np.random.default_rng(12).standard_normal((6, nz, ny, nx))
+    out = []
+    for kernel in ("march", "passes"):
+        with qla.Grid3(nx, ny, nz, 1.0, precision) as g:
+            g.set_step_kernel(kernel)
+            g.set_medium(n)
+            g.set_state(q0)
+            g.step(7)
+            out.append(g.get_state())
+    assert np.array_equal(out[0], out[1])
 
 
 def test_energy_conserved_over_many_steps():
