@@ -273,10 +273,11 @@ def reference_arm(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def kernel_traffic(k, sites):
-    """DRAM bytes per step-kernel launch from the committed ncu summary, if it
-    was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+def kernel_traffic(k, sites, record="traffic.json"):
+    """DRAM bytes per step-kernel launch (per step for the 3D passes) from a
+    committed ncu record, if it was taken on the current kernel sources;
+    else None."""
+    path = os.path.join(ROOT, "profiles", record)
     try:
         with open(path) as f:
             rec = json.load(f)
@@ -696,7 +697,9 @@ def cube_arm(args):
                        "qla_steps_per_bench_step": S, "planes": 6,
                        "launches_per_qla_step": 3, "energy_drift": e / e0 - 1,
                        "l2": "state %.0f MB > 129 MB L2, no flush" % (12 * elt * sites / 1e6)},
-            "roofline": roofline(6, elt, kernel_su, None, ops=alu_ops_per_su_3d(elt),
+            "roofline": roofline(6, elt, kernel_su,
+                                 kernel_traffic(1, sites, "traffic_cube256.json") if elt == 4
+                                 else None, ops=alu_ops_per_su_3d(elt),
                                  kernel_ms_per_qla_step=1e3 * step_time / (args.steps * S),
                                  note="three passes per step: U_x, U_y, U_z + V"),
             "cpu_baseline": cpu,
