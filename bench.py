@@ -260,7 +260,10 @@ def reference_arm(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "sample": sample},
+            # the GPU arm's workload label, so the two lines pair up
+            "config": {"workload": w.name + ("_fp32" if args.precision == "fp32" else "_fp64")
+                       + ("_6planes" if args.six_planes else "_ez"),
+                       "nx": w.nx, "ny": w.ny, "delta": w.delta, "sample": sample},
             "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": threads,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
