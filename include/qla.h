@@ -439,12 +439,18 @@ qla_status qla3_step(qla3_ctx *ctx, long long n_steps);
  * FP64.  Synchronises; QLA_ENONFINITE if not finite. */
 qla_status qla3_energy(qla3_ctx *ctx, double *out);
 
-/* Step kernel: 0 (default) runs one launch per axis (U_x; U_y; U_z then
- * V); 1 fuses the step into one launch that marches along z (U_x, U_y in
- * shared memory per plane, U_z as a register pipeline, then V), which moves
- * a third of the data but is slower on the GPUs measured (its per-plane
- * barriers dominate).  Both apply the same operations in the same order per
- * site: results agree bit for bit.  QLA_EINVAL for other values. */
+/* Step kernel (results agree bit for bit: every kernel applies the same
+ * operations in the same order per site):
+ *   3: one launch per axis (U_x; U_y; U_z then V), shared-memory layers;
+ *   1: one launch marching along z (U_x, U_y in shared memory per plane,
+ *      U_z as a register pipeline, then V): a third of the data of 3 but
+ *      slower on the GPUs measured, its per-plane barriers dominate;
+ *   2: two launches: the 2D marching kernel on every z slice (U_x, U_y in
+ *      registers) and a column pipeline along z (U_z, then V); needs nx
+ *      even and >= 64, ny >= 8 and 6 * nz*ny*pitch < 2^32, else runs 3;
+ *   0 (default): 2 for FP32 (1.8x kernel 3 at 256^3), 3 for FP64 (FP64-pipe
+ *      bound, where kernel 2's window halo costs more than it saves).
+ * QLA_EINVAL for other values. */
 qla_status qla3_set_step_kernel(qla3_ctx *ctx, int kernel);
 
 long long qla3_launch_count(const qla3_ctx *ctx);

@@ -1,8 +1,9 @@
 // Three-dimensional QLA step: Q <- V_z V_y V_x U_z U_y U_x Q, with U_z and
-// V_z read off Eq. 3b4 (see include/qla.h).  Two step kernels: three
-// launches, one per axis (default), and the fused march along z further
-// below (one launch; measured slower on 256^3: its per-plane barriers
-// dominate).  The per-axis form: a CTA stages 32 lines x 40 cells along the active axis (32
+// V_z read off Eq. 3b4 (see include/qla.h).  Three step kernels: three
+// launches, one per axis (the FP64 default); the fused march along z (one
+// launch; measured slower on 256^3: its per-plane barriers dominate); and
+// the 2D march on every slice plus a column pipeline along z (the FP32
+// default), both further below.  The per-axis form: a CTA stages 32 lines x 40 cells along the active axis (32
 // outputs and a 4-cell periodic halo on each side, the reach of U) of all
 // six planes and of the collision coefficients in shared memory, applies
 // the eight bond layers of that axis's U (the layer form of Eq. 2e6, see
@@ -18,6 +19,7 @@
 #include <string>
 
 #include "qla_internal.h"
+#include "qla_march.cuh"
 
 namespace qla {
 namespace {
@@ -491,6 +493,204 @@ cudaError_t march3_t(const void *in, void *out, const void *kc, const void *kv, 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Slices + column pipeline (kernel 2).  Launch 1 runs the 2D marching
+// machinery of qla_march.cuh on every z slice at once (work item = slice,
+// 64-column window, row segment): U_x in registers with warp shuffles, U_y
+// as a register pipeline along y, no V.  It reads per-site records through
+// a one-slice identity index.  Launch 2 gives each thread one (x, y) column
+// and marches it along z: U_z as the same register pipeline (q2 and q5,
+// which no z pair touches, wait four planes in a ring), then V_x V_y V_z,
+// then the store.  Neither launch uses shared-memory layer passes or block
+// barriers.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(32 * march::WARPS)
+k3_slices(const T *__restrict__ in, T *__restrict__ out, const uint32_t *__restrict__ midx,
+          const MedRec<T> *__restrict__ table, int nx, int ny, int pitch, size_t plane_elems,
+          int seg_h, int n_wx, int n_wy, long long n_items) {
+    using M = march::March<T, 6, 2, V_NONE, false>;
+    extern __shared__ __align__(16) unsigned char smem_s[];
+    typename M::Slot *ring =
+        reinterpret_cast<typename M::Slot *>(smem_s) + (threadIdx.x >> 5) * march::NSLOT;
+    const long long item = (long long)blockIdx.x * march::WARPS + (threadIdx.x >> 5);
+    if (item >= n_items) return;
+    const long long per_slice = (long long)n_wx * n_wy;
+    const int slice = int(item / per_slice), local = int(item - slice * per_slice);
+    const size_t base = size_t(slice) * ny * size_t(pitch);
+    M m;
+    m.in = in + base;
+    m.out = out + base;
+    m.midx = midx;
+    m.table = table + base;
+    m.pitch = pitch;
+    m.plane = uint32_t(plane_elems);
+    m.total = uint32_t(ny) * uint32_t(pitch);
+    m.run_item(nx, ny, seg_h, n_wx, local, ring);
+}
+
+template <typename T, int VM>
+struct ZCol {
+    using CC = typename Coef<T>::C;
+    const T *in;
+    T *out;
+    const CC *kc;
+    const V3<T> *kv;
+    size_t col, zstride, plane_elems;
+    int nz, z_lo, z_hi;
+    bool live;
+    T carry[4][2][2];
+    CC kring[4];
+    T dring[4][2];
+
+    template <int PH>
+    __device__ __forceinline__ void plane(int J) {
+        constexpr int S0 = PH, S1 = (PH + 3) & 3, S2 = (PH + 2) & 3, S3 = (PH + 1) & 3;
+        if (!live) return;
+        const size_t g = col + size_t(wrap(J, nz)) * zstride;
+        T q[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) q[k] = in[k * plane_elems + g];
+        kring[S0] = kc[g];
+        uz_local<T, 0>(q, kring[S0]);
+        uz_neighbour<T, 1>(q, carry[0], kring[S0]);
+        uz_local<T, 2>(q, kring[S1]);
+        uz_neighbour<T, 3>(q, carry[1], kring[S2]);
+        uz_local<T, 4>(q, kring[S2]);
+        uz_neighbour<T, 5>(q, carry[2], kring[S3]);
+        uz_local<T, 6>(q, kring[S3]);
+        uz_neighbour<T, 7>(q, carry[3], kring[S3]);
+        const T q2 = dring[S0][0], q5 = dring[S0][1];
+        dring[S0][0] = q[2];
+        dring[S0][1] = q[5];
+        q[2] = q2;
+        q[5] = q5;
+        if (J - HALO3 >= z_lo && J - HALO3 < z_hi) {
+            const size_t go = col + size_t(wrap(J - HALO3, nz)) * zstride;
+            if constexpr (VM == V_ROTATION) {
+                // V_x (Eq. 2e11, rotation reading), V_y (Eq. 2e12), V_z (Eq. 3b4)
+                const V3<T> v = kv[go];
+                rotate1(q[2], q[4], v.gx, v.sx, T(-1));
+                rotate1(q[1], q[5], v.gx, v.sx, T(1));
+                rotate1(q[2], q[3], v.gy, v.sy, T(1));
+                rotate1(q[0], q[5], v.gy, v.sy, T(-1));
+                rotate1(q[1], q[3], v.gz, v.sz, T(-1));
+                rotate1(q[0], q[4], v.gz, v.sz, T(1));
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) out[k * plane_elems + go] = q[k];
+        }
+    }
+};
+
+template <typename T, int VM>
+__global__ void __launch_bounds__(128)
+k3_zcol(const T *__restrict__ in, T *__restrict__ out, const typename Coef<T>::C *__restrict__ kc,
+        const V3<T> *__restrict__ kv, int nx, int ny, int nz, int pitch, size_t plane_elems,
+        int seg) {
+    ZCol<T, VM> m;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int x = int(t % nx), y = int(t / nx);
+    // threads past the last column still take part in nothing but the loop
+    m.live = t < (long long)nx * ny;
+    m.in = in;
+    m.out = out;
+    m.kc = kc;
+    m.kv = kv;
+    m.col = size_t(y) * pitch + x;
+    m.zstride = size_t(ny) * pitch;
+    m.plane_elems = plane_elems;
+    m.nz = nz;
+    m.z_lo = int(blockIdx.y) * seg;
+    m.z_hi = min(nz, m.z_lo + seg);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        m.dring[l][0] = m.dring[l][1] = T(0);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) m.carry[l][a][0] = m.carry[l][a][1] = T(0);
+    }
+    const int J0 = m.z_lo - HALO3, J1 = m.z_hi + HALO3;
+    for (int J = J0; J < J1; J += 4) {
+        m.template plane<0>(J);
+        m.template plane<1>(J + 1);
+        m.template plane<2>(J + 2);
+        m.template plane<3>(J + 3);
+    }
+}
+
+// Can the slices launch run this lattice?  (The march's 32-bit offsets and
+// its window width.)
+bool slices_ok(int nx, int ny, size_t plane_elems) {
+    return nx % 2 == 0 && nx >= 64 && ny >= 8 && 6 * (unsigned long long)plane_elems < (1ull << 32);
+}
+
+template <typename T, int VM>
+cudaError_t slices_t(const void *in, void *out, const uint32_t *midx, const void *mrec,
+                     const void *kc, const void *kv, int nx, int ny, int nz, int pitch,
+                     size_t plane_elems, int num_sms, cudaStream_t st) {
+    using M = march::March<T, 6, 2, V_NONE, false>;
+    const size_t smem = sizeof(typename M::Slot) * march::NSLOT * march::WARPS;
+    auto k1 = k3_slices<T>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    static int per_sm = 1;
+    std::call_once(once, [&] {
+        attr = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (attr == cudaSuccess)
+            attr = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, 32 * march::WARPS,
+                                                                 smem);
+        if (per_sm < 1) per_sm = 1;
+    });
+    if (attr != cudaSuccess) return attr;
+    // launch 1: items of 64-column windows (56 stored) x row segments x slices,
+    // about two per resident warp slot
+    const int n_wx = (nx + 55) / 56;
+    const long long resident = (long long)per_sm * march::WARPS * num_sms;
+    long long n_wy = 2 * resident / ((long long)n_wx * nz);
+    if (n_wy < 1) n_wy = 1;
+    int seg_h = int((ny + n_wy - 1) / n_wy);
+    seg_h = seg_h < 32 ? 32 : (seg_h + 3) / 4 * 4;
+    n_wy = (ny + seg_h - 1) / seg_h;
+    const long long n_items = (long long)n_wx * n_wy * nz;
+    const long long blocks = (n_items + march::WARPS - 1) / march::WARPS;
+    k1<<<unsigned(blocks), 32 * march::WARPS, smem, st>>>(
+        static_cast<const T *>(in), static_cast<T *>(out), midx,
+        static_cast<const MedRec<T> *>(mrec), nx, ny, pitch, plane_elems, seg_h, n_wx, int(n_wy),
+        n_items);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // launch 2: one thread per column, z segments for about two waves of
+    // 128-thread blocks (at least 16 planes each)
+    const long long cols = (long long)nx * ny;
+    const long long cblocks = (cols + 127) / 128;
+    int nseg = int((2LL * 8 * num_sms + cblocks - 1) / cblocks);
+    if (nseg < 1) nseg = 1;
+    int seg = (nz + nseg - 1) / nseg;
+    if (seg < 16) seg = 16;
+    nseg = (nz + seg - 1) / seg;
+    k3_zcol<T, VM><<<dim3(unsigned(cblocks), nseg), 128, 0, st>>>(
+        static_cast<const T *>(out), static_cast<T *>(const_cast<void *>(in)),
+        static_cast<const typename Coef<T>::C *>(kc), static_cast<const V3<T> *>(kv), nx, ny, nz,
+        pitch, plane_elems, seg);
+    return cudaGetLastError();
+}
+
+// Records for the slices launch: the collision coefficient of each site in
+// MedRec form (its potential part unused), and the identity index of one
+// slice (every slice uses the same map).
+template <typename T>
+__global__ void k3_records(const typename Coef<T>::C *__restrict__ kc, size_t plane_elems,
+                           size_t slice_elems, MedRec<T> *__restrict__ rec,
+                           uint32_t *__restrict__ midx) {
+    for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < plane_elems;
+         t += size_t(gridDim.x) * blockDim.x) {
+        MedRec<T> r{};
+        r.c = kc[t];
+        rec[t] = r;
+        if (t < slice_elems) midx[t] = uint32_t(t);
+    }
+}
+
 }  // namespace
 }  // namespace qla
 
@@ -507,9 +707,12 @@ struct qla3_ctx {
     int cur = 0;
     double *n = nullptr, *staging = nullptr, *partials = nullptr, *result = nullptr;
     void *kc = nullptr, *kv = nullptr;
+    void *mrec = nullptr;          // MedRec<T> per site (slices launch)
+    uint32_t *midx = nullptr;      // identity index of one slice
     int eblocks = 1;
     int num_sms = 1;
-    int kernel = 0;   // 0: one pass per axis (default), 1: fused march along z
+    int kernel = 0;   // 0: automatic, 1: fused march along z, 2: slices + column
+                      // pipeline, 3: one pass per axis
     bool has_medium = false, has_state = false;
     long long launches = 0;
     qla_status sticky = QLA_OK;
@@ -519,7 +722,7 @@ struct qla3_ctx {
 namespace {
 
 struct Layout3 {
-    size_t state[2], n, staging, kc, kv, partials, result, total, plane_elems;
+    size_t state[2], n, staging, kc, kv, mrec, midx, partials, result, total, plane_elems;
     int pitch, eblocks;
 };
 
@@ -548,6 +751,9 @@ Layout3 layout3(int nx, int ny, int nz, int prec) {
     L.staging = off;  off += al256(sites * 8);
     L.kc = off;       off += al256(L.plane_elems * kcb);
     L.kv = off;       off += al256(L.plane_elems * kvb);
+    const size_t recb = prec == QLA_FP64 ? sizeof(MedRec<double>) : sizeof(MedRec<float>);
+    L.mrec = off;     off += al256(L.plane_elems * recb);
+    L.midx = off;     off += al256(size_t(ny) * L.pitch * 4);
     L.partials = off; off += al256(nb * 8);
     L.result = off;   off += al256(8);
     L.total = off;
@@ -584,7 +790,21 @@ cudaError_t step3_t(qla3_ctx *c) {
     const int nx = c->nx, ny = c->ny, nz = c->nz, pitch = c->pitch;
     const size_t pe = c->plane_elems;
     void *a = c->state[c->cur], *b = c->state[c->cur ^ 1];
-    if (c->kernel == 1) {
+    // automatic choice: the slices launch for FP32 (1.8x the passes at
+    // 256^3), the passes for FP64 (FP64-pipe bound, where the slices'
+    // window halo costs more than their fewer memory passes save)
+    const int kernel = c->kernel != 0 ? c->kernel : (sizeof(T) == 4 ? 2 : 3);
+    if (kernel == 2 && slices_ok(nx, ny, pe)) {
+        // the slices launch writes b; the column launch reads b, writes a
+        cudaError_t e = c->vmode == V_ROTATION
+            ? slices_t<T, V_ROTATION>(a, b, c->midx, c->mrec, c->kc, c->kv, nx, ny, nz, pitch, pe,
+                                      c->num_sms, c->stream)
+            : slices_t<T, V_NONE>(a, b, c->midx, c->mrec, c->kc, c->kv, nx, ny, nz, pitch, pe,
+                                  c->num_sms, c->stream);
+        c->launches += 2;
+        return e;   // the result is back in state[cur]
+    }
+    if (kernel == 1) {
         cudaError_t e = c->vmode == V_ROTATION
             ? march3_t<T, V_ROTATION>(a, b, c->kc, c->kv, nx, ny, nz, pitch, pe, c->num_sms, c->stream)
             : march3_t<T, V_NONE>(a, b, c->kc, c->kv, nx, ny, nz, pitch, pe, c->num_sms, c->stream);
@@ -651,6 +871,8 @@ qla_status qla3_init(qla3_ctx **out, int nx, int ny, int nz, double delta, int p
     c->staging = reinterpret_cast<double *>(c->ws + L.staging);
     c->kc = c->ws + L.kc;
     c->kv = c->ws + L.kv;
+    c->mrec = c->ws + L.mrec;
+    c->midx = reinterpret_cast<uint32_t *>(c->ws + L.midx);
     c->partials = reinterpret_cast<double *>(c->ws + L.partials);
     c->result = reinterpret_cast<double *>(c->ws + L.result);
     c->eblocks = L.eblocks;
@@ -690,7 +912,17 @@ qla_status qla3_set_medium(qla3_ctx *c, const double *n_host) {
             c->n, c->nx, c->ny, c->nz, c->pitch, c->delta, vscale,
             static_cast<float4 *>(c->kc), static_cast<V3<float> *>(c->kv));
     CUDA3(c, cudaGetLastError(), "qla3_set_medium: kernel");
-    c->launches += 2;
+    const size_t slice = size_t(c->ny) * c->pitch;
+    if (c->prec == QLA_FP64)
+        k3_records<double><<<blocks, 256, 0, c->stream>>>(
+            static_cast<const double2 *>(c->kc), c->plane_elems, slice,
+            static_cast<MedRec<double> *>(c->mrec), c->midx);
+    else
+        k3_records<float><<<blocks, 256, 0, c->stream>>>(
+            static_cast<const float4 *>(c->kc), c->plane_elems, slice,
+            static_cast<MedRec<float> *>(c->mrec), c->midx);
+    CUDA3(c, cudaGetLastError(), "qla3_set_medium: records");
+    c->launches += 3;
     CUDA3(c, cudaStreamSynchronize(c->stream), "qla3_set_medium: sync");
     c->has_medium = true;
     return QLA_OK;
@@ -768,8 +1000,8 @@ qla_status qla3_energy(qla3_ctx *c, double *out) {
 qla_status qla3_set_step_kernel(qla3_ctx *c, int kernel) {
     qla_status s = usable3(c);
     if (s != QLA_OK) return s;
-    if (kernel != 0 && kernel != 1)
-        return fail3(c, QLA_EINVAL, "qla3_set_step_kernel: kernel must be 0 or 1, got %d", kernel);
+    if (kernel < 0 || kernel > 3)
+        return fail3(c, QLA_EINVAL, "qla3_set_step_kernel: kernel must be 0..3, got %d", kernel);
     c->kernel = kernel;
     return QLA_OK;
 }

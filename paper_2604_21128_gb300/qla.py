@@ -566,8 +566,10 @@ class Grid3:
         self._check(load().qla3_step(self._ctx, int(n)))
 
     def set_step_kernel(self, kernel):
-        """"passes" (one launch per axis, default) or "march" (fused)."""
-        self._check(load().qla3_set_step_kernel(self._ctx, {"passes": 0, "march": 1}[kernel]))
+        """"auto" (default), "passes" (one launch per axis), "march" (fused
+        along z) or "slices" (2D march per slice + column pipeline along z)."""
+        k = {"auto": 0, "march": 1, "slices": 2, "passes": 3}[kernel]
+        self._check(load().qla3_set_step_kernel(self._ctx, k))
 
     def energy(self):
         v = ctypes.c_double()

@@ -34,10 +34,10 @@ def medium3(nx, ny, nz, seed):
     return 1.0 + 2.5 * raw
 
 
-@pytest.mark.parametrize("kernel", ["march", "passes"])
+@pytest.mark.parametrize("kernel", ["march", "passes", "slices", "auto"])
 @pytest.mark.parametrize("potential", ["rotation", "none"])
 @pytest.mark.parametrize("shape", [(24, 20, 6), (33, 17, 9), (70, 40, 36), (5, 3, 2),
-                                   (40, 26, 70)])
+                                   (40, 26, 70), (128, 12, 21)])
 def test_fp64_matches_oracle(shape, potential, kernel):
     nx, ny, nz = shape
     n = medium3(nx, ny, nz, seed=nx + ny + nz)
@@ -69,15 +69,16 @@ def test_fp32_matches_oracle():
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-@pytest.mark.parametrize("shape", [(64, 48, 40), (37, 19, 53)])
-def test_march_and_passes_agree_bitwise(shape, precision):
-    """The fused kernel and the per-axis passes apply the same operations in
-    the same order at every site."""
+@pytest.mark.parametrize("shape", [(64, 48, 40), (37, 19, 53), (130, 24, 33)])
+def test_step_kernels_agree_bitwise(shape, precision):
+    """The per-axis passes, the fused march and the slices + column pipeline
+    apply the same operations in the same order at every site (lattices
+    narrower than 64 columns run the passes under "slices")."""
     nx, ny, nz = shape
     n = medium3(nx, ny, nz, seed=11)
     q0 = np.random.default_rng(12).standard_normal((6, nz, ny, nx))
     out = []
-    for kernel in ("march", "passes"):
+    for kernel in ("passes", "march", "slices"):
         with qla.Grid3(nx, ny, nz, 1.0, precision) as g:
             g.set_step_kernel(kernel)
             g.set_medium(n)
@@ -85,6 +86,7 @@ def test_march_and_passes_agree_bitwise(shape, precision):
             g.step(7)
             out.append(g.get_state())
     assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], out[2])
 
 
 def test_energy_conserved_over_many_steps():
