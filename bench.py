@@ -698,13 +698,13 @@ def cube_arm(args):
             "dtype": "f32" if elt == 4 else "f64", "data": "synthetic",
             "config": {"workload": "cube_256_%s_3d" % args.precision, "n": N, "delta": d,
                        "qla_steps_per_bench_step": S, "planes": 6,
-                       "launches_per_qla_step": 3, "energy_drift": e / e0 - 1,
+                       "launches_per_qla_step": 2 if elt == 4 else 3, "energy_drift": e / e0 - 1,
                        "l2": "state %.0f MB > 129 MB L2, no flush" % (12 * elt * sites / 1e6)},
             "roofline": roofline(6, elt, kernel_su,
                                  kernel_traffic(1, sites, "traffic_cube256.json") if elt == 4
                                  else None, ops=alu_ops_per_su_3d(elt),
                                  kernel_ms_per_qla_step=1e3 * step_time / (args.steps * S),
-                                 note="three passes per step: U_x, U_y, U_z + V"),
+                                 note="automatic step kernel: FP32 slices + column pipeline (2 launches), FP64 per-axis passes (3)"),
             "cpu_baseline": cpu,
             "e2e": {"value": total_steps * sites / t_e2e, "unit": "site-updates/s",
                     "h2d_bytes_per_step": (q.nbytes + n3.nbytes) / (args.steps + args.warmup),
