@@ -677,7 +677,7 @@ def cube_arm(args):
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         import oracle
-        side, nst = 96, 3
+        side, nst = 128, 10
         nw = np.ascontiguousarray(n3[:side, :side, :side])
         qw = np.ascontiguousarray(q[:, :side, :side, :side])
         threads = os.cpu_count() or 1
