@@ -218,13 +218,13 @@ def max_over_ranks(world, value):
 # CPU oracle timing (cpu_baseline, and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(w, n_full, side, steps):
+def oracle_sample(w, n_full, side, steps, threads=None):
     """Time the oracle on a side x side window of the workload (the medium
     and packet of the full lattice, taken periodic on the window) for
     ``steps`` steps; returns site-updates/s, seconds and the thread count."""
     import numpy as np
     import oracle
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     oracle.set_threads(threads)
     # window straddling the ellipse's left edge, where the packet arrives
     i0 = max(0, int(w.packet.x0 / w.delta) + int(w.packet.width / w.delta) - side // 2)
@@ -303,7 +303,7 @@ def gpu_arm(args):
     import torch
 
     from paper_2604_21128_gb300 import build as qbuild
-    from paper_2604_21128_gb300 import qla
+    from paper_2604_21128_gb300 import inputs, qla
 
     world, rank, local = dist_setup()
     if world == 1:
@@ -382,6 +382,19 @@ def gpu_arm(args):
         cpu = {"value": v, "unit": "site-updates/s", "cores": threads, "kind": "oracle",
                "sample": "%d x %d crop of the %s workload, %d steps (%.1f s), plain FP64 "
                          "CPU oracle, OpenMP over rows" % (side, side, w.name, nst, dt)}
+        # the same oracle on one thread, and the 256^2 parity workload run in full
+        v1, dt1, _ = oracle_sample(w, n_host.numpy(), 1024, 3, threads=1)
+        cpu["single_thread"] = {"value": v1, "sample": "1024 x 1024 crop, 3 steps (%.1f s)" % dt1}
+        import oracle
+        small = inputs.ellipse_256()
+        n_small = small.medium()
+        q_small = oracle.packet(n_small, small.delta, **small.packet.as_dict())
+        oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        oracle.run(q_small, n_small, small.delta, small.steps)
+        dts = time.perf_counter() - t0
+        cpu["ellipse_256_full"] = {"value": small.nx * small.ny * small.steps / dts,
+                                   "seconds": dts, "steps": small.steps}
 
     if rank == 0:
         line = {
