@@ -10,6 +10,8 @@
 // layer_of), and writes the 32 inner cells of each line; the z pass then
 // applies V_x, V_y, V_z to its outputs.  Three passes read and write the
 // state three times per step: the simple form of the 3D path.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -497,8 +499,8 @@ cudaError_t march3_t(const void *in, void *out, const void *kc, const void *kv, 
 // Slices + column pipeline (kernel 2).  Launch 1 runs the 2D marching
 // machinery of qla_march.cuh on every z slice at once (work item = slice,
 // 64-column window, row segment): U_x in registers with warp shuffles, U_y
-// as a register pipeline along y, no V.  It reads per-site records through
-// a one-slice identity index.  Launch 2 gives each thread one (x, y) column
+// as a register pipeline along y, no V.  It reads the records of k3_dedup
+// through their per-site index.  Launch 2 gives each thread one (x, y) column
 // and marches it along z: U_z as the same register pipeline (q2 and q5,
 // which no z pair touches, wait four planes in a ring), then V_x V_y V_z,
 // then the store.  Neither launch uses shared-memory layer passes or block
@@ -521,8 +523,8 @@ k3_slices(const T *__restrict__ in, T *__restrict__ out, const uint32_t *__restr
     M m;
     m.in = in + base;
     m.out = out + base;
-    m.midx = midx;
-    m.table = table + base;
+    m.midx = midx + base;
+    m.table = table;
     m.pitch = pitch;
     m.plane = uint32_t(plane_elems);
     m.total = uint32_t(ny) * uint32_t(pitch);
@@ -534,14 +536,16 @@ struct ZCol {
     using CC = typename Coef<T>::C;
     const T *in;
     T *out;
-    const CC *kc;
-    const V3<T> *kv;
+    const uint32_t *idx3;
+    const MedRec<T> *rec;
+    const V3<T> *rv;
     size_t col, zstride, plane_elems;
     int nz, z_lo, z_hi;
     bool live;
     T carry[4][2][2];
     CC kring[4];
     T dring[4][2];
+    uint32_t iring[4];       // record index of the four planes in flight
 
     template <int PH>
     __device__ __forceinline__ void plane(int J) {
@@ -551,7 +555,8 @@ struct ZCol {
         T q[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) q[k] = in[k * plane_elems + g];
-        kring[S0] = kc[g];
+        const uint32_t id = idx3[g];
+        kring[S0] = rec[id].c;
         uz_local<T, 0>(q, kring[S0]);
         uz_neighbour<T, 1>(q, carry[0], kring[S0]);
         uz_local<T, 2>(q, kring[S1]);
@@ -561,15 +566,17 @@ struct ZCol {
         uz_local<T, 6>(q, kring[S3]);
         uz_neighbour<T, 7>(q, carry[3], kring[S3]);
         const T q2 = dring[S0][0], q5 = dring[S0][1];
+        const uint32_t io = iring[S0];
         dring[S0][0] = q[2];
         dring[S0][1] = q[5];
+        iring[S0] = id;
         q[2] = q2;
         q[5] = q5;
         if (J - HALO3 >= z_lo && J - HALO3 < z_hi) {
             const size_t go = col + size_t(wrap(J - HALO3, nz)) * zstride;
             if constexpr (VM == V_ROTATION) {
                 // V_x (Eq. 2e11, rotation reading), V_y (Eq. 2e12), V_z (Eq. 3b4)
-                const V3<T> v = kv[go];
+                const V3<T> v = rv[io];
                 rotate1(q[2], q[4], v.gx, v.sx, T(-1));
                 rotate1(q[1], q[5], v.gx, v.sx, T(1));
                 rotate1(q[2], q[3], v.gy, v.sy, T(1));
@@ -585,9 +592,9 @@ struct ZCol {
 
 template <typename T, int VM>
 __global__ void __launch_bounds__(128)
-k3_zcol(const T *__restrict__ in, T *__restrict__ out, const typename Coef<T>::C *__restrict__ kc,
-        const V3<T> *__restrict__ kv, int nx, int ny, int nz, int pitch, size_t plane_elems,
-        int seg) {
+k3_zcol(const T *__restrict__ in, T *__restrict__ out, const uint32_t *__restrict__ idx3,
+        const MedRec<T> *__restrict__ rec, const V3<T> *__restrict__ rv, int nx, int ny, int nz,
+        int pitch, size_t plane_elems, int seg) {
     ZCol<T, VM> m;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int x = int(t % nx), y = int(t / nx);
@@ -595,8 +602,9 @@ k3_zcol(const T *__restrict__ in, T *__restrict__ out, const typename Coef<T>::C
     m.live = t < (long long)nx * ny;
     m.in = in;
     m.out = out;
-    m.kc = kc;
-    m.kv = kv;
+    m.idx3 = idx3;
+    m.rec = rec;
+    m.rv = rv;
     m.col = size_t(y) * pitch + x;
     m.zstride = size_t(ny) * pitch;
     m.plane_elems = plane_elems;
@@ -606,6 +614,7 @@ k3_zcol(const T *__restrict__ in, T *__restrict__ out, const typename Coef<T>::C
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
         m.dring[l][0] = m.dring[l][1] = T(0);
+        m.iring[l] = 0;
 #pragma unroll
         for (int a = 0; a < 2; ++a) m.carry[l][a][0] = m.carry[l][a][1] = T(0);
     }
@@ -625,9 +634,9 @@ bool slices_ok(int nx, int ny, size_t plane_elems) {
 }
 
 template <typename T, int VM>
-cudaError_t slices_t(const void *in, void *out, const uint32_t *midx, const void *mrec,
-                     const void *kc, const void *kv, int nx, int ny, int nz, int pitch,
-                     size_t plane_elems, int num_sms, cudaStream_t st) {
+cudaError_t slices_t(const void *in, void *out, const uint32_t *idx3, const void *rec,
+                     const void *rv, int nx, int ny, int nz, int pitch, size_t plane_elems,
+                     int num_sms, cudaStream_t st) {
     using M = march::March<T, 6, 2, V_NONE, false>;
     const size_t smem = sizeof(typename M::Slot) * march::NSLOT * march::WARPS;
     auto k1 = k3_slices<T>;
@@ -654,8 +663,8 @@ cudaError_t slices_t(const void *in, void *out, const uint32_t *midx, const void
     const long long n_items = (long long)n_wx * n_wy * nz;
     const long long blocks = (n_items + march::WARPS - 1) / march::WARPS;
     k1<<<unsigned(blocks), 32 * march::WARPS, smem, st>>>(
-        static_cast<const T *>(in), static_cast<T *>(out), midx,
-        static_cast<const MedRec<T> *>(mrec), nx, ny, pitch, plane_elems, seg_h, n_wx, int(n_wy),
+        static_cast<const T *>(in), static_cast<T *>(out), idx3,
+        static_cast<const MedRec<T> *>(rec), nx, ny, pitch, plane_elems, seg_h, n_wx, int(n_wy),
         n_items);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -669,25 +678,82 @@ cudaError_t slices_t(const void *in, void *out, const uint32_t *midx, const void
     if (seg < 16) seg = 16;
     nseg = (nz + seg - 1) / seg;
     k3_zcol<T, VM><<<dim3(unsigned(cblocks), nseg), 128, 0, st>>>(
-        static_cast<const T *>(out), static_cast<T *>(const_cast<void *>(in)),
-        static_cast<const typename Coef<T>::C *>(kc), static_cast<const V3<T> *>(kv), nx, ny, nz,
-        pitch, plane_elems, seg);
+        static_cast<const T *>(out), static_cast<T *>(const_cast<void *>(in)), idx3,
+        static_cast<const MedRec<T> *>(rec), static_cast<const V3<T> *>(rv), nx, ny, nz, pitch,
+        plane_elems, seg);
     return cudaGetLastError();
 }
 
-// Records for the slices launch: the collision coefficient of each site in
-// MedRec form (its potential part unused), and the identity index of one
-// slice (every slice uses the same map).
+// Records for the register-resident step (kernel 2).  A site whose six
+// neighbours carry its own n has zero potential angles, and its record
+// depends on n alone: such sites share one record per distinct n through an
+// open-addressing table of UNIFORM_SLOTS keys (n's bits; n > 0, so a key is
+// never 0, the empty mark), and in a piecewise-uniform medium that is the
+// bulk of the lattice, whose records then stay in cache.  Every other site
+// gets its own record.  idx3 maps each stored site to its record; rec holds
+// the collision coefficient in MedRec form (read by the 2D marching
+// machinery; its potential part is unused) and rv the potential
+// coefficients.  Index values depend on scheduling, record contents do not.
 template <typename T>
-__global__ void k3_records(const typename Coef<T>::C *__restrict__ kc, size_t plane_elems,
-                           size_t slice_elems, MedRec<T> *__restrict__ rec,
-                           uint32_t *__restrict__ midx) {
-    for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < plane_elems;
+__global__ void k3_dedup(const double *__restrict__ n, int nx, int ny, int nz, int pitch,
+                         double delta, double vscale, unsigned long long *__restrict__ keys,
+                         unsigned *__restrict__ counter, uint32_t *__restrict__ idx3,
+                         MedRec<T> *__restrict__ rec, V3<T> *__restrict__ rv) {
+    namespace cg = cooperative_groups;
+    const size_t N = size_t(nx) * ny * nz;
+    for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < N;
          t += size_t(gridDim.x) * blockDim.x) {
-        MedRec<T> r{};
-        r.c = kc[t];
-        rec[t] = r;
-        if (t < slice_elems) midx[t] = uint32_t(t);
+        const int x = int(t % nx), y = int((t / nx) % ny), z = int(t / (size_t(nx) * ny));
+        const size_t g = at3(x, y, z, ny, pitch);
+        const double nn = n[g];
+        const double xp = n[at3(wrap(x + 1, nx), y, z, ny, pitch)];
+        const double xm = n[at3(wrap(x - 1, nx), y, z, ny, pitch)];
+        const double yp = n[at3(x, wrap(y + 1, ny), z, ny, pitch)];
+        const double ym = n[at3(x, wrap(y - 1, ny), z, ny, pitch)];
+        const double zp = n[at3(x, y, wrap(z + 1, nz), ny, pitch)];
+        const double zm = n[at3(x, y, wrap(z - 1, nz), ny, pitch)];
+        bool shared = xp == nn && xm == nn && yp == nn && ym == nn && zp == nn && zm == nn;
+        bool owner = false;
+        uint32_t id = 0;
+        if (shared) {
+            const unsigned long long key = static_cast<unsigned long long>(__double_as_longlong(nn));
+            unsigned h = unsigned(mix64(key)) & (UNIFORM_SLOTS - 1);
+            bool placed = false;
+            for (int probe = 0; probe < UNIFORM_SLOTS; ++probe) {
+                const unsigned long long prev = atomicCAS(&keys[h], 0ull, key);
+                if (prev == 0ull || prev == key) {
+                    owner = prev == 0ull;
+                    id = h;
+                    placed = true;
+                    break;
+                }
+                h = (h + 1) & (UNIFORM_SLOTS - 1);
+            }
+            shared = placed;  // a full table: fall back to an own record
+        }
+        if (!shared) {
+            cg::coalesced_group grp = cg::coalesced_threads();
+            unsigned base = 0;
+            if (grp.thread_rank() == 0) base = atomicAdd(counter, grp.size());
+            base = grp.shfl(base, 0);
+            id = UNIFORM_SLOTS + base + grp.thread_rank();
+            owner = true;
+        }
+        if (owner) {
+            // the expressions of k3_medium, so the coefficients are the same
+            const double bx = (xp - xm) / (2.0 * delta) / (nn * nn) * delta * delta;
+            const double by = (yp - ym) / (2.0 * delta) / (nn * nn) * delta * delta;
+            const double bz = (zp - zm) / (2.0 * delta) / (nn * nn) * delta * delta;
+            MedRec<T> r{};
+            coef_c(delta / (4.0 * nn), r.c);
+            rec[id] = r;
+            V3<T> v;
+            coef_v(vscale * bx, v.gx, v.sx);
+            coef_v(vscale * by, v.gy, v.sy);
+            coef_v(vscale * bz, v.gz, v.sz);
+            rv[id] = v;
+        }
+        idx3[g] = id;
     }
 }
 
@@ -707,8 +773,11 @@ struct qla3_ctx {
     int cur = 0;
     double *n = nullptr, *staging = nullptr, *partials = nullptr, *result = nullptr;
     void *kc = nullptr, *kv = nullptr;
-    void *mrec = nullptr;          // MedRec<T> per site (slices launch)
-    uint32_t *midx = nullptr;      // identity index of one slice
+    // kernel 2: per-site record index, records (shared where uniform)
+    uint32_t *idx3 = nullptr;
+    void *rec = nullptr, *rv = nullptr;
+    unsigned long long *keys = nullptr;
+    unsigned *counter = nullptr;
     int eblocks = 1;
     int num_sms = 1;
     int kernel = 0;   // 0: automatic, 1: fused march along z, 2: slices + column
@@ -722,7 +791,8 @@ struct qla3_ctx {
 namespace {
 
 struct Layout3 {
-    size_t state[2], n, staging, kc, kv, mrec, midx, partials, result, total, plane_elems;
+    size_t state[2], n, staging, kc, kv, idx3, rec, rv, keys, counter, partials, result, total,
+        plane_elems;
     int pitch, eblocks;
 };
 
@@ -752,8 +822,12 @@ Layout3 layout3(int nx, int ny, int nz, int prec) {
     L.kc = off;       off += al256(L.plane_elems * kcb);
     L.kv = off;       off += al256(L.plane_elems * kvb);
     const size_t recb = prec == QLA_FP64 ? sizeof(MedRec<double>) : sizeof(MedRec<float>);
-    L.mrec = off;     off += al256(L.plane_elems * recb);
-    L.midx = off;     off += al256(size_t(ny) * L.pitch * 4);
+    const size_t nrec = UNIFORM_SLOTS + sites;
+    L.idx3 = off;     off += al256(L.plane_elems * 4);
+    L.rec = off;      off += al256(nrec * recb);
+    L.rv = off;       off += al256(nrec * kvb);
+    L.keys = off;     off += al256(UNIFORM_SLOTS * 8);
+    L.counter = off;  off += al256(4);
     L.partials = off; off += al256(nb * 8);
     L.result = off;   off += al256(8);
     L.total = off;
@@ -797,9 +871,9 @@ cudaError_t step3_t(qla3_ctx *c) {
     if (kernel == 2 && slices_ok(nx, ny, pe)) {
         // the slices launch writes b; the column launch reads b, writes a
         cudaError_t e = c->vmode == V_ROTATION
-            ? slices_t<T, V_ROTATION>(a, b, c->midx, c->mrec, c->kc, c->kv, nx, ny, nz, pitch, pe,
+            ? slices_t<T, V_ROTATION>(a, b, c->idx3, c->rec, c->rv, nx, ny, nz, pitch, pe,
                                       c->num_sms, c->stream)
-            : slices_t<T, V_NONE>(a, b, c->midx, c->mrec, c->kc, c->kv, nx, ny, nz, pitch, pe,
+            : slices_t<T, V_NONE>(a, b, c->idx3, c->rec, c->rv, nx, ny, nz, pitch, pe,
                                   c->num_sms, c->stream);
         c->launches += 2;
         return e;   // the result is back in state[cur]
@@ -871,8 +945,11 @@ qla_status qla3_init(qla3_ctx **out, int nx, int ny, int nz, double delta, int p
     c->staging = reinterpret_cast<double *>(c->ws + L.staging);
     c->kc = c->ws + L.kc;
     c->kv = c->ws + L.kv;
-    c->mrec = c->ws + L.mrec;
-    c->midx = reinterpret_cast<uint32_t *>(c->ws + L.midx);
+    c->idx3 = reinterpret_cast<uint32_t *>(c->ws + L.idx3);
+    c->rec = c->ws + L.rec;
+    c->rv = c->ws + L.rv;
+    c->keys = reinterpret_cast<unsigned long long *>(c->ws + L.keys);
+    c->counter = reinterpret_cast<unsigned *>(c->ws + L.counter);
     c->partials = reinterpret_cast<double *>(c->ws + L.partials);
     c->result = reinterpret_cast<double *>(c->ws + L.result);
     c->eblocks = L.eblocks;
@@ -912,15 +989,16 @@ qla_status qla3_set_medium(qla3_ctx *c, const double *n_host) {
             c->n, c->nx, c->ny, c->nz, c->pitch, c->delta, vscale,
             static_cast<float4 *>(c->kc), static_cast<V3<float> *>(c->kv));
     CUDA3(c, cudaGetLastError(), "qla3_set_medium: kernel");
-    const size_t slice = size_t(c->ny) * c->pitch;
+    CUDA3(c, cudaMemsetAsync(c->keys, 0, UNIFORM_SLOTS * 8, c->stream), "qla3_set_medium: clear");
+    CUDA3(c, cudaMemsetAsync(c->counter, 0, 4, c->stream), "qla3_set_medium: clear");
     if (c->prec == QLA_FP64)
-        k3_records<double><<<blocks, 256, 0, c->stream>>>(
-            static_cast<const double2 *>(c->kc), c->plane_elems, slice,
-            static_cast<MedRec<double> *>(c->mrec), c->midx);
+        k3_dedup<double><<<blocks, 256, 0, c->stream>>>(
+            c->n, c->nx, c->ny, c->nz, c->pitch, c->delta, vscale, c->keys, c->counter, c->idx3,
+            static_cast<MedRec<double> *>(c->rec), static_cast<V3<double> *>(c->rv));
     else
-        k3_records<float><<<blocks, 256, 0, c->stream>>>(
-            static_cast<const float4 *>(c->kc), c->plane_elems, slice,
-            static_cast<MedRec<float> *>(c->mrec), c->midx);
+        k3_dedup<float><<<blocks, 256, 0, c->stream>>>(
+            c->n, c->nx, c->ny, c->nz, c->pitch, c->delta, vscale, c->keys, c->counter, c->idx3,
+            static_cast<MedRec<float> *>(c->rec), static_cast<V3<float> *>(c->rv));
     CUDA3(c, cudaGetLastError(), "qla3_set_medium: records");
     c->launches += 3;
     CUDA3(c, cudaStreamSynchronize(c->stream), "qla3_set_medium: sync");

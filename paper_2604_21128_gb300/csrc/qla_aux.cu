@@ -46,14 +46,6 @@ __device__ __forceinline__ void make_rec(MedRec<float> &r, double th, double px,
                       __double2float_rn(2.0 * shy * shy), __double2float_rn(sin(py)));
 }
 
-__device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
-    k ^= k >> 33;
-    k *= 0xff51afd7ed558ccdull;
-    k ^= k >> 33;
-    k *= 0xc4ceb9fe1a85ec53ull;
-    k ^= k >> 33;
-    return k;
-}
 
 // One pass over the sites: classify, hand out a record index, write each
 // record once.  A site whose four neighbours carry exactly its n has beta = 0

@@ -80,6 +80,17 @@ template <typename T> struct MedRec {
 };
 constexpr int UNIFORM_SLOTS = 4096;  // open-addressing slots for shared records
 
+// 64-bit finaliser that spreads a key's bits before it picks a slot of the
+// shared-record table (the key is the bit pattern of a site's n).
+__device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
 // (a, b) <- [[c, -g s], [g s, c]] (a, b) with g = +-1.
 // Explicit FMAs fix the rounding, so every kernel produces the same bits.
 __device__ __forceinline__ void rotate(double &a, double &b, double2 k, double g) {
