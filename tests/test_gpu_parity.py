@@ -309,3 +309,34 @@ def test_full_size_16384_bubble_sampled_sites():
         want = oracle.run_window(n, w.delta, pk, steps, (int(ii[k]), int(jj[k])), half)
         assert np.max(np.abs(got[k] - want)) <= 2e-5, (ii[k], jj[k], got[k], want)
     assert np.any(np.abs(got[:6, 2]) > 1e-3)      # the packet is in the sample
+
+
+def test_full_size_8192_fp64_six_planes_sampled_sites():
+    """The 8192^2 workload in FP64 with all six planes evolving (3.2 GB of
+    state), 12 steps in the default launch configuration; sampled sites in
+    the packet, on the ellipse and at the wrap-around edges against the
+    oracle on a periodic window around each (exact inside the dependence
+    cone), to FP64 rounding."""
+    w = inputs.ellipse_8192()
+    steps = 12
+    n = w.medium()
+    pk = w.packet.as_dict()
+    rng = np.random.default_rng(8192)
+    x0 = int(pk["x0"])
+    ii = np.concatenate([x0 + rng.integers(-400, 400, 6), w.nx // 2 + rng.integers(-1300, 1300, 4),
+                         [0, w.nx - 1]])
+    jj = np.concatenate([rng.integers(0, w.ny, 6), w.ny // 2 + rng.integers(-700, 700, 4),
+                         [w.ny - 1, 0]])
+    with qla.Grid(w.nx, w.ny, w.delta, "fp64") as g:
+        g.set_medium(n)
+        g.set_packet(**pk)
+        g.step(steps)
+        got = g.probe(ii, jj)
+    half = oracle.reach_per_step() * steps + 2
+    scale = 0.0
+    for k in range(len(ii)):
+        want = oracle.run_window(n, w.delta, pk, steps, (int(ii[k]), int(jj[k])), half)
+        scale = max(scale, float(np.max(np.abs(want))))
+        assert np.max(np.abs(got[k] - want)) <= 1e-12 * max(1.0, float(np.max(np.abs(want)))), \
+            (ii[k], jj[k], got[k], want)
+    assert scale > 1e-3      # the packet is in the sample
