@@ -64,6 +64,7 @@ def _load():
         lib.orc_run_aniso.restype = i
         lib.orc3_run.argtypes = [i, i, i, d, dp, dp, ll, i]
         lib.orc3_run.restype = i
+        lib.orc3_divergence.argtypes = [i, i, i, d, dp, dp, dp]
         lib.orc_packet.argtypes = [i, i, d, i, i, i, i, dp, d, d, d, d, d, d, d, dp]
         lib.orc_set_threads.argtypes = [i]
         lib.orc_get_threads.restype = i
@@ -185,6 +186,18 @@ def run3(q, n, delta, steps, vmode="rotation"):
     if rc != 0:
         raise ValueError("orc3_run failed (reading not available in 3D, or no memory)")
     return q
+
+
+def divergence3(q, n, delta):
+    """3D Gauss-law monitors: as divergence(), with the z terms d_z q5 in
+    div B and d_z (n q2) in div D.  q (6, nz, ny, nx), n (nz, ny, nx)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    nz, ny, nx = n.shape
+    out = np.empty(6)
+    _load().orc3_divergence(nx, ny, nz, float(delta), _ptr(n), _ptr(q), _ptr(out))
+    keys = ("div_b_sq", "grad_b_sq", "div_d_sq", "grad_d_sq", "div_b_max", "div_d_max")
+    return dict(zip(keys, (float(v) for v in out)))
 
 
 def angles_aniso(n, delta):

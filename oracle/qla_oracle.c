@@ -583,6 +583,45 @@ int orc3_run(int nx, int ny, int nz, double delta, const double *n, double *q,
     return 0;
 }
 
+/* Gauss laws (Eqs. 3.1, 3.2) in 3D with centred periodic differences:
+ * div B = d_x q3 + d_y q4 + d_z q5, div D = d_x (n q0) + d_y (n q1) + d_z (n q2)
+ * (D = n^2 E = n q_E).  out as orc_divergence: sums of (div B)^2, of the
+ * squared diagonal derivatives of B, the same two for D, max |div B|,
+ * max |div D|. */
+void orc3_divergence(int nx, int ny, int nz, double delta, const double *n, const double *q,
+                     double *out)
+{
+    size_t N = (size_t)nx * ny * nz;
+    const double h = 0.5 / delta;
+    double sb = 0.0, gb = 0.0, sd = 0.0, gd = 0.0, mb = 0.0, md = 0.0;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t xp = SITE3((i + 1) % nx, j, k), xm = SITE3((i + nx - 1) % nx, j, k);
+                size_t yp = SITE3(i, (j + 1) % ny, k), ym = SITE3(i, (j + ny - 1) % ny, k);
+                size_t zp = SITE3(i, j, (k + 1) % nz), zm = SITE3(i, j, (k + nz - 1) % nz);
+                double bx = h * (q[3 * N + xp] - q[3 * N + xm]);
+                double by = h * (q[4 * N + yp] - q[4 * N + ym]);
+                double bz = h * (q[5 * N + zp] - q[5 * N + zm]);
+                double dx = h * (n[xp] * q[0 * N + xp] - n[xm] * q[0 * N + xm]);
+                double dy = h * (n[yp] * q[1 * N + yp] - n[ym] * q[1 * N + ym]);
+                double dz = h * (n[zp] * q[2 * N + zp] - n[zm] * q[2 * N + zm]);
+                double db = bx + by + bz, dd = dx + dy + dz;
+                sb += db * db;
+                gb += bx * bx + by * by + bz * bz;
+                sd += dd * dd;
+                gd += dx * dx + dy * dy + dz * dz;
+                if (fabs(db) > mb) mb = fabs(db);
+                if (fabs(dd) > md) md = fabs(dd);
+            }
+    out[0] = sb;
+    out[1] = gb;
+    out[2] = sd;
+    out[3] = gd;
+    out[4] = mb;
+    out[5] = md;
+}
+
 /* ------------------------------------------------------------------ */
 /* Energy (Eq. A13), fields (inverse of Eq. 3b3), initial packet       */
 /* ------------------------------------------------------------------ */

@@ -40,6 +40,8 @@ void orc_fields_aniso(int nx, int ny, const double *n_x, const double *n_y,
                       const double *n_z, const double *q, double *out);
 void orc_angles_aniso(int nx, int ny, double delta, const double *n_x, const double *n_y,
                       const double *n_z, double *ang);
+void orc3_divergence(int nx, int ny, int nz, double delta, const double *n, const double *q,
+                     double *out);
 int orc3_run(int nx, int ny, int nz, double delta, const double *n, double *q,
              long long steps, int vmode);
 int orc_run_aniso(int nx, int ny, double delta, const double *n_x, const double *n_y,

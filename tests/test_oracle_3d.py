@@ -110,3 +110,59 @@ def test_energy_conserved_in_3d():
     q = rng.standard_normal((6, 6, 10, 12))
     qT = oracle.run3(q, n, 1.0, 20)
     assert abs(np.sum(qT ** 2) / np.sum(q ** 2) - 1) < 1e-13
+
+
+def _plane3(nx, ny, nz, m):
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    kx, ky, kz = (2 * math.pi * m[0] / nx, 2 * math.pi * m[1] / ny, 2 * math.pi * m[2] / nz)
+    return kx, ky, kz, np.sin(kx * x + ky * y + kz * z)
+
+
+@pytest.mark.parametrize("delta", [1.0, 0.5])
+def test_divergence3_closed_form(delta):
+    """B = D = (s, s, s), s = sin(k.r): div = cos(k.r)(sin kx + sin ky + sin kz)/delta,
+    so the sums are N/2 (sum of sines)^2 / delta^2 and N/2 (sum of squared
+    sines) / delta^2; D enters as n q (q_E = s / n)."""
+    nx, ny, nz = 20, 12, 16
+    kx, ky, kz, s = _plane3(nx, ny, nz, (3, 2, 5))
+    rng = np.random.default_rng(2)
+    n = 1.0 + rng.random((nz, ny, nx))
+    q = np.zeros((6, nz, ny, nx))
+    q[3] = q[4] = q[5] = s
+    q[0] = q[1] = q[2] = s / n
+    d = oracle.divergence3(q, n, delta)
+    N = nx * ny * nz
+    sines = (math.sin(kx), math.sin(ky), math.sin(kz))
+    for key in ("b", "d"):
+        assert d["div_%s_sq" % key] == pytest.approx(N / 2 * sum(sines) ** 2 / delta ** 2, rel=1e-12)
+        assert d["grad_%s_sq" % key] == pytest.approx(N / 2 * sum(v * v for v in sines)
+                                                       / delta ** 2, rel=1e-12)
+
+
+def test_divergence3_of_a_discrete_curl_is_zero():
+    """B = curl A and D = curl A (q_E = (curl A)/n) with centred differences:
+    the differences commute, so both divergences vanish to rounding."""
+    nx, ny, nz, delta = 13, 11, 9, 0.7
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((3, nz, ny, nx))
+    n = 1.0 + rng.random((nz, ny, nx))
+    d = lambda f, ax: (np.roll(f, -1, ax) - np.roll(f, 1, ax)) / (2 * delta)   # ax: 2 x, 1 y, 0 z
+    curl = np.array([d(A[2], 1) - d(A[1], 0), d(A[0], 0) - d(A[2], 2), d(A[1], 2) - d(A[0], 1)])
+    q = np.zeros((6, nz, ny, nx))
+    q[3:6] = curl
+    q[0:3] = curl / n
+    r = oracle.divergence3(q, n, delta)
+    assert r["div_b_sq"] <= 1e-28 * r["grad_b_sq"]
+    assert r["div_d_sq"] <= 1e-28 * r["grad_d_sq"]
+    assert r["grad_b_sq"] > 1.0
+
+
+def test_divergence3_of_z_uniform_fields_is_the_2d_one():
+    nx, ny, nz = 24, 20, 5
+    n2 = inputs.random_medium(nx, ny, seed=9, lo=1.0, hi=3.0)
+    q2 = inputs.random_state(nx, ny, seed=10)
+    d3 = oracle.divergence3(np.repeat(q2[:, None], nz, axis=1), np.repeat(n2[None], nz, axis=0), 0.8)
+    d2 = oracle.divergence(q2, n2, 0.8)
+    for k in ("div_b_sq", "grad_b_sq", "div_d_sq", "grad_d_sq"):
+        assert d3[k] == pytest.approx(nz * d2[k], rel=1e-12)
+    assert d3["div_b_max"] == pytest.approx(d2["div_b_max"], rel=1e-12)
