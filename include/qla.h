@@ -453,6 +453,14 @@ qla_status qla3_energy(qla3_ctx *ctx, double *out);
  * QLA_EINVAL for other values. */
 qla_status qla3_set_step_kernel(qla3_ctx *ctx, int kernel);
 
+/* Gauss-law monitors in 3D (Eqs. 3.1, 3.2; the paper monitors them in its
+ * 3D runs): div B = d_x q3 + d_y q4 + d_z q5, div D = d_x(n q0) + d_y(n q1)
+ * + d_z(n q2), centred periodic differences; out[6] as qla_divergence
+ * (sums of (div B)^2, of (d_x B_x)^2 + (d_y B_y)^2 + (d_z B_z)^2, the same
+ * two for D, max |div B|, max |div D|), FP64.  Synchronises; QLA_ESTATE
+ * without medium and state, QLA_ENONFINITE if a term is not finite. */
+qla_status qla3_divergence(qla3_ctx *ctx, double *out);
+
 long long qla3_launch_count(const qla3_ctx *ctx);
 const char *qla3_last_error(const qla3_ctx *ctx);
 void qla3_destroy(qla3_ctx *ctx);

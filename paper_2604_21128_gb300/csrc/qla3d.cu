@@ -757,6 +757,86 @@ __global__ void k3_dedup(const double *__restrict__ n, int nx, int ny, int nz, i
     }
 }
 
+// Gauss laws in 3D (Eqs. 3.1, 3.2; the monitors the paper keeps in its 3D
+// runs): div B = d_x q3 + d_y q4 + d_z q5, div D = d_x (n q0) + d_y (n q1)
+// + d_z (n q2), centred periodic differences, FP64 sums per block of the
+// squares and of the squared diagonal derivatives, and the maxima.
+__device__ __forceinline__ double bsum3(double v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    v = threadIdx.x < blockDim.x / 32 ? sh[threadIdx.x] : 0.0;
+    if (threadIdx.x < 32)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    return v;
+}
+__device__ __forceinline__ double bmax3(double v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    v = threadIdx.x < blockDim.x / 32 ? sh[threadIdx.x] : 0.0;
+    if (threadIdx.x < 32)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    __syncthreads();
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k3_div(const T *__restrict__ q, const double *__restrict__ n, int nx, int ny, int nz, int pitch,
+       size_t plane_elems, double h, double *__restrict__ partials) {
+    __shared__ double sh[8];
+    const size_t N = size_t(nx) * ny * nz;
+    double sb = 0.0, gb = 0.0, sd = 0.0, gd = 0.0, mb = 0.0, md = 0.0;
+    for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < N;
+         t += size_t(gridDim.x) * blockDim.x) {
+        const int x = int(t % nx), y = int((t / nx) % ny), z = int(t / (size_t(nx) * ny));
+        const size_t xp = at3(wrap(x + 1, nx), y, z, ny, pitch), xm = at3(wrap(x - 1, nx), y, z, ny, pitch);
+        const size_t yp = at3(x, wrap(y + 1, ny), z, ny, pitch), ym = at3(x, wrap(y - 1, ny), z, ny, pitch);
+        const size_t zp = at3(x, y, wrap(z + 1, nz), ny, pitch), zm = at3(x, y, wrap(z - 1, nz), ny, pitch);
+        const double bx = h * (double(q[3 * plane_elems + xp]) - double(q[3 * plane_elems + xm]));
+        const double by = h * (double(q[4 * plane_elems + yp]) - double(q[4 * plane_elems + ym]));
+        const double bz = h * (double(q[5 * plane_elems + zp]) - double(q[5 * plane_elems + zm]));
+        const double dx = h * (n[xp] * double(q[xp]) - n[xm] * double(q[xm]));
+        const double dy = h * (n[yp] * double(q[plane_elems + yp]) - n[ym] * double(q[plane_elems + ym]));
+        const double dz = h * (n[zp] * double(q[2 * plane_elems + zp]) -
+                               n[zm] * double(q[2 * plane_elems + zm]));
+        const double db = bx + by + bz, dd = dx + dy + dz;
+        sb = fma(db, db, sb);
+        gb = fma(bx, bx, fma(by, by, fma(bz, bz, gb)));
+        sd = fma(dd, dd, sd);
+        gd = fma(dx, dx, fma(dy, dy, fma(dz, dz, gd)));
+        mb = fmax(mb, fabs(db));
+        md = fmax(md, fabs(dd));
+    }
+    const double r0 = bsum3(sb, sh), r1 = bsum3(gb, sh), r2 = bsum3(sd, sh), r3 = bsum3(gd, sh);
+    const double r4 = bmax3(mb, sh), r5 = bmax3(md, sh);
+    if (threadIdx.x == 0) {
+        double *p = partials + size_t(blockIdx.x) * 6;
+        p[0] = r0; p[1] = r1; p[2] = r2; p[3] = r3; p[4] = r4; p[5] = r5;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k3_div_final(const double *__restrict__ partials, int count, double *__restrict__ out) {
+    __shared__ double sh[8];
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int t = threadIdx.x; t < count; t += blockDim.x)
+        for (int k = 0; k < 6; ++k) {
+            const double p = partials[size_t(t) * 6 + k];
+            v[k] = k < 4 ? v[k] + p : fmax(v[k], p);
+        }
+    double r[6];
+    for (int k = 0; k < 6; ++k) r[k] = k < 4 ? bsum3(v[k], sh) : bmax3(v[k], sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 6; ++k) out[k] = r[k];
+}
+
 }  // namespace
 }  // namespace qla
 
@@ -828,8 +908,8 @@ Layout3 layout3(int nx, int ny, int nz, int prec) {
     L.rv = off;       off += al256(nrec * kvb);
     L.keys = off;     off += al256(UNIFORM_SLOTS * 8);
     L.counter = off;  off += al256(4);
-    L.partials = off; off += al256(nb * 8);
-    L.result = off;   off += al256(8);
+    L.partials = off; off += al256(nb * 8 * 6);   // six terms per block (divergence)
+    L.result = off;   off += al256(8 * 6);
     L.total = off;
     return L;
 }
@@ -1081,6 +1161,34 @@ qla_status qla3_set_step_kernel(qla3_ctx *c, int kernel) {
     if (kernel < 0 || kernel > 3)
         return fail3(c, QLA_EINVAL, "qla3_set_step_kernel: kernel must be 0..3, got %d", kernel);
     c->kernel = kernel;
+    return QLA_OK;
+}
+
+qla_status qla3_divergence(qla3_ctx *c, double *out) {
+    qla_status s = usable3(c);
+    if (s != QLA_OK) return s;
+    if (!out) return fail3(c, QLA_EINVAL, "qla3_divergence: null output");
+    if (!c->has_state || !c->has_medium)
+        return fail3(c, QLA_ESTATE, "qla3_divergence: needs medium and state");
+    const double h = 0.5 / c->delta;
+    if (c->prec == QLA_FP64)
+        k3_div<double><<<c->eblocks, 256, 0, c->stream>>>(
+            static_cast<const double *>(c->state[c->cur]), c->n, c->nx, c->ny, c->nz, c->pitch,
+            c->plane_elems, h, c->partials);
+    else
+        k3_div<float><<<c->eblocks, 256, 0, c->stream>>>(
+            static_cast<const float *>(c->state[c->cur]), c->n, c->nx, c->ny, c->nz, c->pitch,
+            c->plane_elems, h, c->partials);
+    CUDA3(c, cudaGetLastError(), "qla3_divergence: kernel");
+    k3_div_final<<<1, 256, 0, c->stream>>>(c->partials, c->eblocks, c->result);
+    CUDA3(c, cudaGetLastError(), "qla3_divergence: final");
+    c->launches += 2;
+    CUDA3(c, cudaMemcpyAsync(out, c->result, 6 * 8, cudaMemcpyDeviceToHost, c->stream),
+          "qla3_divergence: copy");
+    CUDA3(c, cudaStreamSynchronize(c->stream), "qla3_divergence: sync");
+    for (int k = 0; k < 6; ++k)
+        if (!std::isfinite(out[k]))
+            return fail3(c, QLA_ENONFINITE, "qla3_divergence: term %d is %g", k, out[k]);
     return QLA_OK;
 }
 

@@ -81,7 +81,8 @@ def load():
         lib.qla3_init.restype = c_int
         for name, args in (("qla3_set_medium", [c_vp, c_vp]), ("qla3_set_state", [c_vp, c_vp]),
                            ("qla3_get_state", [c_vp, c_vp]), ("qla3_step", [c_vp, c_ll]),
-                           ("qla3_energy", [c_vp, _DP]), ("qla3_set_step_kernel", [c_vp, c_int])):
+                           ("qla3_energy", [c_vp, _DP]), ("qla3_set_step_kernel", [c_vp, c_int]),
+                           ("qla3_divergence", [c_vp, c_vp])):
             getattr(lib, name).argtypes = args
             getattr(lib, name).restype = c_int
         lib.qla3_launch_count.argtypes = [c_vp]
@@ -575,6 +576,12 @@ class Grid3:
         v = ctypes.c_double()
         self._check(load().qla3_energy(self._ctx, ctypes.byref(v)))
         return v.value
+
+    def divergence(self):
+        """3D Gauss-law monitors, a dict with the keys of DIV_KEYS."""
+        out = np.empty(6)
+        self._check(load().qla3_divergence(self._ctx, ctypes.c_void_p(out.ctypes.data)))
+        return dict(zip(DIV_KEYS, (float(v) for v in out)))
 
     @property
     def launches(self):

@@ -112,3 +112,41 @@ def test_errors():
         with pytest.raises(qla.QLAError) as e:
             g.set_medium(np.zeros((8, 8, 8)))
         assert e.value.status == 1                                 # QLA_EINVAL
+
+
+@pytest.mark.parametrize("precision,rel", [("fp64", 1e-10), ("fp32", 2e-5)])
+@pytest.mark.parametrize("shape", [(24, 20, 6), (70, 40, 36)])
+def test_divergence_matches_oracle(shape, precision, rel):
+    nx, ny, nz = shape
+    n = medium3(nx, ny, nz, seed=21)
+    q0 = np.random.default_rng(22).standard_normal((6, nz, ny, nx))
+    want = oracle.divergence3(oracle.run3(q0, n, 0.8, 3), n, 0.8)
+    with qla.Grid3(nx, ny, nz, 0.8, precision) as g:
+        g.set_medium(n)
+        g.set_state(q0)
+        g.step(3)
+        got = g.divergence()
+    for k in qla.DIV_KEYS:
+        assert got[k] == pytest.approx(want[k], rel=rel), (k, got[k], want[k])
+
+
+def test_divergence_closed_form_through_the_abi():
+    """B = D = (s, s, s), s = sin(k.r), on a padded lattice (nx = 40)."""
+    import math
+    nx, ny, nz, delta = 40, 12, 16, 0.5
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    k = (2 * math.pi * 3 / nx, 2 * math.pi * 2 / ny, 2 * math.pi * 5 / nz)
+    s = np.sin(k[0] * x + k[1] * y + k[2] * z)
+    n = 1.5 + 0.25 * np.cos(2 * math.pi * x / nx)
+    q = np.zeros((6, nz, ny, nx))
+    q[3] = q[4] = q[5] = s
+    q[0] = q[1] = q[2] = s / n
+    with qla.Grid3(nx, ny, nz, delta, "fp64") as g:
+        g.set_medium(n)
+        g.set_state(q)
+        d = g.divergence()
+    N = nx * ny * nz
+    sines = [math.sin(v) for v in k]
+    assert d["div_b_sq"] == pytest.approx(N / 2 * sum(sines) ** 2 / delta ** 2, rel=1e-12)
+    assert d["grad_b_sq"] == pytest.approx(N / 2 * sum(v * v for v in sines) / delta ** 2, rel=1e-12)
+    assert d["div_d_sq"] == pytest.approx(d["div_b_sq"], rel=1e-12)
