@@ -430,6 +430,12 @@ qla_status qla3_set_medium(qla3_ctx *ctx, const double *n_host);
 qla_status qla3_set_state(qla3_ctx *ctx, const double *q_host);
 qla_status qla3_get_state(qla3_ctx *ctx, double *q_host);
 
+/* The E_z packet of qla_set_packet (Sec. V-B), uniform along z: every
+ * slice holds the 2D packet on the current medium (q2 = n E_z,
+ * q3 = sin(angle) q2, q4 = -cos(angle) q2, q0 = q1 = q5 = 0).  QLA_ESTATE
+ * without a medium; QLA_EINVAL as for qla_set_packet. */
+qla_status qla3_set_packet(qla3_ctx *ctx, const qla_packet *p);
+
 /* Advance n_steps steps (see qla3_set_step_kernel for the launches);
  * asynchronous on the context's stream.  QLA_ESTATE without
  * medium and state. */

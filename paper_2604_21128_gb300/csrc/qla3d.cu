@@ -757,6 +757,39 @@ __global__ void k3_dedup(const double *__restrict__ n, int nx, int ny, int nz, i
     }
 }
 
+// The E_z packet of Sec. V-B, uniform along z: per slice exactly the 2D
+// packet (minimum-image xi, eta in the x-y plane, q2 = n E_z, q3 = sin(phi)
+// q2, q4 = -cos(phi) q2, the other planes zero).
+__device__ __forceinline__ double min_image3(double x, double x0, double L) {
+    double d = fmod(x - x0 + 0.5 * L, L);
+    if (d < 0.0) d += L;
+    return d - 0.5 * L;
+}
+
+template <typename T>
+__global__ void k3_packet(const double *__restrict__ n, T *__restrict__ q, int nx, int ny, int nz,
+                          int pitch, size_t plane_elems, double delta, qla_packet p, double cphi,
+                          double sphi) {
+    const size_t N = size_t(nx) * ny * nz;
+    const double Lx = nx * delta, Ly = ny * delta;
+    for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < N;
+         t += size_t(gridDim.x) * blockDim.x) {
+        const int x = int(t % nx), y = int((t / nx) % ny), z = int(t / (size_t(nx) * ny));
+        const size_t g = at3(x, y, z, ny, pitch);
+        const double dx = min_image3(x * delta, p.x0, Lx);
+        const double dy = min_image3(y * delta, p.y0, Ly);
+        const double xi = dx * cphi + dy * sphi;
+        const double eta = -dx * sphi + dy * cphi;
+        double ez = p.amplitude * exp(-(xi * xi) / (p.width * p.width)) * cos(p.k0 * xi);
+        if (p.transverse_width > 0.0)
+            ez *= exp(-(eta * eta) / (p.transverse_width * p.transverse_width));
+        const double q2 = n[g] * ez;
+        q[2 * plane_elems + g] = T(q2);
+        q[3 * plane_elems + g] = T(sphi * q2);
+        q[4 * plane_elems + g] = T(-cphi * q2);
+    }
+}
+
 // Gauss laws in 3D (Eqs. 3.1, 3.2; the monitors the paper keeps in its 3D
 // runs): div B = d_x q3 + d_y q4 + d_z q5, div D = d_x (n q0) + d_y (n q1)
 // + d_z (n q2), centred periodic differences, FP64 sums per block of the
@@ -1161,6 +1194,37 @@ qla_status qla3_set_step_kernel(qla3_ctx *c, int kernel) {
     if (kernel < 0 || kernel > 3)
         return fail3(c, QLA_EINVAL, "qla3_set_step_kernel: kernel must be 0..3, got %d", kernel);
     c->kernel = kernel;
+    return QLA_OK;
+}
+
+qla_status qla3_set_packet(qla3_ctx *c, const qla_packet *p) {
+    qla_status s = usable3(c);
+    if (s != QLA_OK) return s;
+    if (!p) return fail3(c, QLA_EINVAL, "qla3_set_packet: null packet");
+    const double v[7] = {p->x0, p->y0, p->angle, p->k0, p->width, p->transverse_width,
+                         p->amplitude};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail3(c, QLA_EINVAL, "qla3_set_packet: non-finite field");
+    if (!(p->width > 0.0) || p->transverse_width < 0.0)
+        return fail3(c, QLA_EINVAL, "qla3_set_packet: width must be > 0, transverse_width >= 0");
+    if (!c->has_medium) return fail3(c, QLA_ESTATE, "qla3_set_packet: set the medium first");
+    const size_t elt = c->prec == QLA_FP64 ? 8 : 4;
+    CUDA3(c, cudaMemsetAsync(c->state[c->cur], 0, c->plane_elems * elt * 6, c->stream),
+          "qla3_set_packet: clear");
+    const size_t N = size_t(c->nx) * c->ny * c->nz;
+    const int blocks = int(std::min<size_t>((N + 255) / 256, size_t(65535) * 16));
+    const double cphi = cos(p->angle), sphi = sin(p->angle);
+    if (c->prec == QLA_FP64)
+        k3_packet<double><<<blocks, 256, 0, c->stream>>>(
+            c->n, static_cast<double *>(c->state[c->cur]), c->nx, c->ny, c->nz, c->pitch,
+            c->plane_elems, c->delta, *p, cphi, sphi);
+    else
+        k3_packet<float><<<blocks, 256, 0, c->stream>>>(
+            c->n, static_cast<float *>(c->state[c->cur]), c->nx, c->ny, c->nz, c->pitch,
+            c->plane_elems, c->delta, *p, cphi, sphi);
+    CUDA3(c, cudaGetLastError(), "qla3_set_packet: kernel");
+    c->launches++;
+    c->has_state = true;
     return QLA_OK;
 }
 

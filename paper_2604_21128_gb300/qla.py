@@ -82,7 +82,8 @@ def load():
         for name, args in (("qla3_set_medium", [c_vp, c_vp]), ("qla3_set_state", [c_vp, c_vp]),
                            ("qla3_get_state", [c_vp, c_vp]), ("qla3_step", [c_vp, c_ll]),
                            ("qla3_energy", [c_vp, _DP]), ("qla3_set_step_kernel", [c_vp, c_int]),
-                           ("qla3_divergence", [c_vp, c_vp])):
+                           ("qla3_divergence", [c_vp, c_vp]),
+                           ("qla3_set_packet", [c_vp, ctypes.POINTER(qla_packet)])):
             getattr(lib, name).argtypes = args
             getattr(lib, name).restype = c_int
         lib.qla3_launch_count.argtypes = [c_vp]
@@ -552,6 +553,11 @@ class Grid3:
         a = np.ascontiguousarray(n, dtype=np.float64)
         assert a.size == self.sites
         self._check(load().qla3_set_medium(self._ctx, ctypes.c_void_p(a.ctypes.data)))
+
+    def set_packet(self, x0, y0, angle, k0, width, transverse_width=0.0, amplitude=1.0):
+        """The E_z packet of Grid.set_packet, uniform along z."""
+        p = qla_packet(x0, y0, angle, k0, width, transverse_width, amplitude)
+        self._check(load().qla3_set_packet(self._ctx, ctypes.byref(p)))
 
     def set_state(self, q):
         a = np.ascontiguousarray(q, dtype=np.float64)

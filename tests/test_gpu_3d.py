@@ -150,3 +150,17 @@ def test_divergence_closed_form_through_the_abi():
     assert d["div_b_sq"] == pytest.approx(N / 2 * sum(sines) ** 2 / delta ** 2, rel=1e-12)
     assert d["grad_b_sq"] == pytest.approx(N / 2 * sum(v * v for v in sines) / delta ** 2, rel=1e-12)
     assert d["div_d_sq"] == pytest.approx(d["div_b_sq"], rel=1e-12)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-14), ("fp32", 2e-7)])
+def test_packet_is_the_2d_packet_in_every_slice(precision, tol):
+    nx, ny, nz = 80, 48, 6
+    n = medium3(nx, ny, nz, seed=31)
+    pk = dict(x0=20.0, y0=30.0, angle=0.4, k0=0.3, width=8.0, transverse_width=12.0)
+    want = np.stack([oracle.packet(n[k], 1.0, **pk) for k in range(nz)], axis=1)
+    with qla.Grid3(nx, ny, nz, 1.0, precision) as g:
+        g.set_medium(n)
+        g.set_packet(**pk)
+        got = g.get_state()
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+    assert np.all(got[[0, 1, 5]] == 0)
