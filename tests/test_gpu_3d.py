@@ -164,3 +164,19 @@ def test_packet_is_the_2d_packet_in_every_slice(precision, tol):
         got = g.get_state()
     assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
     assert np.all(got[[0, 1, 5]] == 0)
+
+
+def test_packet_errors():
+    with qla.Grid3(8, 8, 8, 1.0, "fp32") as g:
+        with pytest.raises(qla.QLAError) as e:
+            g.set_packet(x0=2.0, y0=2.0, angle=0.0, k0=0.3, width=2.0)
+        assert e.value.status == 2                                 # no medium yet
+        g.set_medium(np.ones((8, 8, 8)))
+        for bad in (dict(width=0.0), dict(width=2.0, transverse_width=-1.0),
+                    dict(width=float("nan")), dict(width=2.0, amplitude=float("inf"))):
+            with pytest.raises(qla.QLAError) as e:
+                g.set_packet(x0=2.0, y0=2.0, angle=0.0, k0=0.3, **bad)
+            assert e.value.status == 1
+        g.set_packet(x0=2.0, y0=2.0, angle=0.0, k0=0.3, width=2.0)
+        g.step(2)
+        assert g.energy() > 0
