@@ -1,169 +1,23 @@
-// Convolution kernels of the learned surrogate: 3x3 periodic convolution as
-// an implicit GEMM on the tensor cores (forward, and input gradient with
-// flipped, transposed weights), weight gradient as a split-K GEMM over the
-// pixels with a fixed-order reduction, and the elementwise kernels around
-// them.  All tensors are NHWC; channel counts are multiples of 32.
+// Convolution kernels of the learned surrogate: the 3x3 periodic convolution
+// (forward, and input gradient with flipped, transposed weights) runs on the
+// tcgen05 tensor cores (surr_conv_tc.cu); here are the weight gradient as a
+// split-K GEMM over the pixels (warp-level mma.sync) with a fixed-order
+// reduction, and the elementwise kernels around them.  All tensors are NHWC;
+// channel counts are multiples of 32.
 #include "surr_internal.h"
 
 namespace surr {
 
 // ---------------------------------------------------------------------------
-// Forward / input-gradient convolution.
-//   out[p, co] = sum_{tap, ci} w[co][tap][ci] * in[p shifted by tap, ci]
-// p = (b, y, x) flattened; tap = 3 (dy + 1) + (dx + 1); periodic in y, x.
-// CTA tile 64 pixels x NT output channels, 4 warps (2 x 2), K in steps of 16
-// channels of one tap, double-buffered with cp.async.  Epilogue by MODE:
+// Forward / input-gradient convolution: the tcgen05 implicit GEMM of
+// surr_conv_tc.cu.  Epilogue by MODE:
 //   OUT_BF16: out_bf = act(acc + bias + skip)   (act optional)
 //   OUT_F32 : out_f  = acc + bias
 //   ACC_F32 : out_f += acc
 // ---------------------------------------------------------------------------
-constexpr int CTM = 64;     // pixels per CTA
-constexpr int KS = 16;      // channels per K step
-constexpr int APAD = 24;    // smem row stride (elements): 48 bytes, ldmatrix conflict-free
-
-template <int NT, int MODE, bool ACT, bool SKIP>
-__global__ void __launch_bounds__(128)
-k_conv3x3(const bf16 *__restrict__ in, int B, int H, int W, int cin,
-          const bf16 *__restrict__ w, int cout, const float *__restrict__ bias,
-          const bf16 *__restrict__ skip, bf16 *__restrict__ out_bf, float *__restrict__ out_f) {
-    __shared__ __align__(16) bf16 As[2][CTM][APAD];
-    __shared__ __align__(16) bf16 Bs[2][NT][APAD];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp & 1, wn = warp >> 1;
-    const long long P = (long long)B * H * W;
-    const long long p0 = (long long)blockIdx.x * CTM;
-    const int co0 = blockIdx.y * NT;
-
-    // this thread's A row (pixel) and half (8 channels)
-    const int ar = tid >> 1, ah = tid & 1;
-    const long long pa = p0 + ar;
-    int ab = 0, ay = 0, ax = 0;
-    const bool a_ok = pa < P;
-    if (a_ok) {
-        ab = int(pa / (H * W));
-        const int rem = int(pa - (long long)ab * H * W);
-        ay = rem / W;
-        ax = rem - ay * W;
-    }
-    const int kchunks = cin / KS;
-    const int ksteps = 9 * kchunks;
-
-    auto load = [&](int s, int kstep) {
-        const int tap = kstep / kchunks, ci0 = (kstep - tap * kchunks) * KS;
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        if (a_ok) {
-            const long long ps = (long long)ab * H * W + (long long)wrapi(ay + dy, H) * W +
-                                 wrapi(ax + dx, W);
-            cp16(&As[s][ar][ah * 8], in + ps * cin + ci0 + ah * 8);
-        } else {
-            *reinterpret_cast<uint4 *>(&As[s][ar][ah * 8]) = make_uint4(0, 0, 0, 0);
-        }
-        for (int c = tid; c < NT * 2; c += 128) {
-            const int n = c >> 1, h = c & 1;
-            cp16(&Bs[s][n][h * 8], w + ((long long)(co0 + n) * 9 + tap) * cin + ci0 + h * 8);
-        }
-        cp_commit();
-    };
-
-    constexpr int NI = NT / 16;  // n8 tiles per warp (each warp covers NT / 2 channels)
-    float acc[2][NI][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < NI; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-
-    load(0, 0);
-    for (int ks = 0; ks < ksteps; ++ks) {
-        const int s = ks & 1;
-        if (ks + 1 < ksteps) {
-            load(s ^ 1, ks + 1);
-            cp_wait<1>();
-        } else {
-            cp_wait<0>();
-        }
-        __syncthreads();
-        unsigned a[2][4];
-#pragma unroll
-        for (int mi = 0; mi < 2; ++mi)
-            ldsm_x4(a[mi], &As[s][wm * 32 + mi * 16 + (lane & 15)][(lane >> 4) * 8]);
-#pragma unroll
-        for (int nj = 0; nj < NI / 2; ++nj) {
-            unsigned bfr[4];
-            ldsm_x4(bfr, &Bs[s][wn * (NT / 2) + nj * 16 + (lane & 7) + ((lane >> 4) << 3)]
-                          [((lane >> 3) & 1) * 8]);
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) {
-                mma_bf16(acc[mi][2 * nj], a[mi], bfr[0], bfr[1]);
-                mma_bf16(acc[mi][2 * nj + 1], a[mi], bfr[2], bfr[3]);
-            }
-        }
-        __syncthreads();
-    }
-
-    // epilogue
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi) {
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const long long p = p0 + wm * 32 + mi * 16 + (lane >> 2) + half * 8;
-            if (p >= P) continue;
-#pragma unroll
-            for (int ni = 0; ni < NI; ++ni) {
-                const int co = co0 + wn * (NT / 2) + ni * 8 + (lane & 3) * 2;
-                float v0 = acc[mi][ni][half * 2], v1 = acc[mi][ni][half * 2 + 1];
-                if constexpr (MODE == OUT_BF16) {
-                    if (bias) { v0 += bias[co]; v1 += bias[co + 1]; }
-                    if constexpr (SKIP) {
-                        const __nv_bfloat162 sk =
-                            *reinterpret_cast<const __nv_bfloat162 *>(skip + p * cout + co);
-                        v0 += __bfloat162float(sk.x);
-                        v1 += __bfloat162float(sk.y);
-                    }
-                    if constexpr (ACT) {
-                        v0 = v0 > 0.f ? v0 : LEAK * v0;
-                        v1 = v1 > 0.f ? v1 : LEAK * v1;
-                    }
-                    *reinterpret_cast<__nv_bfloat162 *>(out_bf + p * cout + co) =
-                        __floats2bfloat162_rn(v0, v1);
-                } else if constexpr (MODE == OUT_F32) {
-                    if (bias) { v0 += bias[co]; v1 += bias[co + 1]; }
-                    *reinterpret_cast<float2 *>(out_f + p * cout + co) = make_float2(v0, v1);
-                } else {
-                    float2 *o = reinterpret_cast<float2 *>(out_f + p * cout + co);
-                    const float2 prev = *o;
-                    *o = make_float2(prev.x + v0, prev.y + v1);
-                }
-            }
-        }
-    }
-}
-
-template <int MODE, bool ACT, bool SKIP>
-static cudaError_t conv_t(const ConvArgs &a, cudaStream_t st) {
-    const long long P = (long long)a.B * a.H * a.W;
-    const int nt = (a.cout % 64 == 0) ? 64 : 32;
-    dim3 grid(unsigned((P + CTM - 1) / CTM), unsigned(a.cout / nt));
-    if (nt == 64)
-        k_conv3x3<64, MODE, ACT, SKIP><<<grid, 128, 0, st>>>(a.in, a.B, a.H, a.W, a.cin, a.w,
-                                                            a.cout, a.bias, a.skip, a.out_bf,
-                                                            a.out_f);
-    else
-        k_conv3x3<32, MODE, ACT, SKIP><<<grid, 128, 0, st>>>(a.in, a.B, a.H, a.W, a.cin, a.w,
-                                                            a.cout, a.bias, a.skip, a.out_bf,
-                                                            a.out_f);
-    return cudaGetLastError();
-}
-
 cudaError_t conv3x3(const ConvArgs &a, int mode, bool act, bool skip, cudaStream_t st) {
     if (a.cin % 32 || a.cout % 32) return cudaErrorInvalidValue;
-    if (mode == OUT_BF16) {
-        if (act) return skip ? conv_t<OUT_BF16, true, true>(a, st) : conv_t<OUT_BF16, true, false>(a, st);
-        return skip ? conv_t<OUT_BF16, false, true>(a, st) : conv_t<OUT_BF16, false, false>(a, st);
-    }
-    if (mode == OUT_F32) return conv_t<OUT_F32, false, false>(a, st);
-    return conv_t<ACC_F32, false, false>(a, st);
+    return conv3x3_tc(a, mode, act, skip, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -299,111 +153,173 @@ __global__ void k_sum_splits(const float *__restrict__ part, int splits, long lo
     }
 }
 
+// Many splits of few values (the per-block bias sums): one block per value,
+// each thread a strided share of the splits, then a fixed-order tree.
+__global__ void k_sum_splits_tree(const float *__restrict__ part, int splits, long long n,
+                                  float *__restrict__ g) {
+    __shared__ float red[256];
+    const long long i = blockIdx.x;
+    float s = 0.f;
+    for (int k = threadIdx.x; k < splits; k += blockDim.x) s += part[k * n + i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) g[i] = red[0];
+}
+
 cudaError_t sum_splits(const float *part, int splits, long long n, float *g, cudaStream_t st) {
-    const int blocks = int(std::min<long long>((n + 255) / 256, 4096));
-    k_sum_splits<<<blocks, 256, 0, st>>>(part, splits, n, g);
+    if (splits >= 64 && n <= 65535) {
+        k_sum_splits_tree<<<unsigned(n), 256, 0, st>>>(part, splits, n, g);
+    } else {
+        const int blocks = int(std::min<long long>((n + 255) / 256, 4096));
+        k_sum_splits<<<blocks, 256, 0, st>>>(part, splits, n, g);
+    }
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Elementwise kernels.
+// Elementwise kernels.  Tensors are NHWC with C a multiple of 32; a thread
+// handles eight BF16 or four FP32 channels of one pixel, and every index fits
+// 32 bits (checked where the network is sized).
 // ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void unpack8(uint4 u, float (&v)[8]) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        __nv_bfloat162 b;
+        *reinterpret_cast<uint32_t *>(&b) = w[j];
+        v[2 * j] = __bfloat162float(b.x);
+        v[2 * j + 1] = __bfloat162float(b.y);
+    }
+}
+
+__device__ __forceinline__ uint4 pack8(const float (&v)[8]) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        w[j] = *reinterpret_cast<const uint32_t *>(&b);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ uint4 ld8(const bf16 *p) { return *reinterpret_cast<const uint4 *>(p); }
+__device__ __forceinline__ float4 ld4(const float *p) {
+    return *reinterpret_cast<const float4 *>(p);
+}
 
 // dz = dy * act'(y) (leaky ReLU, from the sign of the activation's output;
 // identity when !act); also accumulates dz into skip_grad if given, and the
 // per-channel sums over this block's pixels into bias_part[block][c].
+// Thread t takes channel t % C of every (256 / C)-th pixel; the phases are
+// summed in a fixed order.
 __global__ void k_act_back(const float *__restrict__ dy, const bf16 *__restrict__ y, long long P,
                            int C, bool act, bf16 *__restrict__ dz, float *__restrict__ skip_grad,
                            float *__restrict__ bias_part, long long pix_per_block) {
-    extern __shared__ float csum[];
-    for (int c = threadIdx.x; c < C; c += blockDim.x) csum[c] = 0.f;
-    __syncthreads();
+    __shared__ float red[256];
+    const int R = blockDim.x / C;
+    const int c = threadIdx.x % C, r = threadIdx.x / C;
     const long long p0 = blockIdx.x * pix_per_block;
     long long p1 = p0 + pix_per_block;
     if (p1 > P) p1 = P;
-    // each thread owns one channel (C <= blockDim.x * k)
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        float s = 0.f;
-        for (long long p = p0; p < p1; ++p) {
-            const long long i = p * C + c;
-            float g = dy[i];
-            if (act && __bfloat162float(y[i]) <= 0.f) g *= LEAK;
-            dz[i] = __float2bfloat16_rn(g);
-            if (skip_grad) skip_grad[i] += g;
-            s += g;
-        }
-        csum[c] = s;
+    float s = 0.f;
+    for (long long p = p0 + r; p < p1; p += R) {
+        const long long i = p * C + c;
+        float g = dy[i];
+        if (act && __bfloat162float(y[i]) <= 0.f) g *= LEAK;
+        dz[i] = __float2bfloat16_rn(g);
+        if (skip_grad) skip_grad[i] += g;
+        s += g;
     }
+    red[threadIdx.x] = s;
     __syncthreads();
-    for (int c = threadIdx.x; c < C; c += blockDim.x) bias_part[blockIdx.x * (long long)C + c] = csum[c];
+    if (threadIdx.x < C) {
+        float t = 0.f;
+        for (int k = 0; k < R; ++k) t += red[k * C + threadIdx.x];
+        bias_part[blockIdx.x * (long long)C + threadIdx.x] = t;
+    }
 }
 
 cudaError_t act_back(const float *dy, const bf16 *y, long long P, int C, bool act, bf16 *dz,
                      float *skip_grad, float *bias_part, int blocks, cudaStream_t st) {
+    if (C > 256 || 256 % C) return cudaErrorInvalidValue;
     const long long per = (P + blocks - 1) / blocks;
-    k_act_back<<<blocks, 256, C * sizeof(float), st>>>(dy, y, P, C, act, dz, skip_grad, bias_part,
-                                                       per);
+    k_act_back<<<blocks, 256, 0, st>>>(dy, y, P, C, act, dz, skip_grad, bias_part, per);
     return cudaGetLastError();
 }
 
 // 2x2 average pooling, NHWC bf16.
 __global__ void k_pool(const bf16 *__restrict__ in, int B, int H, int W, int C,
                        bf16 *__restrict__ out) {
-    const int h = H / 2, w = W / 2;
-    const long long n = (long long)B * h * w * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int c = int(i % C);
-        const long long pix = i / C;
-        const int x = int(pix % w), y = int((pix / w) % h), b = int(pix / ((long long)w * h));
-        const long long base = (((long long)b * H + 2 * y) * W + 2 * x) * C + c;
-        const float s = __bfloat162float(in[base]) + __bfloat162float(in[base + C]) +
-                        __bfloat162float(in[base + (long long)W * C]) +
-                        __bfloat162float(in[base + (long long)W * C + C]);
-        out[i] = __float2bfloat16_rn(0.25f * s);
+    const unsigned h = H / 2, w = W / 2, c8n = C / 8;
+    const unsigned n = unsigned(B) * h * w * c8n;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned c8 = i % c8n, pix = i / c8n;
+        const unsigned x = pix % w, t = pix / w, y = t % h, b = t / h;
+        const size_t base = ((size_t(b) * H + 2 * y) * W + 2 * x) * C + c8 * 8;
+        const size_t row = size_t(W) * C;
+        float a[8], bb[8], cc[8], d[8], o[8];
+        unpack8(ld8(in + base), a);
+        unpack8(ld8(in + base + C), bb);
+        unpack8(ld8(in + base + row), cc);
+        unpack8(ld8(in + base + row + C), d);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o[j] = 0.25f * (a[j] + bb[j] + cc[j] + d[j]);
+        *reinterpret_cast<uint4 *>(out + size_t(pix) * C + c8 * 8) = pack8(o);
     }
 }
 
 // Gradient of the pooling: g_in[2y+a, 2x+b] += g_out[y, x] / 4 (fp32).
 __global__ void k_pool_back(const float *__restrict__ gout, int B, int H, int W, int C,
                             float *__restrict__ gin) {
-    const long long n = (long long)B * H * W * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int c = int(i % C);
-        const long long pix = i / C;
-        const int x = int(pix % W), y = int((pix / W) % H), b = int(pix / ((long long)W * H));
-        gin[i] += 0.25f * gout[(((long long)b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c];
+    const unsigned c4n = C / 4;
+    const unsigned n = unsigned(B) * H * W * c4n;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned c4 = i % c4n, pix = i / c4n;
+        const unsigned x = pix % W, t = pix / W, y = t % H, b = t / H;
+        const float4 g = ld4(gout + ((size_t(b) * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c4 * 4);
+        float4 *o = reinterpret_cast<float4 *>(gin + size_t(pix) * C + c4 * 4);
+        float4 v = *o;
+        v.x += 0.25f * g.x;
+        v.y += 0.25f * g.y;
+        v.z += 0.25f * g.z;
+        v.w += 0.25f * g.w;
+        *o = v;
     }
 }
 
-// Nearest-neighbour 2x upsampling, NHWC bf16.
+// Nearest 2x upsampling, NHWC bf16.
 __global__ void k_up(const bf16 *__restrict__ in, int B, int h, int w, int C,
                      bf16 *__restrict__ out) {
-    const long long n = (long long)B * 4 * h * w * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int c = int(i % C);
-        const long long pix = i / C;
-        const int X = int(pix % (2 * w)), Y = int((pix / (2 * w)) % (2 * h));
-        const int b = int(pix / (4LL * w * h));
-        out[i] = in[(((long long)b * h + Y / 2) * w + X / 2) * C + c];
+    const unsigned c8n = C / 8, W = 2 * w, H = 2 * h;
+    const unsigned n = unsigned(B) * H * W * c8n;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned c8 = i % c8n, pix = i / c8n;
+        const unsigned X = pix % W, t = pix / W, Y = t % H, b = t / H;
+        *reinterpret_cast<uint4 *>(out + size_t(pix) * C + c8 * 8) =
+            ld8(in + ((size_t(b) * h + Y / 2) * w + X / 2) * C + c8 * 8);
     }
 }
 
 // Gradient of the upsampling: g_in[y, x] = sum of the 4 g_out it fed (fp32).
 __global__ void k_up_back(const float *__restrict__ gout, int B, int h, int w, int C,
                           float *__restrict__ gin) {
-    const long long n = (long long)B * h * w * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int c = int(i % C);
-        const long long pix = i / C;
-        const int x = int(pix % w), y = int((pix / w) % h), b = int(pix / ((long long)w * h));
-        const int W = 2 * w;
-        const long long base = (((long long)b * 2 * h + 2 * y) * W + 2 * x) * C + c;
-        gin[i] = gout[base] + gout[base + C] + gout[base + (long long)W * C] +
-                 gout[base + (long long)W * C + C];
+    const unsigned c4n = C / 4, W = 2 * w;
+    const unsigned n = unsigned(B) * h * w * c4n;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned c4 = i % c4n, pix = i / c4n;
+        const unsigned x = pix % w, t = pix / w, y = t % h, b = t / h;
+        const size_t base = ((size_t(b) * 2 * h + 2 * y) * W + 2 * x) * C + c4 * 4;
+        const size_t row = size_t(W) * C;
+        const float4 a = ld4(gout + base), bb = ld4(gout + base + C), c = ld4(gout + base + row),
+                     d = ld4(gout + base + row + C);
+        *reinterpret_cast<float4 *>(gin + size_t(pix) * C + c4 * 4) =
+            make_float4(a.x + bb.x + c.x + d.x, a.y + bb.y + c.y + d.y, a.z + bb.z + c.z + d.z,
+                        a.w + bb.w + c.w + d.w);
     }
 }
 
@@ -447,12 +363,14 @@ __global__ void k_to_bf16(const float *__restrict__ a, long long n, bf16 *__rest
 // Features (fp32 [P][FEAT]) -> padded bf16 input ([P][cpad], zeros beyond).
 __global__ void k_pack_in(const float *__restrict__ f, long long P, int feat, int cpad,
                           bf16 *__restrict__ x) {
-    const long long n = P * cpad;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int c = int(i % cpad);
-        const long long p = i / cpad;
-        x[i] = __float2bfloat16_rn(c < feat ? f[p * feat + c] : 0.f);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
+         p += (long long)gridDim.x * blockDim.x) {
+        for (int c0 = 0; c0 < cpad; c0 += 8) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = c0 + j < feat ? f[p * feat + c0 + j] : 0.f;
+            *reinterpret_cast<uint4 *>(x + p * cpad + c0) = pack8(v);
+        }
     }
 }
 
@@ -463,17 +381,21 @@ __global__ void k_mse(const float *__restrict__ y, int cpad, const float *__rest
     __shared__ double red[256];
     const double inv = 1.0 / double(P * nout);
     double s = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P * cpad;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int c = int(i % cpad);
-        const long long p = i / cpad;
-        float g = 0.f;
-        if (c < nout) {
-            const float d = y[i] - t[p * nout + c];
-            s += double(d) * d;
-            g = float(2.0 * d * inv);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
+         p += (long long)gridDim.x * blockDim.x) {
+        for (int c0 = 0; c0 < cpad; c0 += 4) {
+            float g[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                g[j] = 0.f;
+                if (c0 + j < nout) {
+                    const float d = y[p * cpad + c0 + j] - t[p * nout + c0 + j];
+                    s += double(d) * d;
+                    g[j] = float(2.0 * d * inv);
+                }
+            }
+            *reinterpret_cast<float4 *>(dy + p * cpad + c0) = make_float4(g[0], g[1], g[2], g[3]);
         }
-        dy[i] = g;
     }
     red[threadIdx.x] = s;
     __syncthreads();

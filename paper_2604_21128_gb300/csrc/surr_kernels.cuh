@@ -1,7 +1,9 @@
 // Kernels of the learned surrogate (a convolutional operator that advances
 // the QLA state K steps at once).  Activations and weights are BF16, stored
-// NHWC with the channel count padded to a multiple of 16; every
-// contraction accumulates in FP32 on the tensor cores (mma.sync m16n8k16).
+// NHWC with the channel count padded to a multiple of 32; every
+// contraction accumulates in FP32 on the tensor cores (tcgen05.mma with a TMEM
+// accumulator for the convolutions, mma.sync m16n8k16 for the weight
+// gradient).
 // 3x3 convolutions wrap periodically, like the lattice.
 #pragma once
 

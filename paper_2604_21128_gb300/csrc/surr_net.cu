@@ -217,12 +217,12 @@ qla_status forward(surr_net *n, int B) {
         // inputs: pool before encoder levels >= 1, upsample before decoder
         if (i >= 1 && i < 5) {
             const long long m = pixels(n, B, l) * WIDTH[l - 1];
-            k_pool<<<ew_blocks(m), 256, 0, st>>>(n->E[l - 1], B, h * 2, w * 2, WIDTH[l - 1],
+            k_pool<<<ew_blocks(m / 8), 256, 0, st>>>(n->E[l - 1], B, h * 2, w * 2, WIDTH[l - 1],
                                                  n->Pl[l]);
         } else if (i >= 5 && i < 9) {
             const bf16 *src = (i == 5) ? n->E[4] : n->D[l + 1];
             const long long m = pixels(n, B, l) * WIDTH[l + 1];
-            k_up<<<ew_blocks(m), 256, 0, st>>>(src, B, h / 2, w / 2, WIDTH[l + 1], n->U[l]);
+            k_up<<<ew_blocks(m / 8), 256, 0, st>>>(src, B, h / 2, w / 2, WIDTH[l + 1], n->U[l]);
         }
         NCUDA(n, cudaGetLastError(), "surrogate: resample");
         ConvArgs a{conv_input(n, i), B, h, w, s.cin, n->wb[i], s.cout, n->bias[i],
@@ -281,10 +281,10 @@ qla_status backward(surr_net *n, int B) {
         float *dst = l < 3 ? n->dD[l + 1] : n->dE[4];
         const long long m = pixels(n, B, l + 1) * WIDTH[l + 1];
         if (l < 3) {
-            k_up_back<<<ew_blocks(m), 256, 0, st>>>(n->dU[l], B, h, w, WIDTH[l + 1], dst);
+            k_up_back<<<ew_blocks(m / 4), 256, 0, st>>>(n->dU[l], B, h, w, WIDTH[l + 1], dst);
         } else {
             // dE4 only receives this gradient; D3's up-sampled input is E4
-            k_up_back<<<ew_blocks(m), 256, 0, st>>>(n->dU[l], B, h, w, WIDTH[l + 1], dst);
+            k_up_back<<<ew_blocks(m / 4), 256, 0, st>>>(n->dU[l], B, h, w, WIDTH[l + 1], dst);
         }
         NCUDA(n, cudaGetLastError(), "surrogate: upsample backward");
     }
@@ -295,7 +295,7 @@ qla_status backward(surr_net *n, int B) {
         if (l >= 1) {
             const int H = n->H >> (l - 1), W = n->W >> (l - 1);
             const long long m = pixels(n, B, l - 1) * WIDTH[l - 1];
-            k_pool_back<<<ew_blocks(m), 256, 0, st>>>(n->dP[l], B, H, W, WIDTH[l - 1], n->dE[l - 1]);
+            k_pool_back<<<ew_blocks(m / 4), 256, 0, st>>>(n->dP[l], B, H, W, WIDTH[l - 1], n->dE[l - 1]);
             NCUDA(n, cudaGetLastError(), "surrogate: pool backward");
         }
     }
@@ -304,7 +304,7 @@ qla_status backward(surr_net *n, int B) {
 
 qla_status loss(surr_net *n, int B, const float *target, double *out) {
     const long long P = pixels(n, B, 0);
-    const int blocks = std::min(n->lblocks, ew_blocks(P * CPAD));
+    const int blocks = std::min(n->lblocks, ew_blocks(P));
     k_mse<<<blocks, 256, 0, n->stream>>>(n->Y, CPAD, target, NOUT, P, n->dY, n->lpart);
     NCUDA(n, cudaGetLastError(), "surrogate: loss");
     std::vector<double> h(blocks);
@@ -319,7 +319,7 @@ qla_status loss(surr_net *n, int B, const float *target, double *out) {
 
 qla_status pack(surr_net *n, const float *feat, int B) {
     const long long P = pixels(n, B, 0);
-    k_pack_in<<<ew_blocks(P * CPAD), 256, 0, n->stream>>>(feat, P, FEAT, CPAD, n->X);
+    k_pack_in<<<ew_blocks(P), 256, 0, n->stream>>>(feat, P, FEAT, CPAD, n->X);
     NCUDA(n, cudaGetLastError(), "surrogate: pack");
     return QLA_OK;
 }
@@ -435,6 +435,8 @@ extern "C" {
 
 size_t surr_workspace_bytes(int height, int width, int max_batch) {
     if (height < 16 || width < 16 || height % 16 || width % 16 || max_batch < 1) return 0;
+    // the elementwise kernels index the widest level-0 tensor with 32 bits
+    if ((long long)max_batch * height * width * 32 >= (1LL << 31)) return 0;
     return net_bytes(height, width, max_batch, false, nullptr);
 }
 
@@ -667,8 +669,13 @@ extern "C" qla_status surr_conv3x3_raw(const void *in_bf16, int B, int H, int W,
         return QLA_EINVAL;
     ConvArgs a{static_cast<const bf16 *>(in_bf16), B, H, W, cin, static_cast<const bf16 *>(w_bf16),
                cout, nullptr, nullptr, nullptr, out_f32};
-    return conv3x3(a, OUT_F32, false, false, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess
-               ? QLA_OK : QLA_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (conv3x3(a, OUT_F32, false, false, st) != cudaSuccess) return QLA_ECUDA;
+    int flag = 0;
+    if (cudaStreamSynchronize(st) != cudaSuccess || conv_tc_error(&flag, true) != cudaSuccess ||
+        flag)
+        return QLA_ECUDA;
+    return QLA_OK;
 }
 
 extern "C" qla_status surr_weight_grad_raw(const void *dz_bf16, const void *in_bf16, int B, int H,
