@@ -2,17 +2,20 @@
 // tensor cores: an implicit GEMM
 //   out[p, co] = sum_{tap, ci} w[co][tap][ci] * in[p shifted by tap, ci]
 // with M = 128 pixels per CTA (one TMEM lane each), N = NT output channels,
-// and K walked one tap and 32 input channels per pipeline stage.
+// and K walked in 32-channel chunks.
 //
-// All 128 threads gather the stage's operands with cp.async into shared
-// memory in the no-swizzle K-major layout of the UMMA descriptors (8-row x
-// 16-byte core matrices, 128 bytes each; K-adjacent core matrices 128 bytes
-// apart, 8-row groups 512 bytes apart).  One thread issues two
-// tcgen05.mma (K = 16 each) per stage into an FP32 accumulator in TMEM and
-// commits them to the stage's mbarrier, which frees the stage for the loads
-// two stages later.  The epilogue reads the accumulator back with
-// tcgen05.ld (warp w owns TMEM lanes 32w .. 32w + 31, i.e. its 32 pixels)
-// and applies bias, skip, activation and the output conversion.
+// Operands sit in shared memory in the no-swizzle K-major layout of the UMMA
+// descriptors (8-row x 16-byte core matrices).  One thread issues the
+// tcgen05.mma (K = 16 each) into an FP32 accumulator in TMEM and commits them
+// to an mbarrier, which frees their shared memory for later loads.  The
+// epilogue reads the accumulator back with tcgen05.ld (warp w owns TMEM lanes
+// 32w .. 32w + 31, i.e. its 32 pixels) and applies bias, skip, activation and
+// the output conversion.
+//
+// Two kernels: k_conv3x3_tc gathers a stage per tap and chunk (six stages,
+// four loaded ahead); k_conv3x3_rows, for widths that are multiples of 128,
+// loads one halo'd row patch per chunk that serves all nine taps and keeps
+// the weights resident in persistent CTAs.
 //
 // Every wait on an mbarrier has an iteration limit; a CTA that gives up sets
 // conv_tc_error, skips its epilogue, frees its TMEM and returns.
@@ -23,7 +26,7 @@ namespace {
 
 constexpr int TM = 128;          // pixels per CTA = TMEM lanes
 constexpr int KC = 32;           // input channels per stage (two K = 16 MMAs)
-constexpr int NSTAGE = 4;        // shared-memory stages
+constexpr int NSTAGE = 6;        // shared-memory stages
 constexpr int AHEAD = NSTAGE - 2;  // stages loaded ahead of the MMA
 constexpr unsigned WAIT_LIMIT = 1u << 22;
 
@@ -106,6 +109,88 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// The accumulator rows of this thread's TMEM lane (lane_base) -> output
+// pixel p, channels co0 .. co0 + NT - 1, by MODE (see conv3x3).  Every thread
+// of the warp takes part in the loads; only valid pixels store.
+template <int NT, int MODE, bool ACT, bool SKIP>
+__device__ __forceinline__ void epilogue(uint32_t lane_base, long long p, bool valid, int co0,
+                                         int cout, const float *__restrict__ bias,
+                                         const bf16 *__restrict__ skip, bf16 *__restrict__ out_bf,
+                                         float *__restrict__ out_f) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < NT; c0 += 16) {
+        float v[16];
+        tmem_ld16(lane_base + uint32_t(c0), v);
+        if (!valid) continue;
+        const int co = co0 + c0;
+        if constexpr (MODE == OUT_BF16) {
+            if (bias) {
+                const float4 *bb = reinterpret_cast<const float4 *>(bias + co);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float4 t = bb[j];
+                    v[4 * j] += t.x;
+                    v[4 * j + 1] += t.y;
+                    v[4 * j + 2] += t.z;
+                    v[4 * j + 3] += t.w;
+                }
+            }
+            if constexpr (SKIP) {
+                const uint4 *s = reinterpret_cast<const uint4 *>(skip + p * cout + co);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint4 u = s[h];
+                    const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        __nv_bfloat162 b2;
+                        *reinterpret_cast<uint32_t *>(&b2) = wd[j];
+                        v[h * 8 + 2 * j] += __bfloat162float(b2.x);
+                        v[h * 8 + 2 * j + 1] += __bfloat162float(b2.y);
+                    }
+                }
+            }
+            if constexpr (ACT) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = v[i] > 0.f ? v[i] : LEAK * v[i];
+            }
+            uint32_t wd[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                wd[j] = *reinterpret_cast<const uint32_t *>(&b2);
+            }
+            uint4 *o = reinterpret_cast<uint4 *>(out_bf + p * cout + co);
+            o[0] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+            o[1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+        } else if constexpr (MODE == OUT_F32) {
+            if (bias) {
+                const float4 *bb = reinterpret_cast<const float4 *>(bias + co);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float4 t = bb[j];
+                    v[4 * j] += t.x;
+                    v[4 * j + 1] += t.y;
+                    v[4 * j + 2] += t.z;
+                    v[4 * j + 3] += t.w;
+                }
+            }
+            float4 *o = reinterpret_cast<float4 *>(out_f + p * cout + co);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        } else {
+            float4 *o = reinterpret_cast<float4 *>(out_f + p * cout + co);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 prev = o[j];
+                o[j] = make_float4(prev.x + v[4 * j], prev.y + v[4 * j + 1],
+                                   prev.z + v[4 * j + 2], prev.w + v[4 * j + 3]);
+            }
+        }
+    }
 }
 
 template <int NT>
@@ -226,66 +311,8 @@ k_conv3x3_tc(const bf16 *__restrict__ in, int B, int H, int W, int cin,
     tc_fence_after();
 
     if (ok) {
-        const uint32_t lane_base = tmem + (uint32_t(warp * 32) << 16);
-        const long long p = pa;
-#pragma unroll 1
-        for (int c0 = 0; c0 < NT; c0 += 16) {
-            float v[16];
-            tmem_ld16(lane_base + uint32_t(c0), v);
-            if (p >= P) continue;
-            const int co = co0 + c0;
-            if constexpr (MODE == OUT_BF16) {
-                if (bias) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] += bias[co + i];
-                }
-                if constexpr (SKIP) {
-                    const uint4 *s = reinterpret_cast<const uint4 *>(skip + p * cout + co);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const uint4 u = s[h];
-                        const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            __nv_bfloat162 b2;
-                            *reinterpret_cast<uint32_t *>(&b2) = wd[j];
-                            v[h * 8 + 2 * j] += __bfloat162float(b2.x);
-                            v[h * 8 + 2 * j + 1] += __bfloat162float(b2.y);
-                        }
-                    }
-                }
-                if constexpr (ACT) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = v[i] > 0.f ? v[i] : LEAK * v[i];
-                }
-                uint32_t wd[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                    wd[j] = *reinterpret_cast<const uint32_t *>(&b2);
-                }
-                uint4 *o = reinterpret_cast<uint4 *>(out_bf + p * cout + co);
-                o[0] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-                o[1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
-            } else if constexpr (MODE == OUT_F32) {
-                if (bias) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] += bias[co + i];
-                }
-                float4 *o = reinterpret_cast<float4 *>(out_f + p * cout + co);
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-            } else {
-                float4 *o = reinterpret_cast<float4 *>(out_f + p * cout + co);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float4 prev = o[j];
-                    o[j] = make_float4(prev.x + v[4 * j], prev.y + v[4 * j + 1],
-                                       prev.z + v[4 * j + 2], prev.w + v[4 * j + 3]);
-                }
-            }
-        }
+        epilogue<NT, MODE, ACT, SKIP>(tmem + (uint32_t(warp * 32) << 16), pa, pa < P, co0, cout,
+                                      bias, skip, out_bf, out_f);
     } else if (tid == 0) {
         atomicExch(&g_conv_tc_error, 1);
     }
@@ -296,6 +323,192 @@ k_conv3x3_tc(const bf16 *__restrict__ in, int B, int H, int W, int cin,
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(TCOLS)
                      : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Row-patch variant for W a multiple of 128: a tile is 128 consecutive pixels
+// of one image row, so every tap's operand is the same row patch shifted.  Per
+// 32-channel chunk the CTA loads the patch once -- rows y-1, y, y+1 of pixels
+// x0-1 .. x0+128 (periodic) -- laid out as [row][8-channel group][pixel][16
+// bytes], i.e. K-major core matrices with 8-row groups 128 bytes apart (SBO)
+// and channel groups 130 * 16 bytes apart (LBO).  Tap (dy, dx) is then the
+// descriptor whose start is row dy + 1, pixel dx + 1: 18 MMAs per chunk
+// (9 taps x K = 32) read one patch.  CTAs are persistent over the tiles and
+// keep their N-slice of the weights in shared memory for the whole launch
+// ([tap][chunk][channel group][n][16 bytes]), so the weights leave L2 once per
+// CTA instead of once per tile.  Patches are double-buffered: the next item's
+// patch loads while this item's MMAs run, and the MMAs of the item before
+// must be done (its mbarrier) before its buffer is refilled.  After a tile's
+// last chunk the CTA waits for its MMAs and runs the epilogue from TMEM.
+// ---------------------------------------------------------------------------
+constexpr int PATCH_PIX = TM + 2;                      // pixels per patch row
+constexpr int PATCH_GROUP = PATCH_PIX * 16;            // bytes per channel group
+constexpr int PATCH_BYTES = 3 * 4 * PATCH_GROUP;       // 3 rows x 4 groups
+
+template <int NT, int MODE, bool ACT, bool SKIP>
+__global__ void __launch_bounds__(128)
+k_conv3x3_rows(const bf16 *__restrict__ in, int B, int H, int W, int cin,
+               const bf16 *__restrict__ w, int cout, const float *__restrict__ bias,
+               const bf16 *__restrict__ skip, bf16 *__restrict__ out_bf,
+               float *__restrict__ out_f) {
+    constexpr uint32_t TCOLS = NT;
+    static_assert(NT == 32 || NT == 64 || NT == 128 || NT == 256, "TMEM allocation size");
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int co0 = blockIdx.y * NT;
+    const int kchunks = cin / KC;
+    const long long P = (long long)B * H * W;
+    const long long ntiles = P / TM;
+    // this CTA's tiles: blockIdx.x, + gridDim.x, ...
+    const long long my_tiles =
+        blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long nitems = my_tiles * kchunks;
+    unsigned char *wsm = smem;                                   // weights
+    unsigned char *patch = smem + size_t(18) * cin * NT;         // two patch buffers
+
+    if (tid == 0) {
+        mbar_init(&bar[0]);
+        mbar_init(&bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    // weights of output channels co0 .. co0 + NT - 1, all taps and chunks
+    {
+        const int ci8n = cin / 8;
+        const int total = NT * 9 * ci8n;
+        for (int q = tid; q < total; q += 128) {
+            const int ci8 = q % ci8n, t = (q / ci8n) % 9, n = q / (ci8n * 9);
+            const int c = ci8 >> 2, kg = ci8 & 3;
+            cp16(wsm + ((size_t(t * kchunks + c) * 4 + kg) * NT + n) * 16,
+                 w + ((long long)(co0 + n) * 9 + t) * cin + ci8 * 8);
+        }
+    }
+    auto tile_of = [&](long long item) { return blockIdx.x + (item / kchunks) * gridDim.x; };
+    auto load_patch = [&](long long item) {
+        unsigned char *buf = patch + (item & 1) * PATCH_BYTES;
+        const long long p0 = tile_of(item) * TM;
+        const int c = int(item % kchunks);
+        const long long row = p0 / W;                 // b * H + y
+        const int x0 = int(p0 - row * W), y = int(row % H);
+        const bf16 *img = in + (row - y) * W * cin + c * KC;
+        const int ym = y == 0 ? H - 1 : y - 1, yp = y == H - 1 ? 0 : y + 1;
+        // one pixel of one patch row per iteration: its 64 contiguous bytes
+        // go to the four channel-group arrays
+        for (int q = tid; q < 3 * PATCH_PIX; q += 128) {
+            const int r = q / PATCH_PIX, j = q - r * PATCH_PIX;
+            const int yy = r == 0 ? ym : (r == 1 ? y : yp);
+            int xx = x0 + j - 1;
+            xx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
+            const bf16 *src = img + ((long long)yy * W + xx) * cin;
+            unsigned char *dst = buf + r * 4 * PATCH_GROUP + j * 16;
+#pragma unroll
+            for (int kg = 0; kg < 4; ++kg) cp16(dst + kg * PATCH_GROUP, src + kg * 8);
+        }
+    };
+
+    bool ok = true;
+    if (nitems > 0) load_patch(0);
+    cp_commit();
+    for (long long i = 0; i < nitems; ++i) {
+        const int sb = int(i & 1);
+        const int c = int(i % kchunks);
+        cp_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        if (abort_flag) break;
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t pb = smem_u32(patch + sb * PATCH_BYTES), wb = smem_u32(wsm);
+#pragma unroll 1
+            for (int t = 0; t < 9; ++t) {
+                const int dy = t / 3, dx = t % 3;   // patch row, pixel offset
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t a = pb + (dy * 4 + 2 * h) * PATCH_GROUP + dx * 16;
+                    const uint32_t bw = wb + ((t * kchunks + c) * 4 + 2 * h) * NT * 16;
+                    umma(tmem, umma_desc(a, PATCH_GROUP, 128), umma_desc(bw, NT * 16, 128),
+                         umma_idesc<NT>(), (c | t | h) != 0);
+                }
+            }
+            umma_commit(&bar[sb]);
+        }
+        if (i + 1 < nitems) {
+            // the buffer of item i + 1 last served item i - 1
+            if (i >= 1 && !mbar_wait(&bar[sb ^ 1], uint32_t((i - 1) >> 1) & 1)) ok = false;
+            if (ok) load_patch(i + 1);
+        }
+        cp_commit();
+        if (c == kchunks - 1) {
+            if (!mbar_wait(&bar[sb], uint32_t(i >> 1) & 1)) ok = false;
+            // tcgen05.ld is warp-collective: decide for the whole CTA
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const long long p = tile_of(i) * TM + tid;
+            epilogue<NT, MODE, ACT, SKIP>(tmem + (uint32_t(warp * 32) << 16), p, true, co0, cout,
+                                          bias, skip, out_bf, out_f);
+        }
+        if (!ok) abort_flag = 1;
+    }
+    cp_wait<0>();
+    if (abort_flag && tid == 0) atomicExch(&g_conv_tc_error, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TCOLS)
+                     : "memory");
+}
+
+template <int NT, int MODE, bool ACT, bool SKIP>
+cudaError_t launch_rows(const ConvArgs &a, long long ntiles, cudaStream_t st) {
+    auto k = k_conv3x3_rows<NT, MODE, ACT, SKIP>;
+    const int smem = 18 * a.cin * NT + 2 * PATCH_BYTES;
+    static int dev_sms = 0, dev_smem = 0;
+    if (dev_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (dev_sms < 1) dev_sms = 1;
+    }
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 int(cudaSharedmemCarveoutMaxShared));
+    if (e != cudaSuccess) return e;
+    // CTAs per SM from shared memory (dynamic + static + the 1 KB the
+    // system reserves per CTA) and TMEM (512 columns per SM)
+    int per_sm = dev_smem / (smem + 1024 + 256);
+    per_sm = std::min(per_sm, 512 / NT);
+    per_sm = std::min(per_sm, 16);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int ny = a.cout / NT;
+    long long ctas = (long long)dev_sms * per_sm / ny;
+    if (ctas < 1) ctas = 1;
+    if (ctas > ntiles) ctas = ntiles;
+    k<<<dim3(unsigned(ctas), unsigned(ny)), 128, smem, st>>>(
+        a.in, a.B, a.H, a.W, a.cin, a.w, a.cout, a.bias, a.skip, a.out_bf, a.out_f);
+    return cudaGetLastError();
 }
 
 template <int NT, int MODE, bool ACT, bool SKIP>
@@ -314,6 +527,19 @@ template <int MODE, bool ACT, bool SKIP>
 cudaError_t conv_tc_t(const ConvArgs &a, cudaStream_t st) {
     const long long P = (long long)a.B * a.H * a.W;
     const long long mtiles = (P + TM - 1) / TM;
+    if (a.W % TM == 0) {
+        // row patches; the N slice whose weights fit in about 100 KB
+        int nt = a.cout < 256 ? a.cout : 256;
+        while (nt > 32 && (a.cout % nt != 0 || 18 * a.cin * nt > 100 * 1024)) nt >>= 1;
+        if (18 * a.cin * nt <= 100 * 1024 && a.cout % nt == 0) {
+            switch (nt) {
+            case 256: return launch_rows<256, MODE, ACT, SKIP>(a, mtiles, st);
+            case 128: return launch_rows<128, MODE, ACT, SKIP>(a, mtiles, st);
+            case 64: return launch_rows<64, MODE, ACT, SKIP>(a, mtiles, st);
+            default: return launch_rows<32, MODE, ACT, SKIP>(a, mtiles, st);
+            }
+        }
+    }
     // the widest N tile that divides cout and still gives about one CTA per SM
     int nt = 256;
     while (nt > 32 && (a.cout % nt != 0 || mtiles * (a.cout / nt) < 152)) nt >>= 1;

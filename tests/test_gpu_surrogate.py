@@ -37,7 +37,12 @@ def _ref_conv(x_nhwc, w):
 
 @pytest.mark.parametrize("B,H,W,cin,cout", [(2, 16, 16, 32, 32), (1, 8, 24, 64, 64),
                                             (1, 16, 16, 256, 128), (1, 7, 9, 32, 64),
-                                            (3, 4, 4, 128, 256)])
+                                            (3, 4, 4, 128, 256),
+                                            # widths that are multiples of 128: row patches
+                                            (1, 3, 128, 32, 32), (2, 2, 256, 64, 32),
+                                            (1, 4, 128, 32, 64), (1, 2, 128, 128, 32),
+                                            (1, 2, 256, 32, 128), (1, 2, 128, 64, 128),
+                                            (1, 2, 128, 256, 32)])
 def test_conv_kernel_is_exact_on_bf16_data(B, H, W, cin, cout):
     import torch
     rng = np.random.default_rng(B * 1000 + cin + cout)
@@ -99,8 +104,9 @@ def test_params_round_trip():
     assert np.array_equal(net.params(), theta)
 
 
-def test_forward_matches_fp64_reference():
-    net, theta, feat, _ = _net_and_data()
+@pytest.mark.parametrize("B,H,W", [(2, 32, 32), (1, 32, 128)])
+def test_forward_matches_fp64_reference(B, H, W):
+    net, theta, feat, _ = _net_and_data(B, H, W)
     got = net.forward(feat).cpu().numpy()
     want = ref.forward(theta.astype(np.float64), feat.cpu().numpy())
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
@@ -108,8 +114,9 @@ def test_forward_matches_fp64_reference():
     assert err <= 3e-2
 
 
-def test_gradients_match_fp64_reference():
-    net, theta, feat, target = _net_and_data()
+@pytest.mark.parametrize("B,H,W", [(2, 32, 32), (1, 32, 128)])
+def test_gradients_match_fp64_reference(B, H, W):
+    net, theta, feat, target = _net_and_data(B, H, W)
     loss, g = net.loss_grad(feat, target)
     rloss, rg = ref.loss_grad(theta.astype(np.float64), feat.cpu().numpy(), target.cpu().numpy())
     assert abs(loss / rloss - 1) <= 3e-2
