@@ -19,6 +19,8 @@
 //
 // Every wait on an mbarrier has an iteration limit; a CTA that gives up sets
 // conv_tc_error, skips its epilogue, frees its TMEM and returns.
+#include <cuda.h>
+
 #include "surr_internal.h"
 
 namespace surr {
@@ -331,30 +333,59 @@ k_conv3x3_tc(const bf16 *__restrict__ in, int B, int H, int W, int cin,
 // 32-channel chunk the CTA loads the patch once -- rows y-1, y, y+1 of pixels
 // x0-1 .. x0+128 (periodic) -- laid out as [row][8-channel group][pixel][16
 // bytes], i.e. K-major core matrices with 8-row groups 128 bytes apart (SBO)
-// and channel groups 130 * 16 bytes apart (LBO).  Tap (dy, dx) is then the
+// and channel groups PATCH_ARR bytes apart (LBO).  Tap (dy, dx) is then the
 // descriptor whose start is row dy + 1, pixel dx + 1: 18 MMAs per chunk
-// (9 taps x K = 32) read one patch.  CTAs are persistent over the tiles and
-// keep their N-slice of the weights in shared memory for the whole launch
-// ([tap][chunk][channel group][n][16 bytes]), so the weights leave L2 once per
-// CTA instead of once per tile.  Patches are double-buffered: the next item's
-// patch loads while this item's MMAs run, and the MMAs of the item before
-// must be done (its mbarrier) before its buffer is refilled.  After a tile's
-// last chunk the CTA waits for its MMAs and runs the epilogue from TMEM.
+// (9 taps x K = 32) read one patch.
+//
+// The patch's 128 interior pixels of each row and channel group arrive by
+// TMA (cp.async.bulk.tensor over the NHWC activations, box 8 channels x 128
+// pixels, 2 KB, 128-byte aligned in shared memory), twelve copies per patch
+// issued by one thread and counted on the buffer's "full" mbarrier; the two
+// wrapped edge pixels of each row and group come by cp.async.
+//
+// CTAs are persistent over the tiles and keep their N-slice of the weights in
+// shared memory for the whole launch ([tap][chunk][channel group][n][16
+// bytes]), so the weights leave L2 once per CTA instead of once per tile.
+// Patches rotate through PATCH_BUF buffers: item i + PATCH_BUF - 1 loads while
+// item i's MMAs run, once the MMAs of item i - 1 (which read that buffer) are
+// done.  After a tile's last chunk the CTA waits for its MMAs and runs the
+// epilogue from TMEM.
 // ---------------------------------------------------------------------------
-constexpr int PATCH_PIX = TM + 2;                      // pixels per patch row
-constexpr int PATCH_GROUP = PATCH_PIX * 16;            // bytes per channel group
-constexpr int PATCH_BYTES = 3 * 4 * PATCH_GROUP;       // 3 rows x 4 groups
+constexpr int PATCH_ARR = 2304;                  // bytes per [row][group] array (18 x 128)
+constexpr int PATCH_BUF = 2;                     // patch buffers per CTA
+constexpr int PATCH_J0 = 112;                    // offset of pixel 0: pixel 1 is 128-aligned
+constexpr int PATCH_BYTES = 3 * 4 * PATCH_ARR;   // 3 rows x 4 channel groups
+constexpr uint32_t PATCH_TMA_BYTES = 12 * TM * 16;
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 4-D tiled TMA load (channels, x, y, image) into shared memory, completing
+// on the mbarrier's transaction count.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c, int x,
+                                            int y, int b, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(x), "r"(y), "r"(b), "r"(smem_u32(bar))
+        : "memory");
+}
 
 template <int NT, int MODE, bool ACT, bool SKIP>
 __global__ void __launch_bounds__(128)
-k_conv3x3_rows(const bf16 *__restrict__ in, int B, int H, int W, int cin,
-               const bf16 *__restrict__ w, int cout, const float *__restrict__ bias,
-               const bf16 *__restrict__ skip, bf16 *__restrict__ out_bf,
-               float *__restrict__ out_f) {
+k_conv3x3_rows(const __grid_constant__ CUtensorMap tmap, const bf16 *__restrict__ in, int B,
+               int H, int W, int cin, const bf16 *__restrict__ w, int cout,
+               const float *__restrict__ bias, const bf16 *__restrict__ skip,
+               bf16 *__restrict__ out_bf, float *__restrict__ out_f) {
+    constexpr int nbuf = PATCH_BUF;
     constexpr uint32_t TCOLS = NT;
     static_assert(NT == 32 || NT == 64 || NT == 128 || NT == 256, "TMEM allocation size");
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar[2];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mma_done[PATCH_BUF];
+    __shared__ __align__(8) uint64_t full[PATCH_BUF];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -367,12 +398,17 @@ k_conv3x3_rows(const bf16 *__restrict__ in, int B, int H, int W, int cin,
     const long long my_tiles =
         blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const long long nitems = my_tiles * kchunks;
+    // TMA destinations must be 128-byte aligned: align the base (the launch
+    // adds 128 bytes of slack)
+    unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     unsigned char *wsm = smem;                                   // weights
-    unsigned char *patch = smem + size_t(18) * cin * NT;         // two patch buffers
+    unsigned char *patch = smem + size_t(18) * cin * NT;         // nbuf patch buffers
 
     if (tid == 0) {
-        mbar_init(&bar[0]);
-        mbar_init(&bar[1]);
+        for (int k = 0; k < nbuf; ++k) {
+            mbar_init(&mma_done[k]);
+            mbar_init(&full[k]);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
     }
@@ -399,40 +435,61 @@ k_conv3x3_rows(const bf16 *__restrict__ in, int B, int H, int W, int cin,
                  w + ((long long)(co0 + n) * 9 + t) * cin + ci8 * 8);
         }
     }
-    auto tile_of = [&](long long item) { return blockIdx.x + (item / kchunks) * gridDim.x; };
-    auto load_patch = [&](long long item) {
-        unsigned char *buf = patch + (item & 1) * PATCH_BYTES;
-        const long long p0 = tile_of(item) * TM;
-        const int c = int(item % kchunks);
-        const long long row = p0 / W;                 // b * H + y
-        const int x0 = int(p0 - row * W), y = int(row % H);
-        const bf16 *img = in + (row - y) * W * cin + c * KC;
+    // threads 0 .. 23 write a patch buffer (thread 0 by TMA, all 24 an edge
+    // pixel each); the rest only read it.  Pixel indices fit 32 bits (the
+    // network's workspace check).
+    auto load_patch = [&](unsigned tile, int c, int sb) {
+        unsigned char *buf = patch + sb * PATCH_BYTES;
+        const unsigned p0 = tile * unsigned(TM);
+        const unsigned row = p0 / unsigned(W);       // b * H + y
+        const int x0 = int(p0 - row * unsigned(W)), y = int(row % unsigned(H));
+        const int b = int(row / unsigned(H));
         const int ym = y == 0 ? H - 1 : y - 1, yp = y == H - 1 ? 0 : y + 1;
-        // one pixel of one patch row per iteration: its 64 contiguous bytes
-        // go to the four channel-group arrays
-        for (int q = tid; q < 3 * PATCH_PIX; q += 128) {
-            const int r = q / PATCH_PIX, j = q - r * PATCH_PIX;
-            const int yy = r == 0 ? ym : (r == 1 ? y : yp);
-            int xx = x0 + j - 1;
-            xx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
-            const bf16 *src = img + ((long long)yy * W + xx) * cin;
-            unsigned char *dst = buf + r * 4 * PATCH_GROUP + j * 16;
+        if (tid == 0) {
+            mbar_expect_tx(&full[sb], PATCH_TMA_BYTES);
 #pragma unroll
-            for (int kg = 0; kg < 4; ++kg) cp16(dst + kg * PATCH_GROUP, src + kg * 8);
+            for (int r = 0; r < 3; ++r) {
+                const int yy = r == 0 ? ym : (r == 1 ? y : yp);
+#pragma unroll
+                for (int kg = 0; kg < 4; ++kg)
+                    tma_load_4d(smem_u32(buf + (r * 4 + kg) * PATCH_ARR + PATCH_J0 + 16), &tmap,
+                                c * KC + kg * 8, x0, yy, b, &full[sb]);
+            }
+        }
+        const int r = tid >> 3, e = (tid >> 2) & 1, kg = tid & 3;
+        const int yy = r == 0 ? ym : (r == 1 ? y : yp);
+        const int xx = e ? (x0 + TM == W ? 0 : x0 + TM) : (x0 == 0 ? W - 1 : x0 - 1);
+        cp16(buf + (r * 4 + kg) * PATCH_ARR + PATCH_J0 + (e ? (TM + 1) * 16 : 0),
+             in + ((size_t(b) * H + yy) * W + xx) * cin + c * KC + kg * 8);
+    };
+    // items are (tile, chunk) pairs, chunk fastest; the tiles of this CTA are
+    // blockIdx.x, + gridDim.x, ...
+    auto advance = [&](unsigned &tile, int &c) {
+        if (++c == kchunks) {
+            c = 0;
+            tile += gridDim.x;
         }
     };
 
     bool ok = true;
-    if (nitems > 0) load_patch(0);
-    cp_commit();
+    unsigned pf_tile = blockIdx.x;   // next item to load
+    int pf_c = 0;
+    for (int k = 0; k < nbuf - 1; ++k) {
+        if (k < nitems) {
+            if (tid < 24) load_patch(pf_tile, pf_c, k % nbuf);
+            advance(pf_tile, pf_c);
+        }
+        cp_commit();
+    }
+    unsigned cur_tile = blockIdx.x;
+    int c = 0;
     for (long long i = 0; i < nitems; ++i) {
-        const int sb = int(i & 1);
-        const int c = int(i % kchunks);
-        cp_wait<0>();
+        const int sb = int(i % nbuf);
+        if (ok && !mbar_wait(&full[sb], uint32_t(i / nbuf) & 1)) ok = false;
+        cp_wait<PATCH_BUF - 2>();   // this item's edge pixels (later items' may fly)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_fence_before();
-        __syncthreads();
-        if (abort_flag) break;
+        if (__syncthreads_or(!ok)) break;
         if (tid == 0) {
             tc_fence_after();
             const uint32_t pb = smem_u32(patch + sb * PATCH_BYTES), wb = smem_u32(wsm);
@@ -441,73 +498,118 @@ k_conv3x3_rows(const bf16 *__restrict__ in, int B, int H, int W, int cin,
                 const int dy = t / 3, dx = t % 3;   // patch row, pixel offset
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const uint32_t a = pb + (dy * 4 + 2 * h) * PATCH_GROUP + dx * 16;
+                    const uint32_t a = pb + (dy * 4 + 2 * h) * PATCH_ARR + PATCH_J0 + dx * 16;
                     const uint32_t bw = wb + ((t * kchunks + c) * 4 + 2 * h) * NT * 16;
-                    umma(tmem, umma_desc(a, PATCH_GROUP, 128), umma_desc(bw, NT * 16, 128),
+                    umma(tmem, umma_desc(a, PATCH_ARR, 128), umma_desc(bw, NT * 16, 128),
                          umma_idesc<NT>(), (c | t | h) != 0);
                 }
             }
-            umma_commit(&bar[sb]);
+            umma_commit(&mma_done[sb]);
         }
-        if (i + 1 < nitems) {
-            // the buffer of item i + 1 last served item i - 1
-            if (i >= 1 && !mbar_wait(&bar[sb ^ 1], uint32_t((i - 1) >> 1) & 1)) ok = false;
-            if (ok) load_patch(i + 1);
+        if (i + nbuf - 1 < nitems) {
+            if (tid < 24) {
+                // the buffer of item i + nbuf - 1 last served item i - 1
+                if (i >= 1 && !mbar_wait(&mma_done[(i - 1) % nbuf], uint32_t((i - 1) / nbuf) & 1))
+                    ok = false;
+                if (ok) load_patch(pf_tile, pf_c, int((i + nbuf - 1) % nbuf));
+            }
+            advance(pf_tile, pf_c);
         }
         cp_commit();
         if (c == kchunks - 1) {
-            if (!mbar_wait(&bar[sb], uint32_t(i >> 1) & 1)) ok = false;
+            if (!mbar_wait(&mma_done[sb], uint32_t(i / nbuf) & 1)) ok = false;
             // tcgen05.ld is warp-collective: decide for the whole CTA
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) abort_flag = 1;
-                break;
-            }
+            if (__syncthreads_or(!ok)) break;
             tc_fence_after();
-            const long long p = tile_of(i) * TM + tid;
+            const long long p = (long long)cur_tile * TM + tid;
             epilogue<NT, MODE, ACT, SKIP>(tmem + (uint32_t(warp * 32) << 16), p, true, co0, cout,
                                           bias, skip, out_bf, out_f);
         }
-        if (!ok) abort_flag = 1;
+        advance(cur_tile, c);
     }
     cp_wait<0>();
-    if (abort_flag && tid == 0) atomicExch(&g_conv_tc_error, 1);
+    if (!ok) abort_flag = 1;
     tc_fence_before();
     __syncthreads();
+    if (abort_flag) {
+        // TMA copies may still be in flight: let them land (bounded) before
+        // the CTA's shared memory is released
+        if (tid == 0) {
+            atomicExch(&g_conv_tc_error, 1);
+            for (long long i = nitems - nbuf; i < nitems; ++i)
+                if (i >= 0) mbar_wait(&full[i % nbuf], uint32_t(i / nbuf) & 1);
+        }
+        __syncthreads();
+    }
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(TCOLS)
                      : "memory");
 }
 
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime.
+EncodeTiled encode_tiled() {
+    static EncodeTiled fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return EncodeTiled(nullptr);
+        return reinterpret_cast<EncodeTiled>(p);
+    }();
+    return fn;
+}
+
 template <int NT, int MODE, bool ACT, bool SKIP>
 cudaError_t launch_rows(const ConvArgs &a, long long ntiles, cudaStream_t st) {
     auto k = k_conv3x3_rows<NT, MODE, ACT, SKIP>;
-    const int smem = 18 * a.cin * NT + 2 * PATCH_BYTES;
-    static int dev_sms = 0, dev_smem = 0;
+    // TMA view of the input: (channels, x, y, image), box 8 channels x 128 pixels
+    const EncodeTiled enc = encode_tiled();
+    if (!enc || (reinterpret_cast<uintptr_t>(a.in) & 15)) return cudaErrorNotSupported;
+    CUtensorMap map;
+    const cuuint64_t dims[4] = {cuuint64_t(a.cin), cuuint64_t(a.W), cuuint64_t(a.H),
+                                cuuint64_t(a.B)};
+    const cuuint64_t strides[3] = {cuuint64_t(a.cin) * 2, cuuint64_t(a.W) * a.cin * 2,
+                                   cuuint64_t(a.H) * a.W * a.cin * 2};
+    const cuuint32_t box[4] = {8, TM, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(a.in), dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    static int dev_sms = 0, dev_smem = 0, dev_smem_block = 0;
     if (dev_sms == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&dev_smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (dev_sms < 1) dev_sms = 1;
     }
+    // CTAs per SM from shared memory -- dynamic + static + the 1 KB the system
+    // reserves per CTA -- and TMEM, 512 columns.  (Deeper patch rings measured
+    // slower: the chunk's 18 MMAs into one accumulator, not the loads, bound
+    // a CTA that has to give up CTAs per SM for them.)
+    const int smem = 128 + 18 * a.cin * NT + PATCH_BUF * PATCH_BYTES;
+    const int per_sm = std::min(std::min(dev_smem / (smem + 1024 + 256), 512 / NT), 16);
+    if (smem > dev_smem_block || per_sm < 1) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  int(cudaSharedmemCarveoutMaxShared));
     if (e != cudaSuccess) return e;
-    // CTAs per SM from shared memory (dynamic + static + the 1 KB the
-    // system reserves per CTA) and TMEM (512 columns per SM)
-    int per_sm = dev_smem / (smem + 1024 + 256);
-    per_sm = std::min(per_sm, 512 / NT);
-    per_sm = std::min(per_sm, 16);
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int ny = a.cout / NT;
     long long ctas = (long long)dev_sms * per_sm / ny;
     if (ctas < 1) ctas = 1;
     if (ctas > ntiles) ctas = ntiles;
     k<<<dim3(unsigned(ctas), unsigned(ny)), 128, smem, st>>>(
-        a.in, a.B, a.H, a.W, a.cin, a.w, a.cout, a.bias, a.skip, a.out_bf, a.out_f);
+        map, a.in, a.B, a.H, a.W, a.cin, a.w, a.cout, a.bias, a.skip, a.out_bf, a.out_f);
     return cudaGetLastError();
 }
 
