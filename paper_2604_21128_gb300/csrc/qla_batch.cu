@@ -3,9 +3,10 @@
 //
 // Work is a flat list of items -- (instance, column window, row segment) --
 // of similar cost whatever the lattice sizes.  Each warp of a grid sized to
-// be fully co-resident takes items round-robin and runs the marching step on
-// them (qla_march.cuh); after each step the grid meets at a barrier so that
-// the next step reads finished rows.  The barrier's wait is bounded: a block
+// be fully co-resident takes items from a shared counter as it frees up and
+// runs the marching step on them (qla_march.cuh); after each step the grid
+// meets at a barrier so that the next step reads finished rows.  The
+// barrier's wait is bounded: a block
 // that waits longer than the budget raises an error word and every block
 // leaves, and the host reports QLA_ETIMEOUT.  qla_batch_run captures a whole
 // run (step chunks and batched energy reductions) as one CUDA graph.
@@ -42,6 +43,7 @@ struct BatchItem {
 struct Barrier {
     unsigned count;        // blocks arrived at the current barrier
     unsigned gen;          // barriers completed
+    unsigned next[2];      // next work item of the steps of even / odd parity
     int err;               // set when a wait ran out
     int pad;
 };
@@ -92,11 +94,20 @@ k_batch_march(const BatchInst *__restrict__ insts, const BatchItem *__restrict__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     typename M::Slot *ring =
         reinterpret_cast<typename M::Slot *>(smem_raw) + (threadIdx.x >> 5) * NSLOT;
-    const int warp = blockIdx.x * WARPS + (threadIdx.x >> 5);
-    const int warps = gridDim.x * WARPS;
+    const int lane = threadIdx.x & 31;
     if (*static_cast<volatile int *>(&bar->err)) return;
     for (int s = 0; s < n_steps; ++s) {
-        for (int it = warp; it < n_items; it += warps) {
+        // step s takes items from next[s & 1]; next[(s + 1) & 1] served step
+        // s - 1, which every block has finished, and serves step s + 1, which
+        // starts after the next barrier (whose fence publishes the reset)
+        if (blockIdx.x == 0 && threadIdx.x == 0) bar->next[(s + 1) & 1] = 0;
+        for (;;) {
+            // items go to whichever warp is free next: the step ends with at
+            // most one item's worth of imbalance left at the barrier
+            int it = 0;
+            if (lane == 0) it = int(atomicAdd(&bar->next[s & 1], 1u));
+            it = __shfl_sync(0xffffffffu, it, 0);
+            if (it >= n_items) break;
             const BatchItem bi = items[it];
             const BatchInst &I = insts[bi.inst];
             const int src = (I.cur + step0 + s) & 1;
