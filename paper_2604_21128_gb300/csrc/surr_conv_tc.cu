@@ -12,8 +12,9 @@
 // 32w .. 32w + 31, i.e. its 32 pixels) and applies bias, skip, activation and
 // the output conversion.
 //
-// Two kernels: k_conv3x3_tc gathers a stage per tap and chunk (six stages,
-// four loaded ahead); k_conv3x3_rows, for widths that are multiples of 128,
+// Two kernels: k_conv3x3_tc gathers a stage per tap and 32 or 64 channels
+// (six or four stages, two fewer loaded ahead); k_conv3x3_rows, for widths
+// that are multiples of 128,
 // loads one halo'd row patch per chunk that serves all nine taps and keeps
 // the weights resident in persistent CTAs.
 //
@@ -27,9 +28,11 @@ namespace surr {
 namespace {
 
 constexpr int TM = 128;          // pixels per CTA = TMEM lanes
-constexpr int KC = 32;           // input channels per stage (two K = 16 MMAs)
-constexpr int NSTAGE = 6;        // shared-memory stages
-constexpr int AHEAD = NSTAGE - 2;  // stages loaded ahead of the MMA
+constexpr int KC = 32;           // input channels per row-patch chunk (two K = 16 MMAs)
+
+// Gather-kernel stages: KS input channels of one tap (KS / 16 MMAs), six
+// stages of 32 channels or four of 64, all but two loaded ahead of the MMA.
+template <int KS> constexpr int gather_stages() { return KS == 32 ? 6 : 4; }
 constexpr unsigned WAIT_LIMIT = 1u << 22;
 
 __device__ int g_conv_tc_error;
@@ -195,18 +198,20 @@ __device__ __forceinline__ void epilogue(uint32_t lane_base, long long p, bool v
     }
 }
 
-template <int NT>
+template <int NT, int KS>
 constexpr int stage_bytes() {
-    return TM * KC * 2 + NT * KC * 2;
+    return TM * KS * 2 + NT * KS * 2;
 }
 
-template <int NT, int MODE, bool ACT, bool SKIP>
+template <int NT, int KS, int MODE, bool ACT, bool SKIP>
 __global__ void __launch_bounds__(128)
 k_conv3x3_tc(const bf16 *__restrict__ in, int B, int H, int W, int cin,
              const bf16 *__restrict__ w, int cout, const float *__restrict__ bias,
              const bf16 *__restrict__ skip, bf16 *__restrict__ out_bf, float *__restrict__ out_f) {
-    constexpr int A_BYTES = TM * KC * 2;
-    constexpr int STAGE = stage_bytes<NT>();
+    constexpr int NSTAGE = gather_stages<KS>(), AHEAD = NSTAGE - 2;
+    constexpr int KG = KS / 8;                 // 16-byte channel groups per stage
+    constexpr int A_BYTES = TM * KS * 2;
+    constexpr int STAGE = stage_bytes<NT, KS>();
     constexpr uint32_t TCOLS = NT;   // a power of two, >= 32
     static_assert(NT == 32 || NT == 64 || NT == 128 || NT == 256, "TMEM allocation size");
     extern __shared__ __align__(128) unsigned char smem[];
@@ -245,30 +250,30 @@ k_conv3x3_tc(const bf16 *__restrict__ in, int B, int H, int W, int cin,
         ay = rem / W;
         ax = rem - ay * W;
     }
-    const uint32_t a_off = uint32_t((tid >> 3) * 4 * 128 + (tid & 7) * 16);
-    const int kchunks = cin / KC;
+    const uint32_t a_off = uint32_t((tid >> 3) * KG * 128 + (tid & 7) * 16);
+    const int kchunks = cin / KS;
     const int ksteps = 9 * kchunks;
 
     auto load = [&](int ks) {
         unsigned char *sa = smem + (ks % NSTAGE) * STAGE;
         unsigned char *sb = sa + A_BYTES;
-        const int tap = ks / kchunks, ci0 = (ks - tap * kchunks) * KC;
+        const int tap = ks / kchunks, ci0 = (ks - tap * kchunks) * KS;
         const int dy = tap / 3 - 1, dx = tap % 3 - 1;
         if (a_ok) {
             const long long ps = (long long)ab * H * W + (long long)wrapi(ay + dy, H) * W +
                                  wrapi(ax + dx, W);
             const bf16 *src = in + ps * cin + ci0;
 #pragma unroll
-            for (int kg = 0; kg < 4; ++kg) cp16(sa + a_off + kg * 128, src + kg * 8);
+            for (int kg = 0; kg < KG; ++kg) cp16(sa + a_off + kg * 128, src + kg * 8);
         } else {
 #pragma unroll
-            for (int kg = 0; kg < 4; ++kg)
+            for (int kg = 0; kg < KG; ++kg)
                 *reinterpret_cast<uint4 *>(sa + a_off + kg * 128) = make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
-        for (int c = tid; c < NT * 4; c += 128) {
-            const int n = c >> 2, kg = c & 3;
-            cp16(sb + ((n >> 3) * 4 + kg) * 128 + (n & 7) * 16,
+        for (int c = tid; c < NT * KG; c += 128) {
+            const int n = c / KG, kg = c % KG;
+            cp16(sb + ((n >> 3) * KG + kg) * 128 + (n & 7) * 16,
                  w + ((long long)(co0 + n) * 9 + tap) * cin + ci0 + kg * 8);
         }
     };
@@ -296,8 +301,9 @@ k_conv3x3_tc(const bf16 *__restrict__ in, int B, int H, int W, int cin,
             tc_fence_after();
             const uint32_t a0 = smem_u32(smem + (ks % NSTAGE) * STAGE), b0 = a0 + A_BYTES;
 #pragma unroll
-            for (int k = 0; k < KC / 16; ++k)
-                umma(tmem, umma_desc(a0 + k * 256, 128, 512), umma_desc(b0 + k * 256, 128, 512),
+            for (int k = 0; k < KS / 16; ++k)
+                umma(tmem, umma_desc(a0 + k * 256, 128, KG * 128),
+                     umma_desc(b0 + k * 256, 128, KG * 128),
                      umma_idesc<NT>(), (ks | k) != 0);
             umma_commit(&bar[ks % NSTAGE]);
         }
@@ -613,16 +619,23 @@ cudaError_t launch_rows(const ConvArgs &a, long long ntiles, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int NT, int MODE, bool ACT, bool SKIP>
-cudaError_t launch_nt(const ConvArgs &a, long long mtiles, cudaStream_t st) {
-    auto k = k_conv3x3_tc<NT, MODE, ACT, SKIP>;
-    constexpr int smem = NSTAGE * stage_bytes<NT>();
+template <int NT, int KS, int MODE, bool ACT, bool SKIP>
+cudaError_t launch_ks(const ConvArgs &a, long long mtiles, cudaStream_t st) {
+    auto k = k_conv3x3_tc<NT, KS, MODE, ACT, SKIP>;
+    constexpr int smem = gather_stages<KS>() * stage_bytes<NT, KS>();
     static cudaError_t attr = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    smem);
     if (attr != cudaSuccess) return attr;
     k<<<dim3(unsigned(mtiles), unsigned(a.cout / NT)), 128, smem, st>>>(
         a.in, a.B, a.H, a.W, a.cin, a.w, a.cout, a.bias, a.skip, a.out_bf, a.out_f);
     return cudaGetLastError();
+}
+
+// 64-channel stages (four MMAs per barrier) where the input channels allow.
+template <int NT, int MODE, bool ACT, bool SKIP>
+cudaError_t launch_nt(const ConvArgs &a, long long mtiles, cudaStream_t st) {
+    return a.cin % 64 == 0 ? launch_ks<NT, 64, MODE, ACT, SKIP>(a, mtiles, st)
+                           : launch_ks<NT, 32, MODE, ACT, SKIP>(a, mtiles, st);
 }
 
 template <int MODE, bool ACT, bool SKIP>
