@@ -229,8 +229,7 @@ struct March {
     // state carried along the march
     T carry[4][2][2][LX];   // [neighbour layer][pair][value][x]
     CC kring[LAG][LX];      // collision coefficients of the rows in flight
-    CC knext[LX];           // row J+1's records, looked up one row early
-    CV vnext[LX];
+    CV vnext[LX];           // row J+1's potential coefficients
     // row offsets: next row to stage, the two output rows
     uint32_t o_in, o_now, o_out;
 
@@ -250,19 +249,21 @@ struct March {
         o_in = next_row(o_in);
     }
 
-    template <int S>
+    // Row J + 1's records (staging slot S) into ring slot K of the collision
+    // coefficients and into vnext.
+    template <int S, int K>
     __device__ __forceinline__ void lookup_next() {
 #pragma unroll
         for (int x = 0; x < LX; ++x) {
             const MedRec<T> *r = table + ring[S].idx[lc + x];
-            knext[x] = r->c;
+            kring[K][x] = r->c;
             if constexpr (VIN) vnext[x] = r->v;
         }
     }
 
     // One march iteration for input row J; PH = (J - J0) mod 4 picks the
-    // register ring slots and the staging slot of row J.  On entry knext,
-    // vnext hold row J's records.  Rows J and J - 4 are stored when they
+    // register ring slots and the staging slot of row J.  On entry kring[PH]
+    // and vnext hold row J's records.  Rows J and J - 4 are stored when they
     // fall in [st_lo, st_lo + st_n).
     template <int PH>
     __device__ __forceinline__ void iter(int J, int st_lo, unsigned st_n) {
@@ -279,8 +280,6 @@ struct March {
                 for (int x = 0; x < LX; ++x) q[c][x] = ring[PH].q[p][lc + x];
             }
         }
-#pragma unroll
-        for (int x = 0; x < LX; ++x) kring[S0][x] = knext[x];
         // the previous step's V_x, V_y on the entering row
         if constexpr (VIN) {
 #pragma unroll
@@ -294,9 +293,6 @@ struct March {
                     if (plane_of<P>(c) >= 0) q[c][x] = s[c];
             }
         }
-        // row J + 1's records fly while this row computes
-        lookup_next<(PH + 1) & (NSLOT - 1)>();
-
         apply_ux<T, P, LX>(q, kring[S0]);                          // U_x, row J
 
         // planes U_y does not touch are final for row J now
@@ -317,6 +313,9 @@ struct March {
         uy_neighbour<T, P, LX, 5>(q, carry[2], kring[S3]);         // L6 -> row J-3
         uy_local<T, P, LX, 6>(q, kring[S3]);                       // L7, row J-3
         uy_neighbour<T, P, LX, 7>(q, carry[3], kring[S3]);         // L8 -> row J-4
+        // row J - 3's coefficients (slot S3) are dead: row J + 1's records
+        // go straight into that slot
+        lookup_next<(PH + 1) & (NSLOT - 1), S3>();
 
         // the U_y planes of row J - 4 are final
         if (unsigned(J - LAG - st_lo) < st_n) {
@@ -370,7 +369,7 @@ struct March {
         stage<1>();
         stage<2>();
         cp_async_wait<2>();
-        lookup_next<0>();
+        lookup_next<0, 0>();
         for (int J = J0; J < J1; J += 4) {
             iter<0>(J + 0, y_lo, st_n);
             iter<1>(J + 1, y_lo, st_n);
