@@ -81,7 +81,21 @@ enum {
      * ~1e87 over 400 steps of the 256^2 ellipse workload).  For measuring
      * that, not for physics.  Excludes the two flags above; stepped by the
      * tile kernel with V applied within each launch. */
-    QLA_POTENTIAL_LCU = 16u
+    QLA_POTENTIAL_LCU = 16u,
+    /* FP64 contexts: qla_step advances with the marching kernel in
+     * double-single arithmetic (each amplitude an unevaluated sum of two FP32
+     * words; products exact through FMA, sums by error-free transformations;
+     * cos and sin held as three FP32 words, which reproduce the FP64
+     * coefficients exactly).  The state is converted in place to word pairs
+     * when qla_step starts and back to FP64 when it returns, so every other
+     * call sees an ordinary FP64 context.  Results differ from the native
+     * FP64 kernels by rounding only (relative L2 ~1e-13 after 400 steps).
+     * Not part of Eq. 2e14: an arithmetic for GPUs whose FP32 pipes are
+     * much faster than their FP64 pipe.  Needs QLA_FP64, a lattice the
+     * marching kernel takes (nx even, nx >= 64, ny >= 8), a scalar medium and
+     * the rotation or no-potential reading; QLA_EINVAL otherwise.  The
+     * workspace gains a table of double-single coefficient records. */
+    QLA_DOUBLE_SINGLE = 32u
 };
 
 /* E_z-polarised Gaussian packet (Sec. V-B): with

@@ -49,6 +49,10 @@ Layout layout_for(int nx, int ny, int prec, unsigned flags) {
             L.ttable = off; off += align256(L.plane_elems * trec);
         }
     }
+    L.dstable = 0;
+    if ((flags & QLA_DOUBLE_SINGLE) && prec == QLA_FP64) {
+        L.dstable = off; off += align256((UNIFORM_SLOTS + sites) * sizeof(MedRec<dsf>));
+    }
     L.total = off;
     return L;
 }
@@ -107,6 +111,11 @@ extern "C" {
 size_t qla_workspace_bytes(int nx, int ny, int precision, unsigned flags) {
     if (nx < 1 || ny < 1 || (precision != QLA_FP64 && precision != QLA_FP32)) return 0;
     if (size_t(nx) * size_t(ny) > (size_t(1) << 34)) return 0;
+    if ((flags & QLA_DOUBLE_SINGLE) &&
+        (precision != QLA_FP64 ||
+         (flags & (QLA_ANISOTROPIC | QLA_POTENTIAL_LITERAL | QLA_POTENTIAL_LCU)) ||
+         !ds_shape_ok(nx, ny)))
+        return 0;
     return layout_for(nx, ny, precision, flags).total;
 }
 
@@ -118,12 +127,17 @@ qla_status qla_init_grid(qla_ctx **out, int nx, int ny, double delta, int precis
     if (nx < 1 || ny < 1 || !(delta > 0.0) || !std::isfinite(delta)) return QLA_EINVAL;
     if (precision != QLA_FP64 && precision != QLA_FP32) return QLA_EINVAL;
     if (flags & ~(unsigned)(QLA_TE_ONLY | QLA_POTENTIAL_LITERAL | QLA_POTENTIAL_NONE |
-                            QLA_ANISOTROPIC | QLA_POTENTIAL_LCU))
+                            QLA_ANISOTROPIC | QLA_POTENTIAL_LCU | QLA_DOUBLE_SINGLE))
         return QLA_EINVAL;
     {
         const unsigned v = flags & (QLA_POTENTIAL_LITERAL | QLA_POTENTIAL_NONE | QLA_POTENTIAL_LCU);
         if (v & (v - 1)) return QLA_EINVAL;  // at most one potential reading
     }
+    if ((flags & QLA_DOUBLE_SINGLE) &&
+        (precision != QLA_FP64 || (flags & (QLA_ANISOTROPIC | QLA_POTENTIAL_LITERAL |
+                                            QLA_POTENTIAL_LCU)) ||
+         !ds_shape_ok(nx, ny)))
+        return QLA_EINVAL;
     if (size_t(nx) * size_t(ny) > (size_t(1) << 34)) return QLA_EINVAL;
     if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255)) return QLA_EINVAL;
 
@@ -178,6 +192,7 @@ qla_status qla_init_grid(qla_ctx **out, int nx, int ny, double delta, int precis
         c->n_y = reinterpret_cast<double *>(c->ws + L.n_y);
         if (c->P == 6) c->ttable = c->ws + L.ttable;
     }
+    if (flags & QLA_DOUBLE_SINGLE) c->dstable = c->ws + L.dstable;
     // both state buffers start at zero (pad columns included)
     if (cudaMemsetAsync(c->ws + L.state[0], 0, L.midx - L.state[0], c->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -355,6 +370,22 @@ qla_status qla_step(qla_ctx *c, long long n_steps) {
             c->cur ^= 1;
         }
         c->pending_v = false;
+        return QLA_OK;
+    }
+    if (c->dstable) {
+        // word pairs in place, n double-single steps, back to FP64
+        QLA_CUDA(c, launch_state_to_ds(c, c->state[c->cur]), "qla_step: to double-single");
+        c->launches++;
+        for (long long k = 0; k < n_steps; ++k) {
+            QLA_CUDA(c, launch_step_march_ds(c, c->state[c->cur], c->state[c->cur ^ 1],
+                                             c->pending_v),
+                     "qla_step: kernel");
+            c->launches++;
+            c->cur ^= 1;
+            c->pending_v = c->vmode != V_NONE;
+        }
+        QLA_CUDA(c, launch_state_from_ds(c, c->state[c->cur]), "qla_step: from double-single");
+        c->launches++;
         return QLA_OK;
     }
     const bool march = c->step_kernel == QLA_KERNEL_MARCH ||

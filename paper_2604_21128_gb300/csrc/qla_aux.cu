@@ -46,6 +46,31 @@ __device__ __forceinline__ void make_rec(MedRec<float> &r, double th, double px,
                       __double2float_rn(2.0 * shy * shy), __double2float_rn(sin(py)));
 }
 
+// An FP64 value as three FP32 words whose exact sum it is.
+__device__ __forceinline__ void split3(double v, float &a, float &b, float &c) {
+    a = __double2float_rn(v);
+    const double r = v - double(a);
+    b = __double2float_rn(r);
+    c = __double2float_rn(r - double(b));
+}
+
+__device__ __forceinline__ void split3(double cv, double sv, DSCoef &k) {
+    split3(cv, k.c0, k.c1, k.c2);
+    split3(sv, k.s0, k.s1, k.s2);
+    k.pad0 = k.pad1 = 0.0f;
+}
+
+// Double-single records: the FP64 record's cosines and sines, three words each.
+__device__ __forceinline__ void make_rec(MedRec<dsf> &r, double th, double px, double py) {
+    double s, c;
+    sincos(th, &s, &c);
+    split3(c, s, r.c);
+    double sx, cx, sy, cy;
+    sincos(px, &sx, &cx);
+    sincos(py, &sy, &cy);
+    split3(cx, sx, r.v.x);
+    split3(cy, sy, r.v.y);
+}
 
 // One pass over the sites: classify, hand out a record index, write each
 // record once.  A site whose four neighbours carry exactly its n has beta = 0
@@ -60,7 +85,7 @@ template <typename T>
 __global__ void k_medium(const double *__restrict__ n, int nx, int ny, int pitch, double delta,
                          double vscale, unsigned long long *__restrict__ keys,
                          unsigned *__restrict__ counter, uint32_t *__restrict__ midx,
-                         MedRec<T> *__restrict__ table) {
+                         MedRec<T> *__restrict__ table, MedRec<dsf> *__restrict__ ds_table) {
     namespace cg = cooperative_groups;
     const size_t N = size_t(nx) * ny;
     for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < N;
@@ -106,6 +131,11 @@ __global__ void k_medium(const double *__restrict__ n, int nx, int ny, int pitch
             MedRec<T> r;
             make_rec(r, th, vscale * bx, vscale * by);
             table[id] = r;
+            if (ds_table) {   // QLA_DOUBLE_SINGLE: the same record in word triples
+                MedRec<dsf> rd;
+                make_rec(rd, th, vscale * bx, vscale * by);
+                ds_table[id] = rd;
+            }
         }
         midx[g] = id;
     }
@@ -383,12 +413,44 @@ cudaError_t launch_medium(qla_ctx *c) {
     if (c->prec == QLA_FP64)
         k_medium<double><<<grid_for(N), AUX_THREADS, 0, c->stream>>>(
             c->n, c->nx, c->ny, c->pitch, c->delta, vscale, c->keys, c->counter, c->midx,
-            static_cast<MedRec<double> *>(c->table));
+            static_cast<MedRec<double> *>(c->table), static_cast<MedRec<dsf> *>(c->dstable));
     else
         k_medium<float><<<grid_for(N), AUX_THREADS, 0, c->stream>>>(
             c->n, c->nx, c->ny, c->pitch, c->delta, vscale, c->keys, c->counter, c->midx,
-            static_cast<MedRec<float> *>(c->table));
+            static_cast<MedRec<float> *>(c->table), nullptr);
     c->launches++;
+    return cudaGetLastError();
+}
+
+// QLA_DOUBLE_SINGLE: the state buffer between FP64 and word pairs, in place
+// (each 8-byte element is read and rewritten by one thread).
+__global__ void k_to_ds(double *__restrict__ q, size_t n) {
+    for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < n;
+         t += size_t(gridDim.x) * blockDim.x) {
+        const double v = q[t];
+        const float hi = __double2float_rn(v);
+        const float lo = __double2float_rn(v - double(hi));
+        reinterpret_cast<float2 *>(q)[t] = make_float2(hi, lo);
+    }
+}
+
+__global__ void k_from_ds(double *__restrict__ q, size_t n) {
+    for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < n;
+         t += size_t(gridDim.x) * blockDim.x) {
+        const float2 w = reinterpret_cast<const float2 *>(q)[t];
+        q[t] = double(w.x) + double(w.y);
+    }
+}
+
+cudaError_t launch_state_to_ds(qla_ctx *c, void *state) {
+    const size_t n = size_t(c->P) * c->plane_elems;
+    k_to_ds<<<grid_for(n), AUX_THREADS, 0, c->stream>>>(static_cast<double *>(state), n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_from_ds(qla_ctx *c, void *state) {
+    const size_t n = size_t(c->P) * c->plane_elems;
+    k_from_ds<<<grid_for(n), AUX_THREADS, 0, c->stream>>>(static_cast<double *>(state), n);
     return cudaGetLastError();
 }
 

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <type_traits>
 
 #include "../../include/qla.h"
 
@@ -68,6 +69,25 @@ template <typename T> struct Coef;
 template <> struct Coef<double> { using C = double2; using V = double4_16a; };
 template <> struct Coef<float>  { using C = float4;  using V = float4; };
 
+// Double-single amplitude: the unevaluated sum hi + lo of two FP32 words,
+// |lo| <= ulp(hi) / 2 (Dekker's representation).  Stored as a float2 in the
+// 8 bytes an FP64 amplitude occupies.
+struct dsf {
+    float hi, lo;
+    dsf() = default;
+    __host__ __device__ constexpr dsf(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ constexpr dsf(int v) : hi(float(v)), lo(0.0f) {}
+};
+// A cosine and a sine as three FP32 words each, whose sums are the FP64
+// values exactly (24 + 24 + 24 bits cover the 53 of a double).
+struct alignas(16) DSCoef {
+    float c0, s0, c1, s1, c2, s2, pad0, pad1;
+};
+struct DSCoefV {
+    DSCoef x, y;    // V_x and V_y: cos and sin of the potential angles
+};
+template <> struct Coef<dsf> { using C = DSCoef; using V = DSCoefV; };
+
 // Per-site medium record: collision and potential coefficients together.
 // Sites whose four neighbours have the same n as the site itself (the bulk
 // of any piecewise-uniform medium) share one record per distinct n; every
@@ -108,6 +128,39 @@ __device__ __forceinline__ void rotate(float &a, float &b, float4 k, float g) {
     const float sh = g * k.y, sl = g * k.w;
     const float na = fmaf(k.x, a, fmaf(-sh, b, fmaf(k.z, a, -sl * b)));
     const float nb = fmaf(k.x, b, fmaf(sh, a, fmaf(k.z, b, sl * a)));
+    a = na;
+    b = nb;
+}
+
+// Double-single rotation row: c x + gs y with c, s in three words and
+// gs = +-1 folded into the sine.  The two leading products are exact
+// (p + pe = c0 x.hi and q + qe = s0 y.hi by FMA); their sum is split
+// exactly (Knuth's two-sum); every smaller term is accumulated in FP32 at
+// the low word's scale, and the result renormalised (fast two-sum).  Error
+// ~2^-48 of the inputs' magnitude, unbiased.
+__device__ __forceinline__ dsf ds_row(const DSCoef &k, dsf x, float gs, dsf y) {
+    const float s0 = gs * k.s0, s1 = gs * k.s1, s2 = gs * k.s2;
+    const float p = k.c0 * x.hi, pe = fmaf(k.c0, x.hi, -p);
+    const float q = s0 * y.hi, qe = fmaf(s0, y.hi, -q);
+    const float h = p + q, hb = h - p;
+    const float e = (p - (h - hb)) + (q - hb);
+    float t = e + (pe + qe);
+    t = fmaf(k.c0, x.lo, t);
+    t = fmaf(k.c1, x.hi, t);
+    t = fmaf(k.c1, x.lo, t);
+    t = fmaf(k.c2, x.hi, t);
+    t = fmaf(s0, y.lo, t);
+    t = fmaf(s1, y.hi, t);
+    t = fmaf(s1, y.lo, t);
+    t = fmaf(s2, y.hi, t);
+    const float r = h + t;
+    return dsf(r, t - (r - h));
+}
+
+// (a, b) <- [[c, -g s], [g s, c]] (a, b) in double-single arithmetic.
+__device__ __forceinline__ void rotate(dsf &a, dsf &b, const DSCoef &k, dsf g) {
+    const dsf na = ds_row(k, a, -g.hi, b);
+    const dsf nb = ds_row(k, b, g.hi, a);
     a = na;
     b = nb;
 }
@@ -176,7 +229,13 @@ __device__ __forceinline__ void lcu_y(T (&v)[6], T c1, T s1, T c3, T s3) {
 // six amplitudes (entries absent in E_z mode are ignored).  kv = CoefV.
 template <typename T, int P, int VM, typename KV>
 __device__ __forceinline__ void apply_potential(T (&q)[6], KV kv) {
-    if constexpr (VM == V_ROTATION) {
+    if constexpr (VM == V_ROTATION && std::is_same<T, dsf>::value) {
+        // double-single: the same rotations with three-word cos and sin
+        rotate(q[2], q[4], kv.x, T(-1));
+        if constexpr (P == 6) rotate(q[1], q[5], kv.x, T(1));
+        rotate(q[2], q[3], kv.y, T(1));
+        if constexpr (P == 6) rotate(q[0], q[5], kv.y, T(-1));
+    } else if constexpr (VM == V_ROTATION) {
         // V_x: (q2,q4) by [[c, s], [-s, c]]; (q1,q5) by [[c, -s], [s, c]]
         rotate1(q[2], q[4], kv.x, kv.y, T(-1));
         if constexpr (P == 6) rotate1(q[1], q[5], kv.x, kv.y, T(1));
@@ -289,6 +348,8 @@ struct qla_ctx {
     bool tensor = false;
     double *n_x = nullptr, *n_y = nullptr;
     void *ttable = nullptr;
+    // QLA_DOUBLE_SINGLE contexts: MedRec<dsf> records, indexed like table
+    void *dstable = nullptr;
     double *staging = nullptr;      // ny * nx
     double *partials = nullptr;     // energy partial sums
     double *result = nullptr;       // final energy (device)
@@ -310,6 +371,7 @@ namespace qla {
 struct Layout {
     size_t state[2], midx, table, keys, counter, n, staging, partials, result, total;
     size_t n_x, n_y, ttable;  // QLA_ANISOTROPIC only (else 0)
+    size_t dstable;           // QLA_DOUBLE_SINGLE only (else 0)
     size_t plane_elems;
     int pitch, energy_blocks;
 };
@@ -332,6 +394,14 @@ cudaError_t raw_energy(int prec, const void *state, size_t plane_elems, int nx, 
                        int pitch, double *partials, int nblocks, double *result, cudaStream_t st);
 cudaError_t launch_medium_tensor(qla_ctx *c);
 cudaError_t launch_step_tensor(qla_ctx *c, const void *in, void *out);
+// QLA_DOUBLE_SINGLE: the marching step on word-pair state with the
+// double-single records, and the in-place conversions of the state buffer
+// between FP64 and word pairs.
+cudaError_t launch_step_march_ds(qla_ctx *c, const void *in, void *out, bool vin);
+cudaError_t launch_state_to_ds(qla_ctx *c, void *state);
+cudaError_t launch_state_from_ds(qla_ctx *c, void *state);
+// Lattices the double-single step takes (those of the FP64 marching kernel).
+bool ds_shape_ok(int nx, int ny);
 cudaError_t launch_packet(qla_ctx *c, const qla_packet &p);
 cudaError_t launch_from_f64(qla_ctx *c, int plane, const double *src);
 cudaError_t launch_to_f64(qla_ctx *c, int comp, double *dst);

@@ -17,20 +17,23 @@ template <typename T, int LX> struct Vec;
 template <> struct Vec<float, 4> { using type = float4; };
 template <> struct Vec<float, 2> { using type = float2; };
 template <> struct Vec<double, 2> { using type = double2; };
+template <> struct Vec<dsf, 2> { using type = float4; };   // two (hi, lo) pairs
 
 // Streamed data (state planes, index rows) is read through L2 only, so that
 // L1 keeps the medium records, which every row looks up.
 template <typename T, int LX>
 __device__ __forceinline__ void vload(const T *p, T (&v)[LX]) {
     const auto t = __ldcg(reinterpret_cast<const typename Vec<T, LX>::type *>(p));
-    if constexpr (LX == 4) { v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+    if constexpr (std::is_same<T, dsf>::value) { v[0] = dsf(t.x, t.y); v[1] = dsf(t.z, t.w); }
+    else if constexpr (LX == 4) { v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
     else { v[0] = t.x; v[1] = t.y; }
 }
 
 template <typename T, int LX>
 __device__ __forceinline__ void vstore(T *p, const T (&v)[LX]) {
     typename Vec<T, LX>::type t;
-    if constexpr (LX == 4) { t.x = v[0]; t.y = v[1]; t.z = v[2]; t.w = v[3]; }
+    if constexpr (std::is_same<T, dsf>::value) { t = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo); }
+    else if constexpr (LX == 4) { t.x = v[0]; t.y = v[1]; t.z = v[2]; t.w = v[3]; }
     else { t.x = v[0]; t.y = v[1]; }
     *reinterpret_cast<typename Vec<T, LX>::type *>(p) = t;
 }
@@ -39,6 +42,8 @@ __device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xfff
 __device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 __device__ __forceinline__ double shfl_up1(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 __device__ __forceinline__ double shfl_dn1(double v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ dsf shfl_up1(dsf v) { return dsf(shfl_up1(v.hi), shfl_up1(v.lo)); }
+__device__ __forceinline__ dsf shfl_dn1(dsf v) { return dsf(shfl_dn1(v.hi), shfl_dn1(v.lo)); }
 
 // Rotate the bond (unmoved u, moved m) of a pair whose first component (the
 // row holding cos, -g sin) is the moved one iff a_moved.

@@ -96,7 +96,7 @@ inline int pick_segment(int ny, int n_wx, long long resident_warps) {
 }
 
 template <typename T, int P, int LX, int VM, bool VIN>
-cudaError_t launch_t(qla_ctx *c, const void *in, void *out) {
+cudaError_t launch_t(qla_ctx *c, const void *in, void *out, const void *table) {
     constexpr int WOUT = 32 * LX - 8;
     auto kern = k_step_march<T, P, LX, VM, VIN>;
     const size_t smem = sizeof(typename March<T, P, LX, VM, VIN>::Slot) * NSLOT * WARPS;
@@ -121,7 +121,7 @@ cudaError_t launch_t(qla_ctx *c, const void *in, void *out) {
     const int blocks = (n_items + WARPS - 1) / WARPS;
     kern<<<blocks, 32 * WARPS, smem, c->stream>>>(
         static_cast<const T *>(in), static_cast<T *>(out), c->midx,
-        static_cast<const MedRec<T> *>(c->table), c->nx, c->ny, c->pitch, c->plane_elems, seg,
+        static_cast<const MedRec<T> *>(table), c->nx, c->ny, c->pitch, c->plane_elems, seg,
         n_wx, n_items);
     return cudaGetLastError();
 }
@@ -130,15 +130,27 @@ cudaError_t launch_t(qla_ctx *c, const void *in, void *out) {
 // when one is pending (see qla_ctx::pending_v).
 template <typename T, int P, int LX>
 cudaError_t launch_vm(qla_ctx *c, const void *in, void *out, bool vin) {
+    const void *tb = c->table;
     switch (c->vmode) {
     case V_ROTATION:
-        return vin ? launch_t<T, P, LX, V_ROTATION, true>(c, in, out)
-                   : launch_t<T, P, LX, V_ROTATION, false>(c, in, out);
+        return vin ? launch_t<T, P, LX, V_ROTATION, true>(c, in, out, tb)
+                   : launch_t<T, P, LX, V_ROTATION, false>(c, in, out, tb);
     case V_LITERAL:
-        return vin ? launch_t<T, P, LX, V_LITERAL, true>(c, in, out)
-                   : launch_t<T, P, LX, V_LITERAL, false>(c, in, out);
-    default: return launch_t<T, P, LX, V_NONE, false>(c, in, out);
+        return vin ? launch_t<T, P, LX, V_LITERAL, true>(c, in, out, tb)
+                   : launch_t<T, P, LX, V_LITERAL, false>(c, in, out, tb);
+    default: return launch_t<T, P, LX, V_NONE, false>(c, in, out, tb);
     }
+}
+
+// Double-single steps: word-pair state, MedRec<dsf> records; the rotation
+// or no-potential reading (the flag excludes the others).
+template <int P>
+cudaError_t launch_ds(qla_ctx *c, const void *in, void *out, bool vin) {
+    const void *tb = c->dstable;
+    if (c->vmode == V_ROTATION)
+        return vin ? launch_t<dsf, P, 2, V_ROTATION, true>(c, in, out, tb)
+                   : launch_t<dsf, P, 2, V_ROTATION, false>(c, in, out, tb);
+    return launch_t<dsf, P, 2, V_NONE, false>(c, in, out, tb);
 }
 
 }  // namespace
@@ -156,6 +168,15 @@ bool march_supported(const qla_ctx *c) {
     return c->nx % lx == 0 && c->nx >= 32 * lx && c->ny >= 8 &&
            c->plane_elems < (size_t(1) << 31) && !(c->tensor && c->P == 6) &&
            c->vmode != V_LCU;
+}
+
+bool ds_shape_ok(int nx, int ny) {
+    return nx % 2 == 0 && nx >= 64 && ny >= 8 &&
+           size_t(ny) * ((size_t(nx) + 31) / 32 * 32) < (size_t(1) << 31);
+}
+
+cudaError_t launch_step_march_ds(qla_ctx *c, const void *in, void *out, bool vin) {
+    return c->P == 6 ? launch_ds<6>(c, in, out, vin) : launch_ds<3>(c, in, out, vin);
 }
 
 cudaError_t launch_step_march(qla_ctx *c, const void *in, void *out, bool vin) {

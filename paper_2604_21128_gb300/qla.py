@@ -24,6 +24,7 @@ QLA_POTENTIAL_LITERAL = 2
 QLA_POTENTIAL_NONE = 4
 QLA_ANISOTROPIC = 8
 QLA_POTENTIAL_LCU = 16
+QLA_DOUBLE_SINGLE = 32
 QLA_KERNEL_AUTO, QLA_KERNEL_TILE, QLA_KERNEL_MARCH = 0, 1, 2
 
 STATUS = {0: "QLA_OK", 1: "QLA_EINVAL", 2: "QLA_ESTATE", 3: "QLA_ENOMEM",
@@ -281,19 +282,23 @@ class Grid:
 
     precision: "fp64" or "fp32"; te_only: evolve only q2, q3, q4;
     potential: "rotation" (default reading), "literal", "none" or "lcu";
-    tensor: a diagonal index tensor (set_medium with a (3, ny, nx) array).
+    tensor: a diagonal index tensor (set_medium with a (3, ny, nx) array);
+    double_single: FP64 contexts step in double-single arithmetic on the FP32
+    pipes (QLA_DOUBLE_SINGLE).
     The device workspace is a torch uint8 tensor; work is enqueued on
     ``stream`` (default: torch's current stream on the device)."""
 
     def __init__(self, nx, ny, delta=1.0, precision="fp64", te_only=False,
-                 potential="rotation", device=None, stream=None, tensor=False):
+                 potential="rotation", device=None, stream=None, tensor=False,
+                 double_single=False):
         import torch
         load()
         if not torch.cuda.is_available():
             raise RuntimeError("libqla needs a CUDA device; none is available")
         self.nx, self.ny, self.delta = int(nx), int(ny), float(delta)
         self.precision = {"fp64": QLA_FP64, "fp32": QLA_FP32}[precision]
-        flags = (QLA_TE_ONLY if te_only else 0) | (QLA_ANISOTROPIC if tensor else 0) | {
+        flags = (QLA_TE_ONLY if te_only else 0) | (QLA_ANISOTROPIC if tensor else 0) | \
+            (QLA_DOUBLE_SINGLE if double_single else 0) | {
             "rotation": 0, "literal": QLA_POTENTIAL_LITERAL, "none": QLA_POTENTIAL_NONE,
             "lcu": QLA_POTENTIAL_LCU}[potential]
         self.flags = flags

@@ -36,7 +36,7 @@ def lib():
     return qla.load()
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_boundary_calls():
     names = declared_functions()
     for required in ("qla_init_grid", "qla_set_medium", "qla_set_packet", "qla_step",
                      "qla_energy", "qla_fields"):
@@ -63,6 +63,18 @@ def test_workspace_bytes_host_only(lib):
     # the state ping-pong buffers dominate at scale: 8192^2 FP32 E_z mode
     big = qla.qla_workspace_bytes(8192, 8192, qla.QLA_FP32, qla.QLA_TE_ONLY)
     assert 2 * 3 * 8192 * 8192 * 4 < big < 10 * 8192 * 8192 * 8
+
+
+def test_double_single_workspace_host_only(lib):
+    ds = qla.QLA_DOUBLE_SINGLE
+    plain = qla.qla_workspace_bytes(256, 64, qla.QLA_FP64, qla.QLA_TE_ONLY)
+    with_ds = qla.qla_workspace_bytes(256, 64, qla.QLA_FP64, qla.QLA_TE_ONLY | ds)
+    assert with_ds > plain   # plus one 96-byte double-single record per site
+    for nx, ny, prec, flags in [(256, 64, qla.QLA_FP32, ds), (32, 64, qla.QLA_FP64, ds),
+                                (65, 64, qla.QLA_FP64, ds), (256, 4, qla.QLA_FP64, ds),
+                                (256, 64, qla.QLA_FP64, ds | qla.QLA_POTENTIAL_LITERAL),
+                                (256, 64, qla.QLA_FP64, ds | qla.QLA_ANISOTROPIC)]:
+        assert qla.qla_workspace_bytes(nx, ny, prec, flags) == 0, (nx, ny, prec, flags)
 
 
 @pytest.mark.parametrize("args", [

@@ -1,0 +1,91 @@
+"""QLA_DOUBLE_SINGLE: FP64 contexts stepped in double-single arithmetic,
+against the oracle (the FP64 bar, 1e-12 relative L2) and against the native
+FP64 kernels (rounding-level differences only)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_21128_gb300 import build as qbuild
+from paper_2604_21128_gb300 import inputs, qla
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    qbuild.build()
+    oracle.set_threads(os.cpu_count() or 1)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def run(n, delta, steps, q0=None, packet=None, te=False, potential="rotation", ds=True,
+        calls=1):
+    ny, nx = n.shape
+    with qla.Grid(nx, ny, delta, "fp64", te_only=te, potential=potential,
+                  double_single=ds) as g:
+        g.set_medium(n)
+        if q0 is not None:
+            g.set_state(q0)
+        else:
+            g.set_packet(**packet)
+        for _ in range(calls):
+            g.step(steps // calls)
+        return g.get_state(), g.energy()
+
+
+@pytest.mark.parametrize("te", [True, False])
+def test_ellipse_256_400_steps(te):
+    w = inputs.ellipse_256()
+    n = w.medium()
+    pk = w.packet.as_dict()
+    want = oracle.run(oracle.packet(n, w.delta, **pk), n, w.delta, w.steps)
+    got, e = run(n, w.delta, w.steps, packet=pk, te=te)
+    err = rel_l2(got, want)
+    print("double-single 400 steps (te=%s): rel L2 %.3e" % (te, err))
+    assert err <= 1e-12
+    assert abs(e / oracle.energy(want) - 1) <= 1e-12
+
+
+@pytest.mark.parametrize("te", [True, False])
+@pytest.mark.parametrize("potential", ["rotation", "none"])
+@pytest.mark.parametrize("shape", [(64, 8), (66, 9), (128, 37), (250, 64), (96, 130)])
+def test_random_state_against_oracle_and_native(shape, potential, te):
+    nx, ny = shape
+    n = inputs.random_medium(nx, ny, seed=nx * 17 + ny, lo=1.0, hi=3.5)
+    q0 = inputs.random_state(nx, ny, seed=nx + 5 * ny)
+    if te:
+        q0[[0, 1, 5]] = 0.0
+    want = oracle.run(q0, n, 0.8, 9, potential)
+    got, _ = run(n, 0.8, 9, q0=q0, te=te, potential=potential)
+    native, _ = run(n, 0.8, 9, q0=q0, te=te, potential=potential, ds=False)
+    assert rel_l2(got, want) <= 1e-12, rel_l2(got, want)
+    assert rel_l2(got, native) <= 1e-13, rel_l2(got, native)
+
+
+def test_split_calls_agree_with_one_call():
+    # each call converts the state to word pairs and back
+    w = inputs.scaled(inputs.ellipse_256(), 128, 128, 60)
+    n = w.medium()
+    pk = w.packet.as_dict()
+    want = oracle.run(oracle.packet(n, w.delta, **pk), n, w.delta, 60)
+    one, _ = run(n, w.delta, 60, packet=pk, te=True)
+    many, _ = run(n, w.delta, 60, packet=pk, te=True, calls=6)
+    assert rel_l2(one, want) <= 1e-12
+    assert rel_l2(many, want) <= 1e-12
+    assert rel_l2(many, one) <= 1e-13
+
+
+@pytest.mark.parametrize("kw", [dict(precision="fp32"), dict(potential="literal"),
+                                dict(potential="lcu"), dict(tensor=True),
+                                dict(nx=32), dict(nx=65), dict(ny=4)])
+def test_rejected_configurations(kw):
+    args = dict(nx=64, ny=16, precision="fp64", potential="rotation", tensor=False)
+    args.update(kw)
+    with pytest.raises(qla.QLAError):
+        qla.Grid(args["nx"], args["ny"], 1.0, args["precision"], potential=args["potential"],
+                 tensor=args["tensor"], double_single=True)
