@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--qla-steps", type=int, default=100)
     ap.add_argument("--lane-cols", type=int, default=0, help="marching kernel tuning")
     ap.add_argument("--rows", type=int, default=0, help="marching kernel tuning")
+    ap.add_argument("--double-single", action="store_true",
+                    help="FP64 contexts stepped in double-single arithmetic (QLA_DOUBLE_SINGLE)")
     ap.add_argument("--six-planes", action="store_true",
                     help="evolve all six amplitudes instead of the E_z triple")
     ap.add_argument("--surr-windows", type=int, default=20000)
@@ -87,28 +89,38 @@ def alu_ops_per_su(P, elt):
     return pairs * (16 * 4 + 2 * 4)
 
 
+def ds_ops_per_su(P):
+    """Double-single: a rotation is two rows of 23 FP32 instructions (two
+    exact products, a two-sum, nine correction FMAs, a fast two-sum); the
+    potential rotations take the same form."""
+    pairs = 1 if P == 3 else 2
+    return pairs * (16 + 2) * 46
+
+
 def alu_ops_per_su_3d(elt):
     """3D: per axis 8 layers x 2 pairs of collision rotations, then six
     potential rotations (two per axis)."""
     return 3 * 16 * (8 if elt == 4 else 4) + 6 * (6 if elt == 4 else 4)
 
 
-def roofline(P, elt, su_per_s, traffic, ops=None, **extra):
+def roofline(P, elt, su_per_s, traffic, ops=None, pipe=None, **extra):
     """Roofline object for a step kernel that advances ``su_per_s`` site-updates
     per second of its own run time.  The bound is the roof with the lower
     ceiling in site-updates/s (HBM for FP32, the FP64 pipe for FP64); the
-    other roof's figures ride along under its name."""
+    other roof's figures ride along under its name.  pipe overrides the
+    arithmetic pipe ("fp32" for double-single steps on FP64 state)."""
     ops = alu_ops_per_su(P, elt) if ops is None else ops
-    peak_ops = FP32_INST_PEAK if elt == 4 else FP64_INST_PEAK
+    pipe = pipe or ("fp32" if elt == 4 else "fp64")
+    peak_ops = FP32_INST_PEAK if pipe == "fp32" else FP64_INST_PEAK
     hbm_peak, hbm_kind = peaks()
     bytes_su = 2 * P * elt
     hbm = {"achieved": bytes_su * su_per_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
            "frac": bytes_su * su_per_s / 1e9 / hbm_peak, "peak_kind": hbm_kind,
            "bytes_per_site_update": bytes_su}
     alu = {"achieved": ops * su_per_s / 1e12, "peak": peak_ops / 1e12,
-           "unit": "T%s-inst/s" % ("FP32" if elt == 4 else "FP64"),
+           "unit": "T%s-inst/s" % pipe.upper(),
            "frac": ops * su_per_s / peak_ops,
-           "peak_kind": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2.07 GHz" if elt == 4
+           "peak_kind": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2.07 GHz" if pipe == "fp32"
                                          else "nominal 1.25 TFLOP/s FP64 / 2 flops per FMA"),
            "ops_per_site_update": ops}
     ceil = {"hbm": hbm_peak * 1e9 / bytes_su, "alu": peak_ops / ops}
@@ -262,6 +274,7 @@ def reference_arm(args):
             "data": "synthetic",
             # the GPU arm's workload label, so the two lines pair up
             "config": {"workload": w.name + ("_fp32" if args.precision == "fp32" else "_fp64")
+                       + ("_ds" if args.double_single and args.precision == "fp64" else "")
                        + ("_6planes" if args.six_planes else "_ez"),
                        "nx": w.nx, "ny": w.ny, "delta": w.delta, "sample": sample},
             "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": threads,
@@ -320,7 +333,9 @@ def gpu_arm(args):
     sites = w.nx * w.ny
 
     stream = torch.cuda.Stream(dev)
-    g = qla.Grid(w.nx, w.ny, w.delta, args.precision, te_only=te, stream=stream)
+    ds = bool(args.double_single and args.precision == "fp64")
+    g = qla.Grid(w.nx, w.ny, w.delta, args.precision, te_only=te, stream=stream,
+                 double_single=ds)
     g.set_march_tuning(args.lane_cols, args.rows)
     g.set_medium(n_host)
     g.set_packet(**pk)
@@ -368,7 +383,9 @@ def gpu_arm(args):
     k_used = S * args.steps / max(step_launches, 1)
     per_launch_s = step_time / max(step_launches, 1)
     kernel_su_per_s = sites * k_used / per_launch_s
-    traffic = kernel_traffic(int(round(k_used)), sites)
+    # the committed DRAM record is of the FP32 E_z step kernel
+    traffic = (kernel_traffic(int(round(k_used)), sites)
+               if args.precision == "fp32" and te else None)
     g.close()
 
     e2e = None
@@ -402,9 +419,10 @@ def gpu_arm(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "dtype": "f32" if args.precision == "fp32" else ("f32x2" if ds else "f64"),
+            "data": "synthetic",
             "config": {"workload": w.name + ("_fp32" if elt == 4 else "_fp64")
-                       + ("_ez" if te else "_6planes"),
+                       + ("_ds" if ds else "") + ("_ez" if te else "_6planes"),
                        "nx": w.nx, "ny": w.ny, "delta": w.delta,
                        "qla_steps_per_bench_step": S, "planes": P,
                        "potential": "rotation", "time_block": k_used,
@@ -412,7 +430,12 @@ def gpu_arm(args):
                        "energy_drift": drift,
                        "l2": "state %.0f MB > 129 MB L2, no flush" % (2 * P * elt * sites / 2e6)},
             "roofline": roofline(P, elt, kernel_su_per_s, traffic,
-                                 kernel_ms=1e3 * per_launch_s),
+                                 ops=ds_ops_per_su(P) if ds else None,
+                                 pipe="fp32" if ds else None,
+                                 kernel_ms=1e3 * per_launch_s,
+                                 **({"note": "double-single steps on FP64 state: FP32-pipe "
+                                             "instructions; two in-place conversions per "
+                                             "%d-step call included" % S} if ds else {})),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -433,7 +456,8 @@ def e2e_run(args, w, te, n_host, pk, world, dev):
     from paper_2604_21128_gb300 import qla
     stream = torch.cuda.Stream(dev)
     ez = torch.empty((w.ny, w.nx), dtype=torch.float64).pin_memory()
-    g = qla.Grid(w.nx, w.ny, w.delta, args.precision, te_only=te, stream=stream)
+    g = qla.Grid(w.nx, w.ny, w.delta, args.precision, te_only=te, stream=stream,
+                 double_single=bool(args.double_single and args.precision == "fp64"))
     g.set_march_tuning(args.lane_cols, args.rows)
     S = args.qla_steps
     barrier(world)

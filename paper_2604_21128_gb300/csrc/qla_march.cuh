@@ -235,6 +235,13 @@ struct March {
     T carry[4][2][2][LX];   // [neighbour layer][pair][value][x]
     CC kring[LAG][LX];      // collision coefficients of the rows in flight
     CV vnext[LX];           // row J+1's potential coefficients
+    // FP64 looks row J+1's records up early (their latency hides behind the
+    // row's arithmetic) and copies them into the ring at the next row; FP32
+    // and double-single load them straight into the ring slot that frees at
+    // the end of the row, which saves the copies (measured: FP32 faster,
+    // FP64 slower the other way round)
+    static constexpr bool EARLY = std::is_same<T, double>::value;
+    CC knext[EARLY ? LX : 1];
     // row offsets: next row to stage, the two output rows
     uint32_t o_in, o_now, o_out;
 
@@ -261,14 +268,15 @@ struct March {
 #pragma unroll
         for (int x = 0; x < LX; ++x) {
             const MedRec<T> *r = table + ring[S].idx[lc + x];
-            kring[K][x] = r->c;
+            if constexpr (EARLY) knext[x] = r->c;
+            else kring[K][x] = r->c;
             if constexpr (VIN) vnext[x] = r->v;
         }
     }
 
     // One march iteration for input row J; PH = (J - J0) mod 4 picks the
     // register ring slots and the staging slot of row J.  On entry kring[PH]
-    // and vnext hold row J's records.  Rows J and J - 4 are stored when they
+    // (FP64: knext) and vnext hold row J's records.  Rows J and J - 4 are stored when they
     // fall in [st_lo, st_lo + st_n).
     template <int PH>
     __device__ __forceinline__ void iter(int J, int st_lo, unsigned st_n) {
@@ -285,6 +293,10 @@ struct March {
                 for (int x = 0; x < LX; ++x) q[c][x] = ring[PH].q[p][lc + x];
             }
         }
+        if constexpr (EARLY) {
+#pragma unroll
+            for (int x = 0; x < LX; ++x) kring[S0][x] = knext[x];
+        }
         // the previous step's V_x, V_y on the entering row
         if constexpr (VIN) {
 #pragma unroll
@@ -298,6 +310,9 @@ struct March {
                     if (plane_of<P>(c) >= 0) q[c][x] = s[c];
             }
         }
+        // (FP64) row J + 1's records fly while this row computes
+        if constexpr (EARLY) lookup_next<(PH + 1) & (NSLOT - 1), S3>();
+
         apply_ux<T, P, LX>(q, kring[S0]);                          // U_x, row J
 
         // planes U_y does not touch are final for row J now
@@ -320,7 +335,7 @@ struct March {
         uy_neighbour<T, P, LX, 7>(q, carry[3], kring[S3]);         // L8 -> row J-4
         // row J - 3's coefficients (slot S3) are dead: row J + 1's records
         // go straight into that slot
-        lookup_next<(PH + 1) & (NSLOT - 1), S3>();
+        if constexpr (!EARLY) lookup_next<(PH + 1) & (NSLOT - 1), S3>();
 
         // the U_y planes of row J - 4 are final
         if (unsigned(J - LAG - st_lo) < st_n) {
