@@ -675,7 +675,8 @@ def cube_arm(args):
     S = max(1, args.qla_steps // 5)
     sites = N ** 3
     stream = torch.cuda.Stream()
-    g = qla.Grid3(N, N, N, d, args.precision, stream=stream)
+    ds = bool(args.double_single and args.precision == "fp64")
+    g = qla.Grid3(N, N, N, d, args.precision, stream=stream, double_single=ds)
     t_e2e = time.perf_counter()
     g.set_medium(n3)
     g.set_state(q)
@@ -732,16 +733,21 @@ def cube_arm(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if elt == 4 else "f64", "data": "synthetic",
-            "config": {"workload": "cube_256_%s_3d" % args.precision, "n": N, "delta": d,
+            "dtype": "f32" if elt == 4 else ("f32x2" if ds else "f64"), "data": "synthetic",
+            "config": {"workload": "cube_256_%s%s_3d" % (args.precision, "_ds" if ds else ""),
+                       "n": N, "delta": d,
                        "qla_steps_per_bench_step": S, "planes": 6,
-                       "launches_per_qla_step": 2 if elt == 4 else 3, "energy_drift": e / e0 - 1,
+                       "launches_per_qla_step": 2 if elt == 4 or ds else 3,
+                       "energy_drift": e / e0 - 1,
                        "l2": "state %.0f MB > 129 MB L2, no flush" % (12 * elt * sites / 1e6)},
             "roofline": roofline(6, elt, kernel_su,
                                  kernel_traffic(1, sites, "traffic_cube256.json") if elt == 4
-                                 else None, ops=alu_ops_per_su_3d(elt),
+                                 else None,
+                                 ops=(3 * 16 * 2 + 6) * 46 if ds else alu_ops_per_su_3d(elt),
+                                 pipe="fp32" if ds else None,
                                  kernel_ms_per_qla_step=1e3 * step_time / (args.steps * S),
-                                 note="automatic step kernel: FP32 slices + column pipeline (2 launches), FP64 per-axis passes (3)"),
+                                 note="double-single slices + column pipeline on FP64 state (2 launches; two in-place conversions per call)" if ds else
+                                 "automatic step kernel: FP32 slices + column pipeline (2 launches), FP64 per-axis passes (3)"),
             "cpu_baseline": cpu,
             "e2e": {"value": total_steps * sites / t_e2e, "unit": "site-updates/s",
                     "h2d_bytes_per_step": (q.nbytes + n3.nbytes) / (args.steps + args.warmup),

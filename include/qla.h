@@ -419,8 +419,12 @@ qla_status surr_weight_grad_raw(const void *dz_bf16, const void *in_bf16, int B,
  * All six planes evolve (the E_z triple does not decouple in 3D).
  * Lattice nx x ny x nz, periodic, site (i, j, k) at host index
  * (k * ny + j) * nx + i; ny, nz <= 65535.  Flags: 0 (rotation reading) or
- * QLA_POTENTIAL_NONE; others give QLA_EINVAL.  Same status conventions and
- * stream semantics as the 2D context.
+ * QLA_POTENTIAL_NONE, optionally with QLA_DOUBLE_SINGLE (FP64 contexts
+ * whose nx is even and >= 64 and ny >= 8: qla3_step converts the state in
+ * place, runs the slices and column kernels in double-single arithmetic
+ * whatever qla3_set_step_kernel chose, and converts back); others give
+ * QLA_EINVAL.  Same status conventions and stream semantics as the 2D
+ * context.
  * ------------------------------------------------------------------------ */
 typedef struct qla3_ctx qla3_ctx;
 

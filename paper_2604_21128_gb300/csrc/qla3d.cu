@@ -45,6 +45,9 @@ template <int L> __host__ __device__ constexpr int layer_sign_z() {
 // Potential coefficients of one site for x, y, z, in the CoefV convention
 // (FP64 (cos, sin), FP32 (gamma = 1 - cos, sin)).
 template <typename T> struct V3 { T gx, sx, gy, sy, gz, sz; };
+// Double-single (QLA_DOUBLE_SINGLE): cos and sin of each axis's angle as
+// three FP32 words (their sums are the FP64 values).
+template <> struct V3<dsf> { DSCoef x, y, z; };
 
 __device__ __forceinline__ void coef_c(double th, double2 &k) {
     double s, c;
@@ -60,6 +63,19 @@ __device__ __forceinline__ void coef_c(double th, float4 &k) {
     sincos(th, &s, &c);
     split2(c, k.x, k.z);
     split2(s, k.y, k.w);
+}
+__device__ __forceinline__ void split3(double v, float &a, float &b, float &c) {
+    a = __double2float_rn(v);
+    const double r = v - double(a);
+    b = __double2float_rn(r);
+    c = __double2float_rn(r - double(b));
+}
+__device__ __forceinline__ void coef_ds(double ph, DSCoef &k) {
+    double s, c;
+    sincos(ph, &s, &c);
+    split3(c, k.c0, k.c1, k.c2);
+    split3(s, k.s0, k.s1, k.s2);
+    k.pad0 = k.pad1 = 0.0f;
 }
 __device__ __forceinline__ void coef_v(double ph, double &g, double &s) {
     g = cos(ph);
@@ -596,7 +612,16 @@ struct ZCol {
             --to_skip;
         } else if (to_store > 0) {
             --to_store;
-            if constexpr (VM == V_ROTATION) {
+            if constexpr (VM == V_ROTATION && std::is_same<T, dsf>::value) {
+                // the same rotations in double-single arithmetic
+                const V3<T> v = rv[io];
+                rotate(q[2], q[4], v.x, T(-1));
+                rotate(q[1], q[5], v.x, T(1));
+                rotate(q[2], q[3], v.y, T(1));
+                rotate(q[0], q[5], v.y, T(-1));
+                rotate(q[1], q[3], v.z, T(-1));
+                rotate(q[0], q[4], v.z, T(1));
+            } else if constexpr (VM == V_ROTATION) {
                 // V_x (Eq. 2e11, rotation reading), V_y (Eq. 2e12), V_z (Eq. 3b4)
                 const V3<T> v = rv[io];
                 rotate1(q[2], q[4], v.gx, v.sx, T(-1));
@@ -714,8 +739,8 @@ cudaError_t slices_t(const void *in, void *out, const uint32_t *idx3, const void
     if (seg < 16) seg = 16;
     nseg = (nz + seg - 1) / seg;
     // FP32 loads four planes ahead (3.5% faster than one at 256^3); FP64 is
-    // bound by its FMA pipe and loads one ahead
-    k3_zcol<T, VM, sizeof(T) == 4 ? 4 : 1><<<dim3(unsigned(cblocks), nseg), 128, 0, st>>>(
+    // bound by its FMA pipe and loads one ahead; double-single two
+    k3_zcol<T, VM, sizeof(T) == 4 ? 4 : (std::is_same<T, dsf>::value ? 2 : 1)><<<dim3(unsigned(cblocks), nseg), 128, 0, st>>>(
         static_cast<const T *>(out), static_cast<T *>(const_cast<void *>(in)), idx3,
         static_cast<const MedRec<T> *>(rec), static_cast<const V3<T> *>(rv), nx, ny, nz, pitch,
         plane_elems, seg);
@@ -736,7 +761,8 @@ template <typename T>
 __global__ void k3_dedup(const double *__restrict__ n, int nx, int ny, int nz, int pitch,
                          double delta, double vscale, unsigned long long *__restrict__ keys,
                          unsigned *__restrict__ counter, uint32_t *__restrict__ idx3,
-                         MedRec<T> *__restrict__ rec, V3<T> *__restrict__ rv) {
+                         MedRec<T> *__restrict__ rec, V3<T> *__restrict__ rv,
+                         MedRec<dsf> *__restrict__ rec_ds, V3<dsf> *__restrict__ rv_ds) {
     namespace cg = cooperative_groups;
     const size_t N = size_t(nx) * ny * nz;
     for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < N;
@@ -790,6 +816,16 @@ __global__ void k3_dedup(const double *__restrict__ n, int nx, int ny, int nz, i
             coef_v(vscale * by, v.gy, v.sy);
             coef_v(vscale * bz, v.gz, v.sz);
             rv[id] = v;
+            if (rec_ds) {   // QLA_DOUBLE_SINGLE: the same records in word triples
+                MedRec<dsf> rd{};
+                coef_ds(delta / (4.0 * nn), rd.c);
+                rec_ds[id] = rd;
+                V3<dsf> vd;
+                coef_ds(vscale * bx, vd.x);
+                coef_ds(vscale * by, vd.y);
+                coef_ds(vscale * bz, vd.z);
+                rv_ds[id] = vd;
+            }
         }
         idx3[g] = id;
     }
@@ -927,6 +963,9 @@ struct qla3_ctx {
     // kernel 2: per-site record index, records (shared where uniform)
     uint32_t *idx3 = nullptr;
     void *rec = nullptr, *rv = nullptr;
+    // QLA_DOUBLE_SINGLE: double-single records, indexed like rec and rv
+    bool ds = false;
+    void *rec_ds = nullptr, *rv_ds = nullptr;
     unsigned long long *keys = nullptr;
     unsigned *counter = nullptr;
     int eblocks = 1;
@@ -943,7 +982,7 @@ namespace {
 
 struct Layout3 {
     size_t state[2], n, staging, kc, kv, idx3, rec, rv, keys, counter, partials, result, total,
-        plane_elems;
+        plane_elems, rec_ds, rv_ds;
     int pitch, eblocks;
 };
 
@@ -954,7 +993,7 @@ bool dims_ok(int nx, int ny, int nz) {
            size_t(nx) * ny * nz <= (size_t(1) << 31);
 }
 
-Layout3 layout3(int nx, int ny, int nz, int prec) {
+Layout3 layout3(int nx, int ny, int nz, int prec, bool ds) {
     Layout3 L{};
     const size_t elt = prec == QLA_FP64 ? 8 : 4;
     L.pitch = (nx + 31) / 32 * 32;
@@ -981,6 +1020,11 @@ Layout3 layout3(int nx, int ny, int nz, int prec) {
     L.counter = off;  off += al256(4);
     L.partials = off; off += al256(nb * 8 * 6);   // six terms per block (divergence)
     L.result = off;   off += al256(8 * 6);
+    L.rec_ds = L.rv_ds = 0;
+    if (ds) {
+        L.rec_ds = off; off += al256(nrec * sizeof(MedRec<dsf>));
+        L.rv_ds = off;  off += al256(nrec * sizeof(V3<dsf>));
+    }
     L.total = off;
     return L;
 }
@@ -1055,8 +1099,12 @@ extern "C" {
 
 size_t qla3_workspace_bytes(int nx, int ny, int nz, int precision, unsigned flags) {
     if (!dims_ok(nx, ny, nz) || (precision != QLA_FP64 && precision != QLA_FP32)) return 0;
-    if (flags & ~(unsigned)QLA_POTENTIAL_NONE) return 0;
-    return layout3(nx, ny, nz, precision).total;
+    if (flags & ~(unsigned)(QLA_POTENTIAL_NONE | QLA_DOUBLE_SINGLE)) return 0;
+    const bool ds = (flags & QLA_DOUBLE_SINGLE) != 0;
+    if (ds && (precision != QLA_FP64 ||
+               !slices_ok(nx, ny, size_t(nz) * ny * size_t((nx + 31) / 32 * 32))))
+        return 0;
+    return layout3(nx, ny, nz, precision, ds).total;
 }
 
 qla_status qla3_init(qla3_ctx **out, int nx, int ny, int nz, double delta, int precision,
@@ -1079,7 +1127,8 @@ qla_status qla3_init(qla3_ctx **out, int nx, int ny, int nz, double delta, int p
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return QLA_ECUDA; }
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (c->num_sms < 1) c->num_sms = 1;
-    const Layout3 L = layout3(nx, ny, nz, precision);
+    c->ds = (flags & QLA_DOUBLE_SINGLE) != 0;
+    const Layout3 L = layout3(nx, ny, nz, precision, c->ds);
     if (workspace) {
         c->ws = static_cast<char *>(workspace);
     } else {
@@ -1099,6 +1148,10 @@ qla_status qla3_init(qla3_ctx **out, int nx, int ny, int nz, double delta, int p
     c->idx3 = reinterpret_cast<uint32_t *>(c->ws + L.idx3);
     c->rec = c->ws + L.rec;
     c->rv = c->ws + L.rv;
+    if (c->ds) {
+        c->rec_ds = c->ws + L.rec_ds;
+        c->rv_ds = c->ws + L.rv_ds;
+    }
     c->keys = reinterpret_cast<unsigned long long *>(c->ws + L.keys);
     c->counter = reinterpret_cast<unsigned *>(c->ws + L.counter);
     c->partials = reinterpret_cast<double *>(c->ws + L.partials);
@@ -1145,11 +1198,13 @@ qla_status qla3_set_medium(qla3_ctx *c, const double *n_host) {
     if (c->prec == QLA_FP64)
         k3_dedup<double><<<blocks, 256, 0, c->stream>>>(
             c->n, c->nx, c->ny, c->nz, c->pitch, c->delta, vscale, c->keys, c->counter, c->idx3,
-            static_cast<MedRec<double> *>(c->rec), static_cast<V3<double> *>(c->rv));
+            static_cast<MedRec<double> *>(c->rec), static_cast<V3<double> *>(c->rv),
+            static_cast<MedRec<dsf> *>(c->rec_ds), static_cast<V3<dsf> *>(c->rv_ds));
     else
         k3_dedup<float><<<blocks, 256, 0, c->stream>>>(
             c->n, c->nx, c->ny, c->nz, c->pitch, c->delta, vscale, c->keys, c->counter, c->idx3,
-            static_cast<MedRec<float> *>(c->rec), static_cast<V3<float> *>(c->rv));
+            static_cast<MedRec<float> *>(c->rec), static_cast<V3<float> *>(c->rv), nullptr,
+            nullptr);
     CUDA3(c, cudaGetLastError(), "qla3_set_medium: records");
     c->launches += 3;
     CUDA3(c, cudaStreamSynchronize(c->stream), "qla3_set_medium: sync");
@@ -1206,6 +1261,28 @@ qla_status qla3_step(qla3_ctx *c, long long n_steps) {
     if (n_steps == 0) return QLA_OK;
     if (!c->has_medium || !c->has_state)
         return fail3(c, QLA_ESTATE, "qla3_step: set a medium and a state first");
+    if (c->ds) {
+        // word pairs in place, n double-single steps (slices + column
+        // pipeline; the result returns to state[cur]), back to FP64
+        const size_t n = 6 * c->plane_elems;
+        CUDA3(c, raw_to_ds(c->state[c->cur], n, c->stream), "qla3_step: to double-single");
+        void *a = c->state[c->cur], *b = c->state[c->cur ^ 1];
+        for (long long k = 0; k < n_steps; ++k) {
+            const cudaError_t e =
+                c->vmode == V_ROTATION
+                    ? slices_t<dsf, V_ROTATION>(a, b, c->idx3, c->rec_ds, c->rv_ds, c->nx, c->ny,
+                                                c->nz, c->pitch, c->plane_elems, c->num_sms,
+                                                c->stream)
+                    : slices_t<dsf, V_NONE>(a, b, c->idx3, c->rec_ds, c->rv_ds, c->nx, c->ny,
+                                            c->nz, c->pitch, c->plane_elems, c->num_sms,
+                                            c->stream);
+            CUDA3(c, e, "qla3_step: kernel");
+            c->launches += 2;
+        }
+        CUDA3(c, raw_from_ds(c->state[c->cur], n, c->stream), "qla3_step: from double-single");
+        c->launches += 2;
+        return QLA_OK;
+    }
     for (long long k = 0; k < n_steps; ++k)
         CUDA3(c, c->prec == QLA_FP64 ? step3_t<double>(c) : step3_t<float>(c), "qla3_step: kernel");
     return QLA_OK;

@@ -442,16 +442,22 @@ __global__ void k_from_ds(double *__restrict__ q, size_t n) {
     }
 }
 
-cudaError_t launch_state_to_ds(qla_ctx *c, void *state) {
-    const size_t n = size_t(c->P) * c->plane_elems;
-    k_to_ds<<<grid_for(n), AUX_THREADS, 0, c->stream>>>(static_cast<double *>(state), n);
+cudaError_t raw_to_ds(void *q, size_t n, cudaStream_t st) {
+    k_to_ds<<<grid_for(n), AUX_THREADS, 0, st>>>(static_cast<double *>(q), n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_state_from_ds(qla_ctx *c, void *state) {
-    const size_t n = size_t(c->P) * c->plane_elems;
-    k_from_ds<<<grid_for(n), AUX_THREADS, 0, c->stream>>>(static_cast<double *>(state), n);
+cudaError_t raw_from_ds(void *q, size_t n, cudaStream_t st) {
+    k_from_ds<<<grid_for(n), AUX_THREADS, 0, st>>>(static_cast<double *>(q), n);
     return cudaGetLastError();
+}
+
+cudaError_t launch_state_to_ds(qla_ctx *c, void *state) {
+    return raw_to_ds(state, size_t(c->P) * c->plane_elems, c->stream);
+}
+
+cudaError_t launch_state_from_ds(qla_ctx *c, void *state) {
+    return raw_from_ds(state, size_t(c->P) * c->plane_elems, c->stream);
 }
 
 // Raw-pointer forms of the conversions and the energy for a six-plane state

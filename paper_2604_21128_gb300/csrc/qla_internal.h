@@ -402,6 +402,9 @@ cudaError_t launch_state_to_ds(qla_ctx *c, void *state);
 cudaError_t launch_state_from_ds(qla_ctx *c, void *state);
 // Lattices the double-single step takes (those of the FP64 marching kernel).
 bool ds_shape_ok(int nx, int ny);
+// n FP64 values <-> n (hi, lo) FP32 word pairs, in place.
+cudaError_t raw_to_ds(void *q, size_t n, cudaStream_t st);
+cudaError_t raw_from_ds(void *q, size_t n, cudaStream_t st);
 cudaError_t launch_packet(qla_ctx *c, const qla_packet &p);
 cudaError_t launch_from_f64(qla_ctx *c, int plane, const double *src);
 cudaError_t launch_to_f64(qla_ctx *c, int comp, double *dst);

@@ -521,17 +521,20 @@ class Grid3:
     """A three-dimensional context (qla3_* in the C ABI): nx x ny x nz
     periodic lattice, six planes, precision "fp64" or "fp32", potential
     "rotation" or "none".  Arrays are (6, nz, ny, nx) states and (nz, ny, nx)
-    media; the workspace is a torch uint8 tensor, work runs on ``stream``."""
+    media; the workspace is a torch uint8 tensor, work runs on ``stream``.
+    double_single: FP64 contexts step in double-single arithmetic
+    (QLA_DOUBLE_SINGLE; the slices and column kernels)."""
 
     def __init__(self, nx, ny, nz, delta=1.0, precision="fp64", potential="rotation",
-                 stream=None):
+                 stream=None, double_single=False):
         import torch
         lib = load()
         if not torch.cuda.is_available():
             raise RuntimeError("libqla needs a CUDA device; none is available")
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         prec = {"fp64": QLA_FP64, "fp32": QLA_FP32}[precision]
-        flags = {"rotation": 0, "none": QLA_POTENTIAL_NONE}[potential]
+        flags = {"rotation": 0, "none": QLA_POTENTIAL_NONE}[potential] | \
+            (QLA_DOUBLE_SINGLE if double_single else 0)
         nbytes = int(lib.qla3_workspace_bytes(self.nx, self.ny, self.nz, prec, flags))
         if nbytes == 0:
             raise QLAError(1, "invalid 3D lattice or flags")

@@ -89,3 +89,38 @@ def test_rejected_configurations(kw):
     with pytest.raises(qla.QLAError):
         qla.Grid(args["nx"], args["ny"], 1.0, args["precision"], potential=args["potential"],
                  tensor=args["tensor"], double_single=True)
+
+
+def medium3(nx, ny, nz, seed):
+    rng = np.random.default_rng(seed)
+    raw = rng.random((nz, ny, nx))
+    for ax in range(3):
+        raw = (raw + np.roll(raw, 1, ax) + np.roll(raw, -1, ax)) / 3
+    return 1.0 + 2.5 * raw
+
+
+@pytest.mark.parametrize("potential", ["rotation", "none"])
+@pytest.mark.parametrize("shape", [(64, 8, 3), (66, 9, 5), (128, 20, 12)])
+def test_3d_against_oracle_and_native(shape, potential):
+    nx, ny, nz = shape
+    n = medium3(nx, ny, nz, seed=nx + ny + nz)
+    q0 = np.random.default_rng(nx * ny + nz).standard_normal((6, nz, ny, nx))
+    steps = 6
+    want = oracle.run3(q0, n, 0.9, steps, potential)
+    out = {}
+    for ds in (True, False):
+        with qla.Grid3(nx, ny, nz, 0.9, "fp64", potential=potential, double_single=ds) as g:
+            g.set_medium(n)
+            g.set_state(q0)
+            g.step(steps)
+            out[ds] = g.get_state()
+    assert rel_l2(out[True], want) <= 1e-12, rel_l2(out[True], want)
+    assert rel_l2(out[True], out[False]) <= 1e-13, rel_l2(out[True], out[False])
+
+
+@pytest.mark.parametrize("kw", [dict(precision="fp32"), dict(nx=32), dict(nx=65), dict(ny=4)])
+def test_3d_rejected_configurations(kw):
+    args = dict(nx=64, ny=16, nz=4, precision="fp64")
+    args.update(kw)
+    with pytest.raises(qla.QLAError):
+        qla.Grid3(args["nx"], args["ny"], args["nz"], 1.0, args["precision"], double_single=True)
