@@ -339,6 +339,9 @@ void qla_batch_destroy(qla_batch *b);
  * 256; 3x3 periodic convolutions, leaky ReLU 0.1, 2x2 average pooling,
  * nearest 2x upsampling with additive skips; BF16 weights and activations,
  * FP32 accumulation on the tensor cores, FP32 master weights and Adam.
+ * The convolutions' device waits are bounded: a wait that runs out makes
+ * the next synchronising call (surr_loss_grad, surr_train_step,
+ * surr_advance) return QLA_ETIMEOUT.
  * Inputs per site (features, FP32 [h][w][6]): q2, q3, q4, n - 1.5,
  * 4 dn/dx, 4 dn/dy; output ([h][w][3]): the change of q2, q3, q4.
  * ------------------------------------------------------------------------ */

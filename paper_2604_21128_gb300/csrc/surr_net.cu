@@ -305,6 +305,16 @@ qla_status backward(surr_net *n, int B) {
     return QLA_OK;
 }
 
+// After a stream synchronisation: did a tcgen05 convolution give up one of
+// its bounded waits since the last check?  (Its CTAs then skipped their
+// epilogues, so the outputs are not to be trusted.)
+qla_status tc_waits_ok(surr_net *n) {
+    int flag = 0;
+    NCUDA(n, conv_tc_error(&flag, true), "surrogate: wait flag");
+    if (flag) return nfail(n, QLA_ETIMEOUT, "surrogate: a tensor-core wait ran out");
+    return QLA_OK;
+}
+
 qla_status loss(surr_net *n, int B, const float *target, double *out) {
     const long long P = pixels(n, B, 0);
     const int blocks = std::min(n->lblocks, ew_blocks(P));
@@ -314,6 +324,8 @@ qla_status loss(surr_net *n, int B, const float *target, double *out) {
     NCUDA(n, cudaMemcpyAsync(h.data(), n->lpart, sizeof(double) * blocks, cudaMemcpyDeviceToHost,
                              n->stream), "surrogate: loss copy");
     NCUDA(n, cudaStreamSynchronize(n->stream), "surrogate: sync");
+    const qla_status w = tc_waits_ok(n);
+    if (w != QLA_OK) return w;
     double s = 0.0;
     for (double v : h) s += v;
     *out = s;
@@ -636,6 +648,7 @@ qla_status surr_advance(qla_ctx *c, surr_net *n, int windows, int K, double ener
         if (cudaMemcpyAsync(h.data(), sums, h.size() * 8, cudaMemcpyDeviceToHost, c->stream) ||
             cudaStreamSynchronize(c->stream))
             return QLA_ECUDA;
+        if ((s = tc_waits_ok(n)) != QLA_OK) return s;
         double e1 = 0.0, dd = 0.0, gg = 0.0;
         for (int b = 0; b < blocks; ++b) {
             e1 += h[b * 3];
