@@ -408,6 +408,14 @@ qla_status surr_weight_grad_raw(const void *dz_bf16, const void *in_bf16, int B,
                                 int cout, int cin, int splits, float *part, float *dw_f32,
                                 void *cuda_stream);
 
+/* Test hook for the bounded waits: while on is non-zero, one CTA of every
+ * gather-form tensor-core convolution waits for an mbarrier phase that never
+ * completes, gives up after 2 s of wall time, skips its output and raises
+ * the error flag, so surr_conv3x3_raw returns QLA_ETIMEOUT (and the
+ * network's next synchronising call would).  No fault and no hang: the other
+ * CTAs finish, the stalled one frees its tensor memory and returns. */
+qla_status surr_test_stall_conv(int on);
+
 /* ------------------------------------------------------------------------
  * Three dimensions.  The paper runs its scaling tests with a 3D code whose z
  * sequence it does not print; Eq. 3b4 (i dQ/dt = W^-1/2 M W^-1/2 Q) fixes

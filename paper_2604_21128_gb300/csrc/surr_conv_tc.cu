@@ -33,9 +33,12 @@ constexpr int KC = 32;           // input channels per row-patch chunk (two K = 
 // Gather-kernel stages: KS input channels of one tap (KS / 16 MMAs), six
 // stages of 32 channels or four of 64, all but two loaded ahead of the MMA.
 template <int KS> constexpr int gather_stages() { return KS == 32 ? 6 : 4; }
-constexpr unsigned WAIT_LIMIT = 1u << 22;
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // a wait gives up after 2 s
 
 __device__ int g_conv_tc_error;
+// Test hook (surr_test_stall_conv): CTA (0, 0) of each launch waits for a
+// phase that never completes, so its bounded wait runs out.
+__device__ int g_conv_tc_stall;
 
 // Shared-memory matrix descriptor (tcgen05 format): start address, leading
 // byte offset (K direction), stride byte offset (8-row direction), all in
@@ -58,20 +61,35 @@ __device__ __forceinline__ void mbar_init(uint64_t *b) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(b)) : "memory");
 }
 
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of the given parity; false once WAIT_NS of wall time
+// have passed (try_wait may suspend the thread for a while on each call, so
+// the bound is on time, not on the number of calls).
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
     const uint32_t a = smem_u32(b);
-    for (unsigned i = 0; i < WAIT_LIMIT; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
+    if (mbar_try(a, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try(a, parity)) return true;
+        if (global_ns() - t0 > WAIT_NS) return false;
     }
-    return false;
 }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -311,7 +329,9 @@ k_conv3x3_tc(const bf16 *__restrict__ in, int B, int H, int W, int cin,
     // the last commit covers every MMA of the tile
     if (ok) {
         const int kl = ksteps - 1;
-        ok = mbar_wait(&bar[kl % NSTAGE], (kl / NSTAGE) & 1);
+        // the test hook waits for the phase after the last one (never completes)
+        const uint32_t stall = g_conv_tc_stall && blockIdx.x == 0 && blockIdx.y == 0;
+        ok = mbar_wait(&bar[kl % NSTAGE], ((kl / NSTAGE) & 1) ^ stall);
     }
     cp_wait<0>();
     // tcgen05.ld is warp-collective: every thread takes the same branch below
@@ -679,6 +699,10 @@ cudaError_t conv3x3_tc(const ConvArgs &a, int mode, bool act, bool skip, cudaStr
     }
     if (mode == OUT_F32) return conv_tc_t<OUT_F32, false, false>(a, st);
     return conv_tc_t<ACC_F32, false, false>(a, st);
+}
+
+cudaError_t conv_tc_stall(int on) {
+    return cudaMemcpyToSymbol(g_conv_tc_stall, &on, sizeof(int));
 }
 
 cudaError_t conv_tc_error(int *flag, bool reset) {

@@ -27,6 +27,8 @@ cudaError_t conv3x3_tc(const ConvArgs &a, int mode, bool act, bool skip, cudaStr
 // Reads (and with reset, clears) the flag a tcgen05 convolution sets when one
 // of its mbarrier waits gives up.
 cudaError_t conv_tc_error(int *flag, bool reset);
+// Test hook: make one CTA of each tcgen05 gather convolution run out its wait.
+cudaError_t conv_tc_stall(int on);
 cudaError_t weight_grad(const bf16 *dz, const bf16 *in, int B, int H, int W, int cout, int cin,
                         int splits, float *part, cudaStream_t st);
 cudaError_t sum_splits(const float *part, int splits, long long n, float *g, cudaStream_t st);

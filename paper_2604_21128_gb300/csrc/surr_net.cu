@@ -688,10 +688,13 @@ extern "C" qla_status surr_conv3x3_raw(const void *in_bf16, int B, int H, int W,
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (conv3x3(a, OUT_F32, false, false, st) != cudaSuccess) return QLA_ECUDA;
     int flag = 0;
-    if (cudaStreamSynchronize(st) != cudaSuccess || conv_tc_error(&flag, true) != cudaSuccess ||
-        flag)
+    if (cudaStreamSynchronize(st) != cudaSuccess || conv_tc_error(&flag, true) != cudaSuccess)
         return QLA_ECUDA;
-    return QLA_OK;
+    return flag ? QLA_ETIMEOUT : QLA_OK;
+}
+
+extern "C" qla_status surr_test_stall_conv(int on) {
+    return conv_tc_stall(on ? 1 : 0) == cudaSuccess ? QLA_OK : QLA_ECUDA;
 }
 
 extern "C" qla_status surr_weight_grad_raw(const void *dz_bf16, const void *in_bf16, int B, int H,

@@ -207,3 +207,36 @@ def test_trained_network_beats_the_zero_change_predictor_and_checks_hold():
         assert e_net < 0.25 * e_zero
         assert err <= 0.25
         torch.cuda.synchronize()
+
+
+def test_conv_wait_that_runs_out_reports_timeout_and_recovers():
+    """A CTA whose mbarrier wait never completes gives up (2 s bound), skips its
+    output and the call returns QLA_ETIMEOUT; the next call is exact again."""
+    import time
+
+    import torch
+    lib = qla.load()
+    rng = np.random.default_rng(99)
+    B, H, W, cin, cout = 1, 8, 16, 32, 32
+    x = _bf16(rng, (B, H, W, cin))
+    w = _bf16(rng, (cout, 9, cin), 0.1)
+    out = torch.zeros((B, H, W, cout), dtype=torch.float32, device="cuda")
+
+    def call():
+        return lib.surr_conv3x3_raw(ctypes.c_void_p(x.data_ptr()), B, H, W, cin,
+                                    ctypes.c_void_p(w.data_ptr()), cout,
+                                    ctypes.c_void_p(out.data_ptr()), None)
+
+    assert lib.surr_test_stall_conv(1) == 0
+    try:
+        t0 = time.perf_counter()
+        st = call()
+        dt = time.perf_counter() - t0
+    finally:
+        assert lib.surr_test_stall_conv(0) == 0
+    assert st == 5, st                      # QLA_ETIMEOUT
+    assert 1.0 < dt < 30.0, dt
+    assert call() == 0
+    torch.cuda.synchronize()
+    want = _ref_conv(x, w).numpy()
+    assert np.linalg.norm(out.cpu().numpy() - want) <= 1e-5 * np.linalg.norm(want)
