@@ -235,6 +235,11 @@ struct March {
     T carry[4][2][2][LX];   // [neighbour layer][pair][value][x]
     CC kring[LAG][LX];      // collision coefficients of the rows in flight
     CV vnext[LX];           // row J+1's potential coefficients
+    // whether row J+1's site has its own record: shared records (index below
+    // UNIFORM_SLOTS) belong to sites whose four neighbours carry their n, so
+    // beta = 0 and V is exactly the identity there (cos 1, sin 0 in FP64;
+    // 1 - cos 0, sin 0 in FP32): skipping it changes no bit
+    bool vlive[LX];
     // FP64 looks row J+1's records up early (their latency hides behind the
     // row's arithmetic) and copies them into the ring at the next row; FP32
     // and double-single load them straight into the ring slot that frees at
@@ -267,10 +272,14 @@ struct March {
     __device__ __forceinline__ void lookup_next() {
 #pragma unroll
         for (int x = 0; x < LX; ++x) {
-            const MedRec<T> *r = table + ring[S].idx[lc + x];
+            const uint32_t id = ring[S].idx[lc + x];
+            const MedRec<T> *r = table + id;
             if constexpr (EARLY) knext[x] = r->c;
             else kring[K][x] = r->c;
-            if constexpr (VIN) vnext[x] = r->v;
+            if constexpr (VIN) {
+                vlive[x] = id >= uint32_t(UNIFORM_SLOTS);
+                if (vlive[x]) vnext[x] = r->v;
+            }
         }
     }
 
@@ -301,6 +310,7 @@ struct March {
         if constexpr (VIN) {
 #pragma unroll
             for (int x = 0; x < LX; ++x) {
+                if (!vlive[x]) continue;
                 T s[6];
 #pragma unroll
                 for (int c = 0; c < 6; ++c) s[c] = plane_of<P>(c) >= 0 ? q[c][x] : T(0);
