@@ -7,6 +7,7 @@ shift in the wrong direction or a wrong angle in the oracle fails at least
 one of them (the generator fit fails for any error in a single coupling).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -375,14 +376,28 @@ def fresnel_R(theta, n1, n2):
     return ((n1 * np.cos(theta) - root) / (n1 * np.cos(theta) + root)) ** 2
 
 
+def paper_values():
+    """The printed values of tests/golden/paper_values.txt (cited there)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split("=")
+                vals[k.strip()] = float(v)
+    return vals
+
+
 def test_fresnel_angles_printed_in_the_paper():
     """R = T at 0.336 pi (n 1->3) and 0.094 pi (3->1); critical 0.108 pi."""
     from scipy.optimize import brentq
+    pv = paper_values()
     a1 = brentq(lambda t: fresnel_R(t, 1.0, 3.0) - 0.5, 0.01, 1.5)
     a2 = brentq(lambda t: fresnel_R(t, 3.0, 1.0) - 0.5, 0.01, 0.3)
-    assert abs(a1 / math.pi - 0.336) < 0.001
-    assert abs(a2 / math.pi - 0.094) < 0.001
-    assert abs(math.asin(1 / 3) / math.pi - 0.108) < 0.001
+    assert abs(a1 / math.pi - pv["fresnel_equal_angle_1_to_3"]) < 0.001
+    assert abs(a2 / math.pi - pv["fresnel_equal_angle_3_to_1"]) < 0.001
+    assert abs(math.asin(1 / 3) / math.pi - pv["critical_angle_3_to_1"]) < 0.001
     assert fresnel_R(np.array([0.0]), 1.0, 2.0)[0] == pytest.approx(1 / 9)
 
 
@@ -475,10 +490,16 @@ def _oblique_reflectance(n1, n2, theta, ly_cells, delta=0.5, w=30.0, L=600.0, x0
     return back, float(np.sum(wgt * _fresnel_s(n1, n2, np.arctan2(ky, kk))) / np.sum(wgt))
 
 
+_PV = paper_values()
+
+
 @pytest.mark.parametrize("n1,n2,theta,ly_cells,tol", [
-    (1.0, 3.0, 0.336 * math.pi, 36, 0.015),   # R = T at the front of the ellipse
-    (3.0, 1.0, 0.094 * math.pi, 58, 0.02),    # R = T inside the dielectric
-    (3.0, 1.0, 0.2 * math.pi, 20, 0.005),     # beyond the critical angle 0.108 pi: R = 1
+    # R = T at the front of the ellipse
+    (1.0, 3.0, _PV["fresnel_equal_angle_1_to_3"] * math.pi, 36, 0.015),
+    # R = T inside the dielectric
+    (3.0, 1.0, _PV["fresnel_equal_angle_3_to_1"] * math.pi, 58, 0.02),
+    # beyond the critical angle 0.108 pi: R = 1
+    (3.0, 1.0, 0.2 * math.pi, 20, 0.005),
 ])
 def test_oblique_incidence_matches_fresnel_s(n1, n2, theta, ly_cells, tol):
     """The scheme reproduces the s-polarised reflectance the paper uses in
@@ -488,3 +509,16 @@ def test_oblique_incidence_matches_fresnel_s(n1, n2, theta, ly_cells, tol):
     got, want = _oblique_reflectance(n1, n2, theta, ly_cells)
     print("n1 %g n2 %g theta %.3f pi: R %.4f (Fresnel %.4f)" % (n1, n2, theta / math.pi, got, want))
     assert abs(got - want) < tol
+
+
+def test_energy_conserved_to_the_printed_digits():
+    """The scalar-medium runs conserve energy to the number of significant
+    figures the paper states (tests/golden/paper_values.txt); the rotation
+    reading of V does so by construction, the 256^2 ellipse workload over its
+    400 steps."""
+    digits = paper_values()["energy_significant_digits"]
+    w = inputs.ellipse_256()
+    n = w.medium()
+    q0 = oracle.packet(n, w.delta, **w.packet.as_dict())
+    qT = oracle.run(q0, n, w.delta, w.steps)
+    assert abs(oracle.energy(qT) / oracle.energy(q0) - 1) < 10.0 ** (-digits)
