@@ -74,7 +74,8 @@ def peaks():
 # 16 collision rotations (8 layers of U_x, 8 of U_y) and 2 potential
 # rotations on each live pair (1 pair in E_z mode, 2 with six planes).  FP32:
 # a collision rotation with two-word coefficients is 8 FP32 instructions
-# (4 per output), a potential rotation 6; FP64: 4 per rotation either way.
+# (4 per output), a potential rotation 6; FP64: a collision rotation is 3
+# (three shears), a potential rotation 4.
 # Peaks from the unit counts and the maximum clock: 152 SMs x 128 FP32 lanes
 # x 2.07 GHz for FP32 instructions; the nominal 1.25 TFLOP/s FP64 rate
 # counted as FMA-class instructions (2 flops each) for FP64.
@@ -86,7 +87,7 @@ def alu_ops_per_su(P, elt):
     pairs = 1 if P == 3 else 2
     if elt == 4:
         return pairs * (16 * 8 + 2 * 6)
-    return pairs * (16 * 4 + 2 * 4)
+    return pairs * (16 * 3 + 2 * 4)
 
 
 def ds_ops_per_su(P):
@@ -100,7 +101,7 @@ def ds_ops_per_su(P):
 def alu_ops_per_su_3d(elt):
     """3D: per axis 8 layers x 2 pairs of collision rotations, then six
     potential rotations (two per axis)."""
-    return 3 * 16 * (8 if elt == 4 else 4) + 6 * (6 if elt == 4 else 4)
+    return 3 * 16 * (8 if elt == 4 else 3) + 6 * (6 if elt == 4 else 4)
 
 
 def roofline(P, elt, su_per_s, traffic, ops=None, pipe=None, **extra):

@@ -49,10 +49,9 @@ template <typename T> struct V3 { T gx, sx, gy, sy, gz, sz; };
 // three FP32 words (their sums are the FP64 values).
 template <> struct V3<dsf> { DSCoef x, y, z; };
 
+// FP64 collision coefficients: (tan(theta/2), sin theta), three shears.
 __device__ __forceinline__ void coef_c(double th, double2 &k) {
-    double s, c;
-    sincos(th, &s, &c);
-    k = make_double2(c, s);
+    k = make_double2(tan(0.5 * th), sin(th));
 }
 __device__ __forceinline__ void split2(double v, float &hi, float &lo) {
     hi = __double2float_rn(v);

@@ -21,9 +21,8 @@ inline int grid_for(size_t n, int threads = AUX_THREADS) {
 // reading) or beta (printed shear).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void make_rec(MedRec<double> &r, double th, double px, double py) {
-    double s, c;
-    sincos(th, &s, &c);
-    r.c = make_double2(c, s);
+    // collision: (tan(theta/2), sin theta) for the three-shear rotation
+    r.c = make_double2(tan(0.5 * th), sin(th));
     double sx, cx, sy, cy;
     sincos(px, &sx, &cx);
     sincos(py, &sy, &cy);

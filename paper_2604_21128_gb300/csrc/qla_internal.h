@@ -56,7 +56,8 @@ __host__ __device__ constexpr Pair pair_of(bool xdir, int k) {
 
 // ----------------------------------------------------------------------------
 // Coefficient records, one per site.
-//   FP64: CoefC = (cos theta, sin theta); CoefV = (cos phi_x, sin phi_x,
+//   FP64: CoefC = (tan(theta/2), sin theta), the three-shear form of the
+//         rotation (rotate below); CoefV = (cos phi_x, sin phi_x,
 //         cos phi_y, sin phi_y) with phi = beta/2 (rotation reading) or beta
 //         (printed shear).
 //   FP32: CoefC = (c_hi, s_hi, c_lo, s_lo): cos theta and sin theta each
@@ -111,14 +112,18 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
     return k;
 }
 
-// (a, b) <- [[c, -g s], [g s, c]] (a, b) with g = +-1.
-// Explicit FMAs fix the rounding, so every kernel produces the same bits.
+// (a, b) <- [[c, -g s], [g s, c]] (a, b) with g = +-1, as three shears:
+// a -= g t b, b += g s a, a -= g t b with k = (t, s) = (tan(theta/2),
+// sin theta).  The product of the shears is the rotation because
+// 1 - t s = cos theta and t (2 - t s) = sin theta; its determinant is 1 for
+// any rounded t and s.  Three FMAs instead of two products and two FMAs: the
+// FP64 step is bound by the FP64 pipe.  Explicit FMAs fix the rounding, so
+// every kernel produces the same bits.
 __device__ __forceinline__ void rotate(double &a, double &b, double2 k, double g) {
-    const double s = g * k.y;
-    const double na = fma(k.x, a, -(s * b));
-    const double nb = fma(k.x, b, s * a);
-    a = na;
-    b = nb;
+    const double t = g * k.x, s = g * k.y;
+    a = fma(-t, b, a);
+    b = fma(s, a, b);
+    a = fma(-t, b, a);
 }
 
 // Same rotation with two-word c and s: the low-word terms are accumulated
