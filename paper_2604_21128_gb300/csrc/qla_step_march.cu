@@ -35,11 +35,13 @@ namespace {
 
 using namespace march;
 
-// Blocks per SM the register allocation must allow: the FP32 two-column
-// E_z variant is held to 128 registers (16 warps per SM); the others take
-// what they need.
+// Blocks per SM the register allocation must allow: the two-column E_z
+// variants in FP32 and FP64 are held to 128 registers (16 warps per SM; in
+// FP64 the extra warps hide the FP64 pipe's result latency, measured 10%
+// faster at 8192^2 than 3 blocks at 164 registers despite a few hundred
+// bytes of spills); the others take what they need.
 template <typename T, int P, int LX> constexpr int min_blocks() {
-    return (sizeof(T) == 4 && P == 3 && LX == 2) ? 4 : 1;
+    return ((sizeof(T) == 4 || std::is_same<T, double>::value) && P == 3 && LX == 2) ? 4 : 1;
 }
 
 template <typename T, int P, int LX, int VM, bool VIN>
