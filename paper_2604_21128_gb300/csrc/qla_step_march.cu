@@ -35,13 +35,18 @@ namespace {
 
 using namespace march;
 
-// Blocks per SM the register allocation must allow: the two-column E_z
-// variants in FP32 and FP64 are held to 128 registers (16 warps per SM; in
-// FP64 the extra warps hide the FP64 pipe's result latency, measured 10%
-// faster at 8192^2 than 3 blocks at 164 registers despite a few hundred
-// bytes of spills); the others take what they need.
+// Blocks per SM the register allocation must allow: the two-column
+// variants in FP32 (E_z and six planes) and in FP64 E_z are held to 128
+// registers (16 warps per SM).  Measured at 8192^2 against what they take
+// unconstrained (3 blocks): FP32 six planes 11% faster (149 registers, a few
+// bytes of spills at 128), FP64 E_z 10% (164 registers, a few hundred bytes
+// of spills; the extra warps hide the FP64 pipe's result latency).  FP64 six
+// planes (246) and double-single keep what they need.
 template <typename T, int P, int LX> constexpr int min_blocks() {
-    return ((sizeof(T) == 4 || std::is_same<T, double>::value) && P == 3 && LX == 2) ? 4 : 1;
+    return LX == 2 && (std::is_same<T, float>::value ||
+                       (std::is_same<T, double>::value && P == 3))
+               ? 4
+               : 1;
 }
 
 template <typename T, int P, int LX, int VM, bool VIN>
