@@ -521,12 +521,14 @@ cudaError_t march3_t(const void *in, void *out, const void *kc, const void *kv, 
 // then the store.  Neither launch uses shared-memory layer passes or block
 // barriers.
 // ---------------------------------------------------------------------------
-template <typename T>
+// PS: the planes stepped (6, or one triple of the six-plane storage: U_x and
+// U_y never couple (q2, q3, q4) with (q0, q1, q5); U_z does, in launch 2).
+template <typename T, int PS>
 __global__ void __launch_bounds__(32 * march::WARPS)
 k3_slices(const T *__restrict__ in, T *__restrict__ out, const uint32_t *__restrict__ midx,
           const MedRec<T> *__restrict__ table, int nx, int ny, int pitch, size_t plane_elems,
           int seg_h, int n_wx, int n_wy, long long n_items) {
-    using M = march::March<T, 6, 2, V_NONE, false>;
+    using M = march::March<T, PS, 2, V_NONE, false>;
     extern __shared__ __align__(16) unsigned char smem_s[];
     typename M::Slot *ring =
         reinterpret_cast<typename M::Slot *>(smem_s) + (threadIdx.x >> 5) * march::NSLOT;
@@ -693,13 +695,14 @@ bool slices_ok(int nx, int ny, size_t plane_elems) {
     return nx % 2 == 0 && nx >= 64 && ny >= 8 && 6 * (unsigned long long)plane_elems < (1ull << 32);
 }
 
-template <typename T, int VM>
-cudaError_t slices_t(const void *in, void *out, const uint32_t *idx3, const void *rec,
-                     const void *rv, int nx, int ny, int nz, int pitch, size_t plane_elems,
-                     int num_sms, cudaStream_t st) {
-    using M = march::March<T, 6, 2, V_NONE, false>;
+// Launch 1 of the slices step for the plane set PS.
+template <typename T, int PS>
+cudaError_t slices_launch(const void *in, void *out, const uint32_t *idx3, const void *rec,
+                          int nx, int ny, int nz, int pitch, size_t plane_elems, int num_sms,
+                          cudaStream_t st) {
+    using M = march::March<T, PS, 2, V_NONE, false>;
     const size_t smem = sizeof(typename M::Slot) * march::NSLOT * march::WARPS;
-    auto k1 = k3_slices<T>;
+    auto k1 = k3_slices<T, PS>;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     static int per_sm = 1;
@@ -726,7 +729,29 @@ cudaError_t slices_t(const void *in, void *out, const uint32_t *idx3, const void
         static_cast<const T *>(in), static_cast<T *>(out), idx3,
         static_cast<const MedRec<T> *>(rec), nx, ny, pitch, plane_elems, seg_h, n_wx, int(n_wy),
         n_items);
-    cudaError_t e = cudaGetLastError();
+    return cudaGetLastError();
+}
+
+// Kernels one slices step launches: double-single runs launch 1 once per
+// triple (a six-plane launch needs 250 registers, two blocks per SM).
+template <typename T> constexpr int slices_launches() {
+    return std::is_same<T, dsf>::value ? 3 : 2;
+}
+
+template <typename T, int VM>
+cudaError_t slices_t(const void *in, void *out, const uint32_t *idx3, const void *rec,
+                     const void *rv, int nx, int ny, int nz, int pitch, size_t plane_elems,
+                     int num_sms, cudaStream_t st) {
+    cudaError_t e;
+    if constexpr (std::is_same<T, dsf>::value) {
+        e = slices_launch<T, P_TE6>(in, out, idx3, rec, nx, ny, nz, pitch, plane_elems, num_sms,
+                                    st);
+        if (e == cudaSuccess)
+            e = slices_launch<T, P_TM6>(in, out, idx3, rec, nx, ny, nz, pitch, plane_elems,
+                                        num_sms, st);
+    } else {
+        e = slices_launch<T, 6>(in, out, idx3, rec, nx, ny, nz, pitch, plane_elems, num_sms, st);
+    }
     if (e != cudaSuccess) return e;
     // launch 2: one thread per column, z segments for about two waves of
     // 128-thread blocks (at least 16 planes each)
@@ -1276,7 +1301,7 @@ qla_status qla3_step(qla3_ctx *c, long long n_steps) {
                                             c->nz, c->pitch, c->plane_elems, c->num_sms,
                                             c->stream);
             CUDA3(c, e, "qla3_step: kernel");
-            c->launches += 2;
+            c->launches += slices_launches<dsf>();
         }
         CUDA3(c, raw_from_ds(c->state[c->cur], n, c->stream), "qla3_step: from double-single");
         c->launches += 2;

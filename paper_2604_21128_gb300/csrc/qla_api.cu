@@ -380,7 +380,7 @@ qla_status qla_step(qla_ctx *c, long long n_steps) {
             QLA_CUDA(c, launch_step_march_ds(c, c->state[c->cur], c->state[c->cur ^ 1],
                                              c->pending_v),
                      "qla_step: kernel");
-            c->launches++;
+            c->launches += step_march_ds_launches(c);
             c->cur ^= 1;
             c->pending_v = c->vmode != V_NONE;
         }

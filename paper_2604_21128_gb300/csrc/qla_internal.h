@@ -14,12 +14,29 @@ namespace qla {
 // ----------------------------------------------------------------------------
 // Amplitude numbering (Eq. 3b3) and plane mapping.  A context stores P live
 // planes: P = 6 holds q0..q5 in order; P = 3 (E_z polarisation) holds
-// q2, q3, q4 as planes 0, 1, 2.  plane_of<P>(c) is -1 for an absent q_c.
+// q2, q3, q4 as planes 0, 1, 2.  Collisions and potential steps never couple
+// the triple (q2, q3, q4) with (q0, q1, q5) (Eqs. 2e3, 2e8, 2e11, 2e12), so a
+// kernel may also step one triple of a six-plane state in place: the plane
+// sets P_TE6 (q2, q3, q4) and P_TM6 (q0, q1, q5), with the six-plane storage.
+// plane_of<P>(c) is q_c's plane in storage, -1 for an absent q_c;
+// slot_of<P>(c) its index among the set's nplanes<P>() planes.
 // ----------------------------------------------------------------------------
+constexpr int P_TE6 = 7, P_TM6 = 8;
 template <int P>
 __host__ __device__ constexpr int plane_of(int c) {
-    return P == 6 ? c : (c >= 2 && c <= 4 ? c - 2 : -1);
+    return P == 6       ? c
+         : P == 3       ? (c >= 2 && c <= 4 ? c - 2 : -1)
+         : P == P_TE6   ? (c >= 2 && c <= 4 ? c : -1)
+                        : (c == 0 || c == 1 || c == 5 ? c : -1);
 }
+template <int P> __host__ __device__ constexpr int nplanes() { return P == 6 ? 6 : 3; }
+template <int P>
+__host__ __device__ constexpr int slot_of(int c) {
+    return P == 6 ? c : P == P_TM6 ? (c == 5 ? 2 : c) : c - 2;
+}
+// whether the set holds the E_z triple, the (q0, q1, q5) triple
+template <int P> __host__ __device__ constexpr bool has_te() { return P != P_TM6; }
+template <int P> __host__ __device__ constexpr bool has_tm() { return P == 6 || P == P_TM6; }
 
 // ----------------------------------------------------------------------------
 // The eight collisions of one evolution operator U (Eqs. 2e6, 2e9).
@@ -234,26 +251,27 @@ __device__ __forceinline__ void lcu_y(T (&v)[6], T c1, T s1, T c3, T s3) {
 // six amplitudes (entries absent in E_z mode are ignored).  kv = CoefV.
 template <typename T, int P, int VM, typename KV>
 __device__ __forceinline__ void apply_potential(T (&q)[6], KV kv) {
+    constexpr bool te = has_te<P>(), tm = has_tm<P>();
     if constexpr (VM == V_ROTATION && std::is_same<T, dsf>::value) {
         // double-single: the same rotations with three-word cos and sin
-        rotate(q[2], q[4], kv.x, T(-1));
-        if constexpr (P == 6) rotate(q[1], q[5], kv.x, T(1));
-        rotate(q[2], q[3], kv.y, T(1));
-        if constexpr (P == 6) rotate(q[0], q[5], kv.y, T(-1));
+        if constexpr (te) rotate(q[2], q[4], kv.x, T(-1));
+        if constexpr (tm) rotate(q[1], q[5], kv.x, T(1));
+        if constexpr (te) rotate(q[2], q[3], kv.y, T(1));
+        if constexpr (tm) rotate(q[0], q[5], kv.y, T(-1));
     } else if constexpr (VM == V_ROTATION) {
         // V_x: (q2,q4) by [[c, s], [-s, c]]; (q1,q5) by [[c, -s], [s, c]]
-        rotate1(q[2], q[4], kv.x, kv.y, T(-1));
-        if constexpr (P == 6) rotate1(q[1], q[5], kv.x, kv.y, T(1));
+        if constexpr (te) rotate1(q[2], q[4], kv.x, kv.y, T(-1));
+        if constexpr (tm) rotate1(q[1], q[5], kv.x, kv.y, T(1));
         // V_y: (q2,q3) by [[c, -s], [s, c]]; (q0,q5) by [[c, s], [-s, c]]
-        rotate1(q[2], q[3], kv.z, kv.w, T(1));
-        if constexpr (P == 6) rotate1(q[0], q[5], kv.z, kv.w, T(-1));
+        if constexpr (te) rotate1(q[2], q[3], kv.z, kv.w, T(1));
+        if constexpr (tm) rotate1(q[0], q[5], kv.z, kv.w, T(-1));
     } else if constexpr (VM == V_LITERAL) {
         // V_x: q4 <- -sin q2 + cos q4; q5 <- +sin q1 + cos q5
-        shear1(q[2], q[4], kv.x, kv.y, T(-1));
-        if constexpr (P == 6) shear1(q[1], q[5], kv.x, kv.y, T(1));
+        if constexpr (te) shear1(q[2], q[4], kv.x, kv.y, T(-1));
+        if constexpr (tm) shear1(q[1], q[5], kv.x, kv.y, T(1));
         // V_y: q3 <- sin q2 + cos q3; q5 <- -sin q0 + cos q5
-        shear1(q[2], q[3], kv.z, kv.w, T(1));
-        if constexpr (P == 6) shear1(q[0], q[5], kv.z, kv.w, T(-1));
+        if constexpr (te) shear1(q[2], q[3], kv.z, kv.w, T(1));
+        if constexpr (tm) shear1(q[0], q[5], kv.z, kv.w, T(-1));
     } else if constexpr (VM == V_LCU) {
         T cx, sx, cy, sy;
         cos_sin(kv.x, kv.y, cx, sx);
@@ -403,6 +421,7 @@ cudaError_t launch_step_tensor(qla_ctx *c, const void *in, void *out);
 // double-single records, and the in-place conversions of the state buffer
 // between FP64 and word pairs.
 cudaError_t launch_step_march_ds(qla_ctx *c, const void *in, void *out, bool vin);
+int step_march_ds_launches(const qla_ctx *c);   // kernels one such step launches
 cudaError_t launch_state_to_ds(qla_ctx *c, void *state);
 cudaError_t launch_state_from_ds(qla_ctx *c, void *state);
 // Lattices the double-single step takes (those of the FP64 marching kernel).

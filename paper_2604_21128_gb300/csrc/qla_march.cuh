@@ -214,9 +214,9 @@ struct March {
     using CV = typename Coef<T>::V;
     static constexpr int W = 32 * LX;   // window columns
     static constexpr int WOUT = W - 8;  // stored columns
-    // one staged row: P planes of W values, then W record indices
+    // one staged row: the set's planes of W values, then W record indices
     struct Slot {
-        T q[P][W];
+        T q[nplanes<P>()][W];
         uint32_t idx[W];
     };
 
@@ -259,8 +259,11 @@ struct March {
     template <int S>
     __device__ __forceinline__ void stage() {
 #pragma unroll
-        for (int p = 0; p < P; ++p)
-            cp_async<LX * sizeof(T)>(&ring[S].q[p][lc], in + p * plane + o_in);
+        for (int c = 0; c < 6; ++c) {
+            const int p = plane_of<P>(c);
+            if (p >= 0)
+                cp_async<LX * sizeof(T)>(&ring[S].q[slot_of<P>(c)][lc], in + p * plane + o_in);
+        }
         cp_async<LX * 4>(&ring[S].idx[lc], midx + o_in);
         cp_async_commit();
         o_in = next_row(o_in);
@@ -296,10 +299,9 @@ struct March {
         T q[6][LX];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            const int p = plane_of<P>(c);
-            if (p >= 0) {
+            if (plane_of<P>(c) >= 0) {
 #pragma unroll
-                for (int x = 0; x < LX; ++x) q[c][x] = ring[PH].q[p][lc + x];
+                for (int x = 0; x < LX; ++x) q[c][x] = ring[PH].q[slot_of<P>(c)][lc + x];
             }
         }
         if constexpr (EARLY) {

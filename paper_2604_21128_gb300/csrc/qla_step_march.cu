@@ -182,9 +182,17 @@ bool ds_shape_ok(int nx, int ny) {
            size_t(ny) * ((size_t(nx) + 31) / 32 * 32) < (size_t(1) << 31);
 }
 
+// Six-plane double-single steps run as two launches, one per decoupled
+// triple (P_TE6, then P_TM6), each with the E_z kernel's register budget:
+// a single six-plane launch needs 255 registers (two blocks per SM) and
+// reached a quarter of the E_z rate.  The arithmetic per pair is unchanged.
 cudaError_t launch_step_march_ds(qla_ctx *c, const void *in, void *out, bool vin) {
-    return c->P == 6 ? launch_ds<6>(c, in, out, vin) : launch_ds<3>(c, in, out, vin);
+    if (c->P != 6) return launch_ds<3>(c, in, out, vin);
+    const cudaError_t e = launch_ds<P_TE6>(c, in, out, vin);
+    return e != cudaSuccess ? e : launch_ds<P_TM6>(c, in, out, vin);
 }
+
+int step_march_ds_launches(const qla_ctx *c) { return c->P == 6 ? 2 : 1; }
 
 cudaError_t launch_step_march(qla_ctx *c, const void *in, void *out, bool vin) {
     if (c->prec == QLA_FP64)

@@ -67,6 +67,27 @@ def test_random_state_against_oracle_and_native(shape, potential, te):
     assert rel_l2(got, native) <= 1e-13, rel_l2(got, native)
 
 
+@pytest.mark.parametrize("potential", ["rotation", "none"])
+def test_six_planes_step_each_triple_like_the_e_z_kernel(potential):
+    """The operators never couple (q2, q3, q4) with (q0, q1, q5), and a
+    six-plane double-single step runs one launch per triple: its (q2, q3, q4)
+    planes must be bit-identical to an E_z context's on the same triple, and
+    the other triple must not depend on the first."""
+    nx, ny = 250, 64
+    n = inputs.random_medium(nx, ny, seed=3, lo=1.0, hi=3.5)
+    q0 = inputs.random_state(nx, ny, seed=11)
+    six, _ = run(n, 0.8, 9, q0=q0, potential=potential)
+    te = q0.copy()
+    te[[0, 1, 5]] = 0.0
+    tri, _ = run(n, 0.8, 9, q0=te, te=True, potential=potential)
+    assert np.array_equal(six[[2, 3, 4]], tri[[2, 3, 4]])
+    tm = q0.copy()
+    tm[[2, 3, 4]] = 0.0
+    other, _ = run(n, 0.8, 9, q0=tm, potential=potential)
+    assert np.array_equal(six[[0, 1, 5]], other[[0, 1, 5]])
+    assert not np.any(other[[2, 3, 4]])
+
+
 def test_split_calls_agree_with_one_call():
     # each call converts the state to word pairs and back
     w = inputs.scaled(inputs.ellipse_256(), 128, 128, 60)
