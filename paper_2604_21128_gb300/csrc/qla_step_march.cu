@@ -107,16 +107,19 @@ cudaError_t launch_t(qla_ctx *c, const void *in, void *out, const void *table) {
     constexpr int WOUT = 32 * LX - 8;
     auto kern = k_step_march<T, P, LX, VM, VIN>;
     const size_t smem = sizeof(typename March<T, P, LX, VM, VIN>::Slot) * NSLOT * WARPS;
-    static int blocks_per_sm = -1;  // per instantiation, per process
-    if (blocks_per_sm < 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(smem));
-        if (e != cudaSuccess) return e;
+    // per instantiation, per process; initialised once (thread-safe)
+    struct Occ { cudaError_t err; int per_sm; };
+    static const Occ occ = [&] {
+        Occ o{cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+              1};
         int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * WARPS, smem);
-        if (e != cudaSuccess) return e;
-        blocks_per_sm = b > 0 ? b : 1;
-    }
+        if (o.err == cudaSuccess)
+            o.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * WARPS, smem);
+        o.per_sm = b > 0 ? b : 1;
+        return o;
+    }();
+    if (occ.err != cudaSuccess) return occ.err;
+    const int blocks_per_sm = occ.per_sm;
     const int n_wx = (c->nx + WOUT - 1) / WOUT;
     int seg = c->march_seg;
     if (seg <= 0)

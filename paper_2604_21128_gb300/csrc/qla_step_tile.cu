@@ -179,13 +179,10 @@ cudaError_t launch_tile_t(qla_ctx *c, const void *in, void *out) {
     constexpr int RX = TX + 2 * HALO, RY = TY + 2 * HALO;
     const size_t smem = size_t(RX) * RY * (sizeof(SC) + P * sizeof(T));
     auto kern = k_step_tile<T, P, VM, VIN, TS>;
-    static bool configured = false;  // per instantiation, per process
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(smem));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    // per instantiation, per process; set once (thread-safe)
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (attr != cudaSuccess) return attr;
     dim3 grid((c->nx + TX - 1) / TX, (c->ny + TY - 1) / TY);
     kern<<<grid, THREADS, smem, c->stream>>>(
         static_cast<const T *>(in), static_cast<T *>(out),

@@ -609,15 +609,19 @@ cudaError_t launch_rows(const ConvArgs &a, long long ntiles, cudaStream_t st) {
             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    static int dev_sms = 0, dev_smem = 0, dev_smem_block = 0;
-    if (dev_sms == 0) {
+    // the device's SM count and shared-memory limits, read once (thread-safe)
+    struct Dev { int sms, smem, smem_block; };
+    static const Dev dv = [] {
+        Dev d{0, 0, 0};
         int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        cudaDeviceGetAttribute(&dev_smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (dev_sms < 1) dev_sms = 1;
-    }
+        cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&d.smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&d.smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (d.sms < 1) d.sms = 1;
+        return d;
+    }();
+    const int dev_sms = dv.sms, dev_smem = dv.smem, dev_smem_block = dv.smem_block;
     // CTAs per SM from shared memory -- dynamic + static + the 1 KB the system
     // reserves per CTA -- and TMEM, 512 columns.  (Deeper patch rings measured
     // slower: the chunk's 18 MMAs into one accumulator, not the loads, bound
