@@ -122,10 +122,17 @@ cudaError_t launch_t(qla_ctx *c, const void *in, void *out, const void *table) {
     const int blocks_per_sm = occ.per_sm;
     const int n_wx = (c->nx + WOUT - 1) / WOUT;
     int seg = c->march_seg;
-    if (seg <= 0)
-        seg = pick_segment(c->ny, n_wx, (long long)blocks_per_sm * WARPS * c->num_sms);
-    else
+    if (seg <= 0) {
+        long long resident = (long long)blocks_per_sm * WARPS * c->num_sms;
+        // FP64 E_z is bound by the FP64 pipe, which few warps keep busy, while
+        // every segment re-reads 8 rows: half an item per resident warp slot
+        // measured best (8192^2: 1024-row segments 8.6e9 site-updates/s
+        // against 8.4e9 at 256; 4096^2: 256 rows 8.4e9 against 7.7e9 at 64)
+        if (std::is_same<T, double>::value && P == 3) resident /= 4;
+        seg = pick_segment(c->ny, n_wx, resident);
+    } else {
         seg = (seg + 3) / 4 * 4;
+    }
     const int n_wy = (c->ny + seg - 1) / seg;
     const int n_items = n_wx * n_wy;
     const int blocks = (n_items + WARPS - 1) / WARPS;
