@@ -88,6 +88,34 @@ def test_six_planes_step_each_triple_like_the_e_z_kernel(potential):
     assert not np.any(other[[2, 3, 4]])
 
 
+def test_launch_counts_match_the_kernels_each_step_runs():
+    """A double-single call converts the state twice and launches the
+    marching kernel once per step, twice with six planes (one launch per
+    triple); in 3D a step is two slices launches (one per triple) and the
+    column launch."""
+    nx, ny = 128, 40
+    n = inputs.random_medium(nx, ny, seed=1, lo=1.0, hi=3.0)
+    q0 = inputs.random_state(nx, ny, seed=2)
+    for te, per_step in ((True, 1), (False, 2)):
+        q = q0.copy()
+        if te:
+            q[[0, 1, 5]] = 0.0
+        with qla.Grid(nx, ny, 0.8, "fp64", te_only=te, double_single=True) as g:
+            g.set_medium(n)
+            g.set_state(q)
+            before = g.launches
+            g.step(5)
+            assert g.launches - before == 2 + 5 * per_step, te
+    nz = 16
+    n3 = np.ones((nz, ny, nx))
+    with qla.Grid3(nx, ny, nz, 0.9, "fp64", double_single=True) as g3:
+        g3.set_medium(n3)
+        g3.set_packet(x0=30.0, y0=20.0, angle=0.0, k0=0.3, width=6.0)
+        before = g3.launches
+        g3.step(4)
+        assert g3.launches - before == 2 + 4 * 3
+
+
 def test_split_calls_agree_with_one_call():
     # each call converts the state to word pairs and back
     w = inputs.scaled(inputs.ellipse_256(), 128, 128, 60)
