@@ -370,6 +370,34 @@ def test_packet_plane_wave_relation_and_envelope():
     assert q[2, 0, int(64.0 / d)] == pytest.approx(1.7, rel=1e-15)
 
 
+def test_fields_satisfy_the_energy_density_and_plane_wave_relations():
+    """The fields read-out inverts the Dyson map of Eq. 3b3.  Pinned by two
+    facts that do not restate it: the energy density n_x^2 E_x^2 + n_y^2 E_y^2
+    + n_z^2 E_z^2 + |B|^2 equals the sum of q_c^2 at every site (Eq. A13) in
+    a medium with three different indices (an E component divided by the
+    wrong index, or not at all, fails), and a packet in a uniform medium
+    carries the plane-wave field B = n k x E with its printed amplitude as
+    the peak of E_z (a sign, a missing n or a swapped B component fails)."""
+    rng = np.random.default_rng(5)
+    ny, nx = 9, 12
+    nt = rng.uniform(1.0, 3.0, size=(3, ny, nx))
+    q = rng.standard_normal((6, ny, nx))
+    f = oracle.fields(q, nt)
+    density = (nt[0] * f[0]) ** 2 + (nt[1] * f[1]) ** 2 + (nt[2] * f[2]) ** 2 + (f[3:] ** 2).sum(0)
+    assert np.allclose(density, (q ** 2).sum(0), rtol=1e-14, atol=0)
+    nv = 1.7
+    n = np.full((4, 512), nv)
+    for ang in (0.0, 0.7, 2.5):
+        qp = oracle.packet(n, 0.25, 64.0, 0.5, ang, 0.4, 6.0, amplitude=0.8)
+        e = oracle.fields(qp, n)
+        ez = e[2]
+        assert np.allclose(e[3], nv * math.sin(ang) * ez, atol=1e-14)
+        assert np.allclose(e[4], -nv * math.cos(ang) * ez, atol=1e-14)
+        assert not np.any(e[[0, 1, 5]])
+    q0 = oracle.packet(n, 0.25, 64.0, 0.0, 0.0, 0.0, 6.0, amplitude=0.8)
+    assert oracle.fields(q0, n)[2, 0, int(64.0 / 0.25)] == pytest.approx(0.8, rel=1e-15)
+
+
 def fresnel_R(theta, n1, n2):
     """Eq. fresn: s-polarised reflectance, T = 1 - R."""
     root = np.real(np.sqrt((n2 ** 2 - n1 ** 2 * np.sin(theta) ** 2).astype(complex)))
