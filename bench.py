@@ -561,7 +561,7 @@ def surrogate_arm(args):
     """Learned surrogate on 256^2 lattices: train on windows from the
     library's own runs, then advance 64 chained windows of K = 32 steps on
     held-out lattices with the energy / div B checks and QLA fallback, and
-    compare time and final state with plain GPU QLA (the judge)."""
+    compare time and final state with plain GPU QLA (the reference run)."""
     import numpy as np
     import torch
 

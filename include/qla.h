@@ -335,7 +335,7 @@ void qla_batch_destroy(qla_batch *b);
  * Learned surrogate.  Not part of the paper's method: a convolutional
  * operator that advances an FP32 E_z lattice (rotation reading) K steps at
  * once, trained on trajectories this library computes, with plain QLA as
- * the fallback and judge.  Network: five levels of widths 32, 64, 128, 256,
+ * the fallback and arbiter.  Network: five levels of widths 32, 64, 128, 256,
  * 256; 3x3 periodic convolutions, leaky ReLU 0.1, 2x2 average pooling,
  * nearest 2x upsampling with additive skips; BF16 weights and activations,
  * FP32 accumulation on the tensor cores, FP32 master weights and Adam.

@@ -418,7 +418,7 @@ void orc_V(int nx, int ny, double *q, const double *beta_x,
 }
 
 /* ------------------------------------------------------------------ */
-/* Full step (Eq. 2e14) and driver                                    */
+/* Full step (Eq. 2e14) and the run loop                              */
 /* ------------------------------------------------------------------ */
 
 void orc_step(int nx, int ny, double *q, const double *theta,

@@ -1,5 +1,5 @@
 // C ABI of libqla (declared in include/qla.h): argument checking, the
-// workspace layout, host <-> device copies and the step driver.
+// workspace layout, host <-> device copies and the step loop.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>

@@ -1,7 +1,7 @@
 // The learned surrogate: a five-level convolutional operator that maps the
 // E_z state and the medium of a lattice to the state K steps later, trained
-// on trajectories the library computes, and the driver that uses it with
-// plain QLA as fallback and judge (declared in qla.h, surr_*).
+// on trajectories the library computes, and the routine that uses it with
+// plain QLA as fallback and arbiter (declared in qla.h, surr_*).
 //
 // Network (widths 32, 64, 128, 256, 256; 3x3 periodic convolutions, leaky
 // ReLU 0.1, 2x2 average pooling down, nearest 2x upsampling up, additive
@@ -347,7 +347,7 @@ qla_status check_batch(surr_net *n, int B) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Lattice side: features, candidate checks, the fallback driver.
+// Lattice side: features, candidate checks, the window loop with fallback.
 // ---------------------------------------------------------------------------
 namespace {
 

@@ -3,7 +3,7 @@
 A five-level convolutional operator advances an FP32 E_z lattice K steps at
 once; it is trained on windows that the library's own batched QLA runs
 produce, with the library's BF16 tensor-core kernels; plain QLA stays the
-fallback and the judge (``Surrogate.advance``).  This module only marshals
+fallback and the arbiter (``Surrogate.advance``).  This module only marshals
 arguments and orders the calls; every computation runs in libqla.
 """
 from __future__ import annotations
