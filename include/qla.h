@@ -496,11 +496,14 @@ qla_status qla3_set_step_kernel(qla3_ctx *ctx, int kernel);
  * without medium and state, QLA_ENONFINITE if a term is not finite. */
 qla_status qla3_divergence(qla3_ctx *ctx, double *out);
 
+/* Kernel launches enqueued by this context since creation (diagnostics; a
+ * double-single step counts its per-triple slices launches separately). */
 long long qla3_launch_count(const qla3_ctx *ctx);
 const char *qla3_last_error(const qla3_ctx *ctx);
 void qla3_destroy(qla3_ctx *ctx);
 
-/* Kernel launches enqueued by this context since creation (diagnostics). */
+/* Kernel launches enqueued by this context since creation (diagnostics; a
+ * six-plane double-single step is two launches, one per decoupled triple). */
 long long qla_launch_count(const qla_ctx *ctx);
 
 /* Text of the last error on this context ("" if none); valid until the next
