@@ -60,3 +60,24 @@ def test_clock_parser():
     assert rec["sm_mhz"] == 2010 and rec["sm_max_mhz"] == 2070 and rec["samples"] == 3
     assert rec["reasons"] == ["sw_power_cap"]
     assert bench.ClockSampler.parse("") is None
+
+
+def test_roofline_instruction_counts_follow_the_rotation_forms():
+    """Per site-update: 16 collision and 2 potential rotations per live pair
+    (1 pair in E_z mode, 2 with six planes).  FP32 collisions take 8
+    instructions (two-word coefficients), potential rotations 6; FP64
+    collisions 3 (three shears), potential rotations 4; double-single rows 23
+    per output.  3D: per axis 16 collision rotations on 2 pairs, then six
+    potential rotations."""
+    assert bench.alu_ops_per_su(3, 4) == 16 * 8 + 2 * 6
+    assert bench.alu_ops_per_su(6, 4) == 2 * (16 * 8 + 2 * 6)
+    assert bench.alu_ops_per_su(3, 8) == 16 * 3 + 2 * 4
+    assert bench.alu_ops_per_su(6, 8) == 2 * (16 * 3 + 2 * 4)
+    assert bench.ds_ops_per_su(3) == 18 * 2 * 23
+    assert bench.alu_ops_per_su_3d(4) == 3 * 16 * 8 + 6 * 6
+    assert bench.alu_ops_per_su_3d(8) == 3 * 16 * 3 + 6 * 4
+    r = bench.roofline(3, 8, 8.6e9, None)
+    assert r["bound"] == "alu" and r["ops_per_site_update"] == 56
+    assert r["frac"] == pytest.approx(8.6e9 * 56 / bench.FP64_INST_PEAK)
+    r = bench.roofline(3, 4, 1.26e11, None)
+    assert r["bound"] == "hbm" and r["bytes_per_site_update"] == 24
