@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+from golden.paper_values import load as paper_values
 from paper_2604_21128_gb300 import inputs
 
 NX, NY = 8, 8
@@ -187,6 +188,37 @@ def test_rotation_reading_is_orthogonal_and_literal_is_not():
     assert np.max(np.abs(M.T @ M - np.eye(6 * N))) < 1e-13
     L = assemble_step(n, 1.0, "literal")
     assert np.max(np.abs(L.T @ L - np.eye(6 * N))) > 1e-3
+
+
+def test_printed_operator_count_sixteen_unitary_of_eighteen():
+    """Sec. VII counts the operators of one step as 18, of which 16 are
+    unitary.  With Eqs. 2e6 and 2e9 read as the assembly above (eight
+    collisions C or C-dagger per direction, streams aside) and Eqs. 2e11,
+    2e12 as printed, the step has 16 collision factors, all orthogonal, and
+    two potential factors that are not; the rotation reading of V makes all
+    18 orthogonal."""
+    pv = paper_values()
+    n = inputs.random_medium(NX, NY, seed=9, lo=1.0, hi=3.0, smooth=1)
+    a = {k: v.ravel() for k, v in tensor_angles((n, n, n), 1.0).items()}
+    Cx = local_op([Cx_matrix(a["t1"][k], a["t2"][k]) for k in range(N)])
+    Cy = local_op([Cy_matrix(a["t0"][k], a["t2"][k]) for k in range(N)])
+    collisions = [Cx, Cx.T] * 4 + [Cy, Cy.T] * 4
+    printed_v = [local_op([Vx_literal(a["b0"][k], a["b2"][k]) for k in range(N)]),
+                 local_op([Vy_literal(a["b1"][k], a["b3"][k]) for k in range(N)])]
+    rotation_v = [local_op([Vx_rotation(a["b0"][k], a["b2"][k]) for k in range(N)]),
+                  local_op([Vy_rotation(a["b1"][k], a["b3"][k]) for k in range(N)])]
+
+    def orthogonal(M):
+        return np.max(np.abs(M.T @ M - np.eye(M.shape[0]))) < 1e-13
+
+    factors = collisions + printed_v
+    assert len(factors) == pv["operators_per_step"]
+    assert sum(orthogonal(M) for M in factors) == pv["unitary_operators_per_step"]
+    assert all(orthogonal(M) for M in collisions + rotation_v)
+    # and the step these factors make is the oracle's (Eq. 2e14)
+    q = inputs.random_state(NX, NY, seed=13)
+    want = (assemble_step(n, 1.0, "literal") @ q.ravel()).reshape(q.shape)
+    assert np.max(np.abs(oracle.run(q, n, 1.0, 1, "literal") - want)) < 1e-13
 
 
 def test_U_alone_matches_product_and_reach():

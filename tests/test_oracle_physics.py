@@ -7,12 +7,12 @@ shift in the wrong direction or a wrong angle in the oracle fails at least
 one of them (the generator fit fails for any error in a single coupling).
 """
 import math
-import os
 
 import numpy as np
 import pytest
 
 import oracle
+from golden.paper_values import load as paper_values
 from paper_2604_21128_gb300 import inputs
 
 oracle.set_threads(min(8, max(1, __import__("os").cpu_count() or 1)))
@@ -402,19 +402,6 @@ def fresnel_R(theta, n1, n2):
     """Eq. fresn: s-polarised reflectance, T = 1 - R."""
     root = np.real(np.sqrt((n2 ** 2 - n1 ** 2 * np.sin(theta) ** 2).astype(complex)))
     return ((n1 * np.cos(theta) - root) / (n1 * np.cos(theta) + root)) ** 2
-
-
-def paper_values():
-    """The printed values of tests/golden/paper_values.txt (cited there)."""
-    path = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
-    vals = {}
-    with open(path) as f:
-        for line in f:
-            line = line.strip()
-            if line and not line.startswith("#"):
-                k, v = line.split("=")
-                vals[k.strip()] = float(v)
-    return vals
 
 
 def test_fresnel_angles_printed_in_the_paper():
