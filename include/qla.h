@@ -92,7 +92,9 @@ enum {
      * FP64 kernels by rounding only (relative L2 ~1e-13 after 400 steps).
      * Not part of Eq. 2e14: an arithmetic for GPUs whose FP32 pipes are
      * much faster than their FP64 pipe.  Needs QLA_FP64, a lattice the
-     * marching kernel takes (nx even, nx >= 64, ny >= 8), a scalar medium and
+     * marching kernel takes (nx even, nx >= 64, ny >= 8, and the live planes
+     * x ny x the padded row length (nx rounded up to 32) at most 2^32, the
+     * kernel's 32-bit element offsets), a scalar medium and
      * the rotation or no-potential reading; QLA_EINVAL otherwise.  The
      * workspace gains a table of double-single coefficient records. */
     QLA_DOUBLE_SINGLE = 32u
@@ -276,7 +278,9 @@ size_t qla_batch_workspace_bytes(int count, const int *nx, const int *ny, int pr
                                  unsigned flags);
 
 /* Create a batch of `count` >= 1 lattices; every nx[k] must be a multiple
- * of 4 and >= 128, every ny[k] >= 8 (the marching kernel's requirements).
+ * of 4 and >= 128, every ny[k] >= 8, and the live planes (3 with
+ * QLA_TE_ONLY, else 6) x ny[k] x nx[k] rounded up to 32 at most 2^32 (the
+ * marching kernel's requirements: 32-bit element offsets).
  * workspace / workspace_bytes / cuda_stream as for qla_init_grid. */
 qla_status qla_batch_create(qla_batch **out, int count, const int *nx, const int *ny,
                             double delta, int precision, unsigned flags, void *cuda_stream,

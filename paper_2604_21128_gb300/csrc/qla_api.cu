@@ -8,10 +8,17 @@
 #include <vector>
 
 #include "qla_internal.h"
+#include "qla_limits.h"
 
 namespace qla {
 
 static size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// The marching kernel takes the lattice and its 32-bit offsets reach every
+// live plane.
+static bool march_ok(const qla_ctx *c) {
+    return march_supported(c) && offsets32_ok(size_t(c->P), c->plane_elems);
+}
 
 Layout layout_for(int nx, int ny, int prec, unsigned flags) {
     Layout L{};
@@ -114,7 +121,8 @@ size_t qla_workspace_bytes(int nx, int ny, int precision, unsigned flags) {
     if ((flags & QLA_DOUBLE_SINGLE) &&
         (precision != QLA_FP64 ||
          (flags & (QLA_ANISOTROPIC | QLA_POTENTIAL_LITERAL | QLA_POTENTIAL_LCU)) ||
-         !ds_shape_ok(nx, ny)))
+         !ds_shape_ok(nx, ny) ||
+         !offsets32_ok((flags & QLA_TE_ONLY) ? 3 : 6, padded_plane(nx, ny))))
         return 0;
     return layout_for(nx, ny, precision, flags).total;
 }
@@ -136,7 +144,8 @@ qla_status qla_init_grid(qla_ctx **out, int nx, int ny, double delta, int precis
     if ((flags & QLA_DOUBLE_SINGLE) &&
         (precision != QLA_FP64 || (flags & (QLA_ANISOTROPIC | QLA_POTENTIAL_LITERAL |
                                             QLA_POTENTIAL_LCU)) ||
-         !ds_shape_ok(nx, ny)))
+         !ds_shape_ok(nx, ny) ||
+         !offsets32_ok((flags & QLA_TE_ONLY) ? 3 : 6, padded_plane(nx, ny))))
         return QLA_EINVAL;
     if (size_t(nx) * size_t(ny) > (size_t(1) << 34)) return QLA_EINVAL;
     if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255)) return QLA_EINVAL;
@@ -389,7 +398,7 @@ qla_status qla_step(qla_ctx *c, long long n_steps) {
         return QLA_OK;
     }
     const bool march = c->step_kernel == QLA_KERNEL_MARCH ||
-                       (c->step_kernel == QLA_KERNEL_AUTO && march_supported(c));
+                       (c->step_kernel == QLA_KERNEL_AUTO && march_ok(c));
     for (long long k = 0; k < n_steps; ++k) {
         const bool vin = c->pending_v;
         QLA_CUDA(c, march ? launch_step_march(c, c->state[c->cur], c->state[c->cur ^ 1], vin)
@@ -498,7 +507,7 @@ qla_status qla_set_step_kernel(qla_ctx *c, int kernel) {
     if (kernel == QLA_KERNEL_MARCH && ((c->tensor && c->P == 6) || c->vmode == V_LCU))
         return fail(c, QLA_EINVAL, "qla_set_step_kernel: six-plane tensor media and the LCU "
                                    "potential use the tile kernel");
-    if (kernel == QLA_KERNEL_MARCH && !march_supported(c))
+    if (kernel == QLA_KERNEL_MARCH && !march_ok(c))
         return fail(c, QLA_EINVAL, "qla_set_step_kernel: the marching kernel needs nx a multiple "
                                    "of its lane width, nx >= 32 lane widths and ny >= 8");
     c->step_kernel = kernel;

@@ -19,6 +19,7 @@
 #include <string>
 #include <vector>
 
+#include "qla_limits.h"
 #include "qla_march.cuh"
 
 namespace qla {
@@ -219,7 +220,10 @@ qla_status bfail(qla_batch *b, qla_status s, const char *fmt, ...) {
             return bfail((b), QLA_ECUDA, "%s: %s", (what), cudaGetErrorString(e_)); \
     } while (0)
 
-bool lattice_ok(int nx, int ny) { return nx >= 128 && nx % 4 == 0 && ny >= 8; }
+bool lattice_ok(int nx, int ny, int planes) {
+    return nx >= 128 && nx % 4 == 0 && ny >= 8 &&
+           offsets32_ok(size_t(planes), padded_plane(nx, ny));
+}
 
 size_t tail_bytes(int count, const int *nx, const int *ny) {
     size_t items = 0;
@@ -441,7 +445,7 @@ size_t qla_batch_workspace_bytes(int count, const int *nx, const int *ny, int pr
     if (flags & (QLA_ANISOTROPIC | QLA_POTENTIAL_LCU)) return 0;  // single contexts only
     size_t total = 0;
     for (int k = 0; k < count; ++k) {
-        if (!lattice_ok(nx[k], ny[k])) return 0;
+        if (!lattice_ok(nx[k], ny[k], (flags & QLA_TE_ONLY) ? 3 : 6)) return 0;
         const size_t b = qla_workspace_bytes(nx[k], ny[k], precision, flags);
         if (b == 0) return 0;
         total += align256(b);

@@ -5,6 +5,7 @@ import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2604_21128_gb300 import build as qbuild
@@ -75,6 +76,26 @@ def test_double_single_workspace_host_only(lib):
                                 (256, 64, qla.QLA_FP64, ds | qla.QLA_POTENTIAL_LITERAL),
                                 (256, 64, qla.QLA_FP64, ds | qla.QLA_ANISOTROPIC)]:
         assert qla.qla_workspace_bytes(nx, ny, prec, flags) == 0, (nx, ny, prec, flags)
+
+
+def test_lattices_past_the_32_bit_offsets_are_refused_host_only(lib):
+    """The marching kernels address planes x ny x pitch elements with 32-bit
+    offsets: 32768 x 27000 fits with three live planes, not with six."""
+    nx, ny = 32768, 27000
+    assert 3 * ny * nx <= 2 ** 32 < 6 * ny * nx
+    ds = qla.QLA_DOUBLE_SINGLE
+    assert qla.qla_workspace_bytes(nx, ny, qla.QLA_FP64, qla.QLA_TE_ONLY | ds) > 0
+    assert qla.qla_workspace_bytes(nx, ny, qla.QLA_FP64, ds) == 0
+    # plain contexts stay valid (lattices the marching kernel declines step
+    # on the tile kernel, whose offsets are 64-bit)
+    assert qla.qla_workspace_bytes(nx, ny, qla.QLA_FP32, 0) > 0
+    lib_ = qla.load()
+    one = lambda v: np.array([v], dtype=np.int32)
+    nxa, nya = one(nx), one(ny)
+    wb = lambda flags: int(lib_.qla_batch_workspace_bytes(
+        1, ctypes.c_void_p(nxa.ctypes.data), ctypes.c_void_p(nya.ctypes.data), qla.QLA_FP32, flags))
+    assert wb(qla.QLA_TE_ONLY) > 0
+    assert wb(0) == 0
 
 
 @pytest.mark.parametrize("args", [
