@@ -210,7 +210,8 @@ qla_status qla_probe(qla_ctx *ctx, int count, const int *i, const int *j, double
  * see qla_set_march_tuning), nx >= 32 times that count and ny >= 8, and the
  * shared-memory tile kernel otherwise.  QLA_KERNEL_TILE / QLA_KERNEL_MARCH
  * force one (QLA_EINVAL if the marching kernel does not support the
- * lattice).  Both compute the same operator sequence; FP64 results agree to
+ * lattice, including one whose live planes exceed its 32-bit element
+ * offsets: planes x ny x padded nx > 2^32).  Both compute the same operator sequence; FP64 results agree to
  * rounding order. */
 typedef enum { QLA_KERNEL_AUTO = 0, QLA_KERNEL_TILE = 1, QLA_KERNEL_MARCH = 2 } qla_step_kernel;
 qla_status qla_set_step_kernel(qla_ctx *ctx, int kernel);
@@ -397,7 +398,11 @@ qla_status surr_features(qla_ctx *ctx, float *feat_dev);
 qla_status surr_advance(qla_ctx *ctx, surr_net *n, int windows, int K, double energy_tol,
                         double div_tol, float *scratch_dev, int *accepted, double *energies);
 
+/* Text of the last error on this network ("" if none); valid until the
+ * next call on it. */
 const char *surr_last_error(const surr_net *n);
+/* Wait for the network's stream, then free its host-side handle; the
+ * device workspace stays the caller's. */
 void surr_destroy(surr_net *n);
 
 /* The network's two contraction kernels on their own (device pointers,
@@ -503,7 +508,10 @@ qla_status qla3_divergence(qla3_ctx *ctx, double *out);
 /* Kernel launches enqueued by this context since creation (diagnostics; a
  * double-single step counts its per-triple slices launches separately). */
 long long qla3_launch_count(const qla3_ctx *ctx);
+/* Text of the last error on this context ("" if none); valid until the next
+ * call on the context. */
 const char *qla3_last_error(const qla3_ctx *ctx);
+/* Free the context (and its workspace if the library allocated it). */
 void qla3_destroy(qla3_ctx *ctx);
 
 /* Kernel launches enqueued by this context since creation (diagnostics; a
