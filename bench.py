@@ -3,11 +3,13 @@
 
 One bench step = ``--qla-steps`` (default 100) time steps of the whole lattice
 followed by the FP64 energy reduction (Eq. A13) read back to the host, the
-monitoring cadence of the 8192^2 workload.  Default workload: 8192 x 8192
-periodic lattice, unit spacing, rotated dielectric ellipse (n_in = 2, semi-axes
-1200 x 600, 30 degrees, tanh edge 8) in vacuum, E_z packet k0 = 0.2, width 300;
-FP32 storage and arithmetic, E_z polarisation (q2, q3, q4 live), 200 bench
-steps = the workload's 20000 time steps.
+monitoring cadence of the 8192^2 workload.  Default workload: the largest
+single-GPU lattice, 16384 x 16384 periodic, unit spacing, an elliptical vacuum
+bubble (n = 1, semi-axes 2400 x 1200, tanh edge 8) in a uniform dielectric
+n = 2, E_z packet k0 = 0.2, width 600 launched inside the dielectric; FP32
+storage and arithmetic, E_z polarisation (q2, q3, q4 live).  The default 200
+bench steps are the workload's 20000 time steps.  ``--workload ellipse_8192``
+selects the 8192^2 rotated-ellipse lattice.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the plain CPU
 oracle on the host cores instead (bounded samples of the same workload).
@@ -37,7 +39,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
-    ap.add_argument("--workload", default="ellipse_8192")
+    ap.add_argument("--workload", default="bubble_16384")
     ap.add_argument("--qla-steps", type=int, default=100)
     ap.add_argument("--lane-cols", type=int, default=0, help="marching kernel tuning")
     ap.add_argument("--rows", type=int, default=0, help="marching kernel tuning")
@@ -76,11 +78,60 @@ def peaks():
 # a collision rotation with two-word coefficients is 8 FP32 instructions
 # (4 per output), a potential rotation 6; FP64: a collision rotation is 3
 # (three shears), a potential rotation 4.
-# Peaks from the unit counts and the maximum clock: 152 SMs x 128 FP32 lanes
-# x 2.07 GHz for FP32 instructions; the nominal 1.25 TFLOP/s FP64 rate
-# counted as FMA-class instructions (2 flops each) for FP64.
-FP32_INST_PEAK = 152 * 128 * 2.07e9
-FP64_INST_PEAK = 1.25e12 / 2
+# Peaks: FP32 instructions from the unit counts of the device in use (its SM
+# count x 128 FP32 lanes x its maximum SM clock); FP64 from the datasheet's
+# nominal 1.25 TFLOP/s counted as FMA-class instructions (2 flops each), not
+# a measured rate.
+FP32_LANES_PER_SM = 128
+FP64_NOMINAL_FLOPS = 1.25e12
+DEVICE = {"sms": None, "sm_max_mhz": None}
+
+
+def device_info(dev=None):
+    """SM count (from the device) and maximum SM clock (nvidia-smi, else
+    MEASURED_PEAKS.json, else the GB300 figure of 2070 MHz)."""
+    import torch
+    if dev is not None:
+        DEVICE["sms"] = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = None
+        try:
+            out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm",
+                                  "--format=csv,noheader,nounits", "-i", str(dev.index or 0)],
+                                 capture_output=True, text=True, timeout=20).stdout
+            mhz = float(out.strip().splitlines()[0])
+        except Exception:
+            try:
+                with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                    mhz = float(json.load(f)["sm_max_mhz"])
+            except Exception:
+                mhz = 2070.0
+        DEVICE["sm_max_mhz"] = mhz
+    return DEVICE
+
+
+def fp32_inst_peak():
+    d = DEVICE
+    return d["sms"] * FP32_LANES_PER_SM * d["sm_max_mhz"] * 1e6
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def alu_ops_per_su(P, elt):
@@ -112,7 +163,7 @@ def roofline(P, elt, su_per_s, traffic, ops=None, pipe=None, **extra):
     arithmetic pipe ("fp32" for double-single steps on FP64 state)."""
     ops = alu_ops_per_su(P, elt) if ops is None else ops
     pipe = pipe or ("fp32" if elt == 4 else "fp64")
-    peak_ops = FP32_INST_PEAK if pipe == "fp32" else FP64_INST_PEAK
+    peak_ops = fp32_inst_peak() if pipe == "fp32" else FP64_NOMINAL_FLOPS / 2
     hbm_peak, hbm_kind = peaks()
     bytes_su = 2 * P * elt
     hbm = {"achieved": bytes_su * su_per_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
@@ -121,8 +172,11 @@ def roofline(P, elt, su_per_s, traffic, ops=None, pipe=None, **extra):
     alu = {"achieved": ops * su_per_s / 1e12, "peak": peak_ops / 1e12,
            "unit": "T%s-inst/s" % pipe.upper(),
            "frac": ops * su_per_s / peak_ops,
-           "peak_kind": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2.07 GHz" if pipe == "fp32"
-                                         else "nominal 1.25 TFLOP/s FP64 / 2 flops per FMA"),
+           "peak_kind": ("derived: %d SMs x %d FP32 lanes x %.0f MHz (device query)"
+                         % (DEVICE["sms"], FP32_LANES_PER_SM, DEVICE["sm_max_mhz"])
+                         if pipe == "fp32" else
+                         "nominal (not measured): 1.25 TFLOP/s FP64 datasheet rate / 2 flops "
+                         "per FMA"),
            "ops_per_site_update": ops}
     ceil = {"hbm": hbm_peak * 1e9 / bytes_su, "alu": peak_ops / ops}
     bound = "hbm" if ceil["hbm"] <= ceil["alu"] else "alu"
@@ -279,7 +333,7 @@ def reference_arm(args):
                        + ("_6planes" if args.six_planes else "_ez"),
                        "nx": w.nx, "ny": w.ny, "delta": w.delta, "sample": sample},
             "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": threads,
-                             "kind": "oracle", "sample": sample},
+                             "cpu_model": cpu_model(), "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -323,6 +377,7 @@ def gpu_arm(args):
     if world == 1:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
+    device_info(dev)
     qbuild.build()
     w = workload(args.workload)
     te = not args.six_planes
@@ -397,7 +452,8 @@ def gpu_arm(args):
     if not args.no_cpu and rank == 0 and world == 1:
         side, nst = 4096, 15
         v, dt, threads = oracle_sample(w, n_host.numpy(), side, nst)
-        cpu = {"value": v, "unit": "site-updates/s", "cores": threads, "kind": "oracle",
+        cpu = {"value": v, "unit": "site-updates/s", "cores": threads,
+               "cpu_model": cpu_model(), "kind": "oracle",
                "sample": "%d x %d crop of the %s workload, %d steps (%.1f s), plain FP64 "
                          "CPU oracle, OpenMP over rows" % (side, side, w.name, nst, dt)}
         # the same oracle on one thread, and the 256^2 parity workload run in full
@@ -494,6 +550,7 @@ def batch_arm(args):
     if world == 1:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
+    device_info(dev)
     qbuild.build()
     ws = inputs.batch_instances()
     sizes = [(w.nx, w.ny) for w in ws]
@@ -662,6 +719,7 @@ def cube_arm(args):
     world, rank, local = dist_setup()
     if world == 1:
         torch.cuda.set_device(0)
+    device_info(torch.device("cuda", torch.cuda.current_device()))
     qbuild.build()
     w = inputs.cube_256()
     N, d = w["n"], w["delta"]
@@ -725,6 +783,7 @@ def cube_arm(args):
         oracle.run3(qw, nw, d, nst)
         dt = time.perf_counter() - t0
         cpu = {"value": side ** 3 * nst / dt, "unit": "site-updates/s", "cores": threads,
+               "cpu_model": cpu_model(),
                "kind": "oracle",
                "sample": "%d^3 corner of the cube_256 workload (periodic), %d steps (%.1f s), "
                          "plain FP64 CPU oracle" % (side, nst, dt)}

@@ -117,7 +117,9 @@ typedef struct {
  * reduction scratch).  0 for invalid arguments. */
 size_t qla_workspace_bytes(int nx, int ny, int precision, unsigned flags);
 
-/* Create a context.  nx, ny >= 1; delta > 0 and finite; precision is a
+/* Create a context.  nx, ny >= 1 with nx * ny + 4096 < 2^32 (per-site
+ * record indices are 32-bit; larger lattices give QLA_EINVAL, and 0 from
+ * qla_workspace_bytes); delta > 0 and finite; precision is a
  * qla_precision; cuda_stream is a cudaStream_t (NULL = legacy default
  * stream) on the current device.  workspace: device memory of at least
  * qla_workspace_bytes() bytes, 256-byte aligned, owned by the caller and
@@ -248,7 +250,9 @@ qla_status qla_set_step_kernel(qla_ctx *ctx, int kernel);
  * any stream capture.  The result is bitwise reproducible for a given size
  * and agrees with qla_energy to rounding order.
  * Errors: QLA_EINVAL for a null pointer or a bad size/precision/stride,
- * QLA_ECUDA if the lookup or a launch fails. */
+ * QLA_ECUDA if the lookup or a launch fails, or if a CUDA error of earlier
+ * work on this thread is still pending when the call starts (nothing is
+ * launched then, and that error is left in place for its owner to read). */
 #define QLA_NOALLOC_MAX_PARTIALS 16384
 #define QLA_NOALLOC_SITES_PER_PARTIAL 16384
 qla_status qla_energy_noalloc(const void *planes, int precision, int n_planes, int nx,

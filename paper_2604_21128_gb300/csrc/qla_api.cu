@@ -117,7 +117,7 @@ extern "C" {
 
 size_t qla_workspace_bytes(int nx, int ny, int precision, unsigned flags) {
     if (nx < 1 || ny < 1 || (precision != QLA_FP64 && precision != QLA_FP32)) return 0;
-    if (size_t(nx) * size_t(ny) > (size_t(1) << 34)) return 0;
+    if (!record_ids_ok(size_t(nx) * size_t(ny), UNIFORM_SLOTS)) return 0;
     if ((flags & QLA_DOUBLE_SINGLE) &&
         (precision != QLA_FP64 ||
          (flags & (QLA_ANISOTROPIC | QLA_POTENTIAL_LITERAL | QLA_POTENTIAL_LCU)) ||
@@ -147,7 +147,7 @@ qla_status qla_init_grid(qla_ctx **out, int nx, int ny, double delta, int precis
          !ds_shape_ok(nx, ny) ||
          !offsets32_ok((flags & QLA_TE_ONLY) ? 3 : 6, padded_plane(nx, ny))))
         return QLA_EINVAL;
-    if (size_t(nx) * size_t(ny) > (size_t(1) << 34)) return QLA_EINVAL;
+    if (!record_ids_ok(size_t(nx) * size_t(ny), UNIFORM_SLOTS)) return QLA_EINVAL;
     if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255)) return QLA_EINVAL;
 
     qla_ctx *c = new (std::nothrow) qla_ctx();

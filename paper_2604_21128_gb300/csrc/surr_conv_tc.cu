@@ -18,8 +18,12 @@
 // loads one halo'd row patch per chunk that serves all nine taps and keeps
 // the weights resident in persistent CTAs.
 //
-// Every wait on an mbarrier has an iteration limit; a CTA that gives up sets
-// conv_tc_error, skips its epilogue, frees its TMEM and returns.
+// Every wait on an mbarrier gives up after WAIT_NS of %globaltimer time; a CTA
+// that gives up sets conv_tc_error, skips its epilogue, frees its TMEM and
+// returns.  After such a timeout the launch's outputs are undefined, and so is
+// the TMEM it freed if the wait that ran out was on MMAs still in flight (a
+// genuine hang of the tensor pipe rather than a phase that never comes): the
+// caller should rebuild the network before trusting another result.
 #include <cuda.h>
 
 #include "surr_internal.h"
@@ -662,6 +666,15 @@ cudaError_t launch_nt(const ConvArgs &a, long long mtiles, cudaStream_t st) {
                            : launch_ks<NT, 32, MODE, ACT, SKIP>(a, mtiles, st);
 }
 
+// Streaming multiprocessors of the current device (1 if the query fails).
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+        return 1;
+    return n;
+}
+
 template <int MODE, bool ACT, bool SKIP>
 cudaError_t conv_tc_t(const ConvArgs &a, cudaStream_t st) {
     const long long P = (long long)a.B * a.H * a.W;
@@ -680,8 +693,9 @@ cudaError_t conv_tc_t(const ConvArgs &a, cudaStream_t st) {
         }
     }
     // the widest N tile that divides cout and still gives about one CTA per SM
+    const long long sms = sm_count();
     int nt = 256;
-    while (nt > 32 && (a.cout % nt != 0 || mtiles * (a.cout / nt) < 152)) nt >>= 1;
+    while (nt > 32 && (a.cout % nt != 0 || mtiles * (a.cout / nt) < sms)) nt >>= 1;
     switch (nt) {
     case 256: return launch_nt<256, MODE, ACT, SKIP>(a, mtiles, st);
     case 128: return launch_nt<128, MODE, ACT, SKIP>(a, mtiles, st);

@@ -98,6 +98,18 @@ def test_lattices_past_the_32_bit_offsets_are_refused_host_only(lib):
     assert wb(0) == 0
 
 
+def test_lattices_past_the_32_bit_record_ids_are_refused_host_only(lib):
+    """Per-site record indices are 32-bit (4096 shared slots, then one own
+    record per site), so nx * ny + 4096 must stay below 2^32."""
+    assert 65536 * 65535 + 4096 < 2 ** 32 <= 65536 * 65536 + 4096
+    assert qla.qla_workspace_bytes(65536, 65535, qla.QLA_FP32, qla.QLA_TE_ONLY) > 0
+    assert qla.qla_workspace_bytes(65536, 65536, qla.QLA_FP32, qla.QLA_TE_ONLY) == 0
+    assert qla.qla_workspace_bytes(131072, 32768, qla.QLA_FP32, qla.QLA_TE_ONLY) == 0
+    with pytest.raises(qla.QLAError) as e:
+        qla.qla_init_grid(65536, 65536, 1.0, qla.QLA_FP32, qla.QLA_TE_ONLY, 0, 0, 0)
+    assert e.value.status == 1
+
+
 @pytest.mark.parametrize("args", [
     (0, 4, 1.0, 0, 0), (4, 0, 1.0, 0, 0), (4, 4, 0.0, 0, 0), (4, 4, float("nan"), 0, 0),
     (4, 4, 1.0, 2, 0), (4, 4, 1.0, 0, 64), (4, 4, 1.0, 0, 2 | 4)])

@@ -76,8 +76,16 @@ def test_roofline_instruction_counts_follow_the_rotation_forms():
     assert bench.ds_ops_per_su(3) == 18 * 2 * 23
     assert bench.alu_ops_per_su_3d(4) == 3 * 16 * 8 + 6 * 6
     assert bench.alu_ops_per_su_3d(8) == 3 * 16 * 3 + 6 * 4
+    bench.DEVICE.update(sms=152, sm_max_mhz=2070.0)
     r = bench.roofline(3, 8, 8.6e9, None)
     assert r["bound"] == "alu" and r["ops_per_site_update"] == 56
-    assert r["frac"] == pytest.approx(8.6e9 * 56 / bench.FP64_INST_PEAK)
+    assert r["frac"] == pytest.approx(8.6e9 * 56 / (bench.FP64_NOMINAL_FLOPS / 2))
+    assert r["peak_kind"].startswith("nominal")
+    assert bench.fp32_inst_peak() == pytest.approx(152 * 128 * 2.07e9)
     r = bench.roofline(3, 4, 1.26e11, None)
     assert r["bound"] == "hbm" and r["bytes_per_site_update"] == 24
+
+
+def test_cpu_model_is_named():
+    m = bench.cpu_model()
+    assert isinstance(m, str) and m.strip()
