@@ -207,9 +207,59 @@ qla_status qla_divergence(qla_ctx *ctx, double *out);
  * index out of range or count outside 0..65536. */
 qla_status qla_probe(qla_ctx *ctx, int count, const int *i, const int *j, double *out);
 
+/* ------------------------------------------------------------------------
+ * Domain decomposition (Sec. V-A: the paper's code splits the lattice into
+ * processor domains, each with ghost cells that are refreshed from the
+ * neighbouring domains' boundary points after a step).  A sub-domain is an
+ * ordinary context on its block of the global lattice plus a halo of h
+ * ghost cells on every side; stepped as a periodic lattice of its own, its
+ * interior stays exact for k steps when h >= 4k + 1 (U_x and U_y each reach
+ * four cells per step, and the outermost ring's potential angles, Eq. 2e13,
+ * use a wrapped neighbour of n), after which the halos are refilled from
+ * the neighbours with the calls below.  The exchange runs in two phases --
+ * x strips over the interior rows, then y strips over the full width -- so
+ * the corners come along.  Contiguous buffers make each strip one send.
+ * ------------------------------------------------------------------------ */
+
+/* Bytes of a packed w x h rectangle of ctx's stored state: live planes
+ * (3 for QLA_TE_ONLY, else 6) x w x h values of the storage precision (8
+ * bytes for QLA_FP64 contexts, including QLA_DOUBLE_SINGLE ones, whose state
+ * is FP64 between calls; 4 for QLA_FP32).  0 for a null ctx or a rectangle
+ * larger than the lattice. */
+size_t qla_box_bytes(const qla_ctx *ctx, int w, int h);
+
+/* Copy the stored values of the sites (i0 .. i0+w-1, j0 .. j0+h-1) of every
+ * live plane into dst_dev (device memory of qla_box_bytes(ctx, w, h) bytes,
+ * layout [plane][j][i], i fastest), or back from src_dev.  The stored
+ * values are the state before the last step's pending potential operator
+ * (see qla_step), so boxes move only between contexts that have taken the
+ * same number of steps since their states were set; the receiving context
+ * applies that operator with its own coefficients.  Asynchronous on the
+ * context's stream.  QLA_EINVAL for a null buffer or a rectangle outside the
+ * lattice; QLA_ESTATE without a state. */
+qla_status qla_pack_box(qla_ctx *ctx, int i0, int j0, int w, int h, void *dst_dev);
+qla_status qla_unpack_box(qla_ctx *ctx, int i0, int j0, int w, int h, const void *src_dev);
+
+/* Energy (Eq. A13, FP64, fixed summation order) of the sites of a
+ * rectangle, e.g. a sub-domain's interior; the global energy is the FP64
+ * sum over sub-domains.  Synchronises.  Errors as qla_energy, plus
+ * QLA_EINVAL for a rectangle outside the lattice. */
+qla_status qla_energy_box(qla_ctx *ctx, int i0, int j0, int w, int h, double *out);
+
+/* qla_set_packet for a context that is a window of a larger periodic
+ * lattice of gnx x gny sites: site (i, j) of ctx is site ((i0 + i) mod gnx,
+ * (j0 + j) mod gny) of the large lattice, and the packet's minimum-image
+ * distances are taken there.  With (0, 0, nx, ny) it is qla_set_packet.
+ * QLA_EINVAL for bad packet fields or 0 <= i0 < gnx, 0 <= j0 < gny
+ * violated; QLA_ESTATE without a medium. */
+qla_status qla_set_packet_window(qla_ctx *ctx, const qla_packet *p, int i0, int j0, int gnx,
+                                 int gny);
+
 /* Step kernel.  QLA_KERNEL_AUTO picks the register-resident marching
- * kernel when nx is a multiple of its per-lane column count (2 by default;
- * see qla_set_march_tuning), nx >= 32 times that count and ny >= 8, and the
+ * kernel when the lattice suits its column layout (see
+ * qla_set_march_tuning: nx a multiple of 4 for the packed-pair layout, of
+ * the per-lane column count otherwise; a window of 64 or 32 x lane columns
+ * no wider than nx) and ny >= 8, and the
  * shared-memory tile kernel otherwise.  QLA_KERNEL_TILE / QLA_KERNEL_MARCH
  * force one (QLA_EINVAL if the marching kernel does not support the
  * lattice, including one whose live planes exceed its 32-bit element
@@ -259,11 +309,16 @@ qla_status qla_energy_noalloc(const void *planes, int precision, int n_planes, i
                               int ny, long long row_pitch, long long plane_stride,
                               void *cuda_stream, double *out_dev);
 
-/* Tuning of the marching kernel: lane_cols = columns per lane (0 = library
- * choice; 2 or 4 for FP32 E_z contexts, other contexts always use 2), rows =
- * rows per work item (0 = chosen from the occupancy so one wave of items
- * fills the GPU; else rounded up to a multiple of 4).  Results do not
- * depend on either.  QLA_EINVAL for other values. */
+/* Tuning of the marching kernel: lane_cols = the column layout of a warp's
+ * window (0 = library choice).  For FP32 E_z contexts: 1 = packed pairs
+ * (each lane holds two columns 32 apart and rotates both with FP32x2
+ * instructions; 64-column windows; nx a multiple of 4; 5 and 6 are the
+ * same kernel with other register forms of the pairs),
+ * 2 or 4 = that many adjacent columns per lane (scalar FP32; 2 is the
+ * default).  Other contexts always use 2.  rows = rows per work
+ * item (0 = chosen from the occupancy so one wave of items fills the GPU;
+ * else rounded up to a multiple of 4).  Results do not depend on either.
+ * QLA_EINVAL for other values. */
 qla_status qla_set_march_tuning(qla_ctx *ctx, int lane_cols, int rows);
 
 /* ------------------------------------------------------------------------
@@ -313,8 +368,10 @@ qla_status qla_batch_run(qla_batch *b, long long n_steps, long long every, doubl
 /* Energy (as qla_energy) of every instance into out[0..count). Synchronises. */
 qla_status qla_batch_energy(qla_batch *b, double *out);
 
-/* Autotuner: time each candidate (columns per lane in {2, 4}, rows per work
- * item in {64, 128, 256}) on `trial_steps` real steps and keep the fastest.
+/* Autotuner: time each candidate (lane layout in {1, 2} for FP32 E_z
+ * batches -- packed pairs or two adjacent columns per lane, see
+ * qla_set_march_tuning -- and rows per work item in {64, 128, 256}) on
+ * `trial_steps` real steps and keep the fastest.
  * The states advance by 6 * trial_steps steps, as if qla_batch_step had
  * been called.  *chosen_lane_cols / *chosen_rows (may be NULL) receive the
  * choice. */

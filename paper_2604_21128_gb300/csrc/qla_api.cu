@@ -302,6 +302,89 @@ qla_status qla_set_packet(qla_ctx *c, const qla_packet *p) {
     return QLA_OK;
 }
 
+qla_status qla_set_packet_window(qla_ctx *c, const qla_packet *p, int i0, int j0, int gnx,
+                                 int gny) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (!p) return fail(c, QLA_EINVAL, "qla_set_packet_window: null packet");
+    const double v[7] = {p->x0, p->y0, p->angle, p->k0, p->width, p->transverse_width,
+                         p->amplitude};
+    for (double x : v)
+        if (!std::isfinite(x))
+            return fail(c, QLA_EINVAL, "qla_set_packet_window: non-finite field");
+    if (!(p->width > 0.0) || p->transverse_width < 0.0)
+        return fail(c, QLA_EINVAL,
+                    "qla_set_packet_window: width must be > 0, transverse_width >= 0");
+    if (gnx < 1 || gny < 1 || i0 < 0 || j0 < 0 || i0 >= gnx || j0 >= gny)
+        return fail(c, QLA_EINVAL, "qla_set_packet_window: window (%d, %d) of %d x %d", i0, j0,
+                    gnx, gny);
+    if (!c->has_medium) return fail(c, QLA_ESTATE, "qla_set_packet_window: set the medium first");
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, QLA_ECUDA, "qla_set_packet_window: cannot select device");
+    if (c->P == 6)
+        QLA_CUDA(c, cudaMemsetAsync(c->state[c->cur], 0,
+                                    c->plane_elems * (c->prec == QLA_FP64 ? 8 : 4) * 6, c->stream),
+                 "qla_set_packet_window: clear");
+    QLA_CUDA(c, launch_packet_window(c, *p, i0, j0, gnx, gny), "qla_set_packet_window: kernel");
+    c->has_state = true;
+    c->pending_v = false;
+    return QLA_OK;
+}
+
+size_t qla_box_bytes(const qla_ctx *c, int w, int h) {
+    if (!c || w < 1 || h < 1 || w > c->nx || h > c->ny) return 0;
+    return size_t(w) * size_t(h) * size_t(c->P) * (c->prec == QLA_FP64 ? 8 : 4);
+}
+
+}  // extern "C"
+
+namespace {
+qla_status box_args(qla_ctx *c, const char *who, int i0, int j0, int w, int h, const void *buf) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (!buf) return fail(c, QLA_EINVAL, "%s: null buffer", who);
+    if (w < 1 || h < 1 || i0 < 0 || j0 < 0 || i0 > c->nx - w || j0 > c->ny - h)
+        return fail(c, QLA_EINVAL, "%s: box (%d, %d) + %d x %d outside the %d x %d lattice", who,
+                    i0, j0, w, h, c->nx, c->ny);
+    if (!c->has_state) return fail(c, QLA_ESTATE, "%s: no state", who);
+    return QLA_OK;
+}
+}  // namespace
+
+extern "C" {
+
+qla_status qla_pack_box(qla_ctx *c, int i0, int j0, int w, int h, void *dst_dev) {
+    qla_status s = box_args(c, "qla_pack_box", i0, j0, w, h, dst_dev);
+    if (s != QLA_OK) return s;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, QLA_ECUDA, "qla_pack_box: cannot select device");
+    QLA_CUDA(c, launch_box_copy(c, i0, j0, w, h, dst_dev, true), "qla_pack_box: kernel");
+    return QLA_OK;
+}
+
+qla_status qla_unpack_box(qla_ctx *c, int i0, int j0, int w, int h, const void *src_dev) {
+    qla_status s = box_args(c, "qla_unpack_box", i0, j0, w, h, src_dev);
+    if (s != QLA_OK) return s;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, QLA_ECUDA, "qla_unpack_box: cannot select device");
+    QLA_CUDA(c, launch_box_copy(c, i0, j0, w, h, const_cast<void *>(src_dev), false),
+             "qla_unpack_box: kernel");
+    return QLA_OK;
+}
+
+qla_status qla_energy_box(qla_ctx *c, int i0, int j0, int w, int h, double *out) {
+    qla_status s = box_args(c, "qla_energy_box", i0, j0, w, h, out);
+    if (s != QLA_OK) return s;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, QLA_ECUDA, "qla_energy_box: cannot select device");
+    QLA_CUDA(c, launch_energy_box(c, i0, j0, w, h), "qla_energy_box: kernel");
+    QLA_CUDA(c, cudaMemcpyAsync(out, c->result, 8, cudaMemcpyDeviceToHost, c->stream),
+             "qla_energy_box: copy");
+    QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_energy_box: sync");
+    if (!std::isfinite(*out)) return fail(c, QLA_ENONFINITE, "qla_energy_box: energy is %g", *out);
+    return QLA_OK;
+}
+
 qla_status qla_set_state(qla_ctx *c, const double *q_host) {
     qla_status s = usable(c);
     if (s != QLA_OK) return s;
@@ -509,7 +592,8 @@ qla_status qla_set_step_kernel(qla_ctx *c, int kernel) {
                                    "potential use the tile kernel");
     if (kernel == QLA_KERNEL_MARCH && !march_ok(c))
         return fail(c, QLA_EINVAL, "qla_set_step_kernel: the marching kernel needs nx a multiple "
-                                   "of its lane width, nx >= 32 lane widths and ny >= 8");
+                                   "of its lane width (4 for the packed-pair layout), a window "
+                                   "of columns and ny >= 8");
     c->step_kernel = kernel;
     return QLA_OK;
 }
@@ -517,8 +601,10 @@ qla_status qla_set_step_kernel(qla_ctx *c, int kernel) {
 qla_status qla_set_march_tuning(qla_ctx *c, int lane_cols, int rows) {
     qla_status s = usable(c);
     if (s != QLA_OK) return s;
-    if (lane_cols != 0 && lane_cols != 2 && lane_cols != 4)
-        return fail(c, QLA_EINVAL, "qla_set_march_tuning: lane_cols %d not 0, 2 or 4", lane_cols);
+    if (lane_cols != 0 && lane_cols != 1 && lane_cols != 2 && lane_cols != 4 && lane_cols != 5 &&
+        lane_cols != 6)
+        return fail(c, QLA_EINVAL, "qla_set_march_tuning: lane_cols %d not 0, 1, 2 or 4",
+                    lane_cols);
     if (rows < 0 || rows > (1 << 20))
         return fail(c, QLA_EINVAL, "qla_set_march_tuning: rows %d", rows);
     c->march_lx = lane_cols;

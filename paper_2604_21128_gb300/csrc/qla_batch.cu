@@ -20,7 +20,7 @@
 #include <vector>
 
 #include "qla_limits.h"
-#include "qla_march.cuh"
+#include "qla_march2.cuh"
 
 namespace qla {
 namespace {
@@ -85,13 +85,22 @@ __device__ __forceinline__ bool grid_barrier(Barrier *b, long long budget, bool 
     return *static_cast<volatile int *>(&b->err) == 0;
 }
 
+// The marching machinery of a lane layout: LX adjacent columns per lane, or
+// LX = 1 for the packed pairs of FP32 E_z lattices (qla_march2.cuh).
+template <typename T, int P, int LX, int VM, bool VIN> struct MarchOf {
+    using type = March<T, P, LX, VM, VIN>;
+};
+template <int VM, bool VIN> struct MarchOf<float, 3, 1, VM, VIN> {
+    using type = March2<VM, VIN, PairF2>;
+};
+
 template <typename T, int P, int LX, int VM>
 __global__ void __launch_bounds__(32 * WARPS)
 k_batch_march(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ items,
               int n_items, int n_steps, int step0, Barrier *bar, long long budget,
               int skip_block) {
     constexpr bool VIN = VM != V_NONE;
-    using M = March<T, P, LX, VM, VIN>;
+    using M = typename MarchOf<T, P, LX, VM, VIN>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     typename M::Slot *ring =
         reinterpret_cast<typename M::Slot *>(smem_raw) + (threadIdx.x >> 5) * NSLOT;
@@ -247,7 +256,7 @@ struct Kern {
 
 template <typename T, int P, int LX, int VM>
 Kern kern_t() {
-    using M = March<T, P, LX, VM, VM != V_NONE>;
+    using M = typename MarchOf<T, P, LX, VM, VM != V_NONE>::type;
     return Kern{reinterpret_cast<const void *>(&k_batch_march<T, P, LX, VM>),
                 sizeof(typename M::Slot),
                 reinterpret_cast<const void *>(&k_batch_energy_partial<T, P, VM>)};
@@ -264,17 +273,24 @@ Kern kernels(const qla_batch *b, int lx) {
     if (b->prec == QLA_FP64)
         return b->P == 6 ? kern_vm<double, 6, 2>(b->vmode) : kern_vm<double, 3, 2>(b->vmode);
     if (b->P == 6) return kern_vm<float, 6, 2>(b->vmode);
-    return lx == 4 ? kern_vm<float, 3, 4>(b->vmode) : kern_vm<float, 3, 2>(b->vmode);
+    return lx == 4 ? kern_vm<float, 3, 4>(b->vmode)
+         : lx == 1 ? kern_vm<float, 3, 1>(b->vmode)
+                   : kern_vm<float, 3, 2>(b->vmode);
 }
 
+// FP32 E_z batches: packed pairs (1), 2 (the default) or 4 adjacent columns
+// per lane; other batches: 2.
 int lane_cols_of(const qla_batch *b) {
-    return (b->prec == QLA_FP32 && b->P == 3 && b->lane_cols == 4) ? 4 : 2;
+    if (b->prec == QLA_FP32 && b->P == 3) return b->lane_cols == 0 ? 2 : b->lane_cols;
+    return 2;
 }
+
+int window_out(int lx) { return lx == 1 ? 56 : 32 * lx - 8; }
 
 // Work items for the current tiling; returns the item count.
 qla_status build_items(qla_batch *b, int lx, int rows, int *n_items,
                        std::vector<BatchInst> &hinst) {
-    const int wout = 32 * lx - 8;
+    const int wout = window_out(lx);
     std::vector<BatchItem> items;
     hinst.resize(b->count);
     for (int k = 0; k < b->count; ++k) {
@@ -530,7 +546,7 @@ qla_ctx *qla_batch_instance(qla_batch *b, int k) {
 
 qla_status qla_batch_set_tuning(qla_batch *b, int lane_cols, int rows) {
     if (!b) return QLA_EINVAL;
-    if (lane_cols != 0 && lane_cols != 2 && lane_cols != 4)
+    if (lane_cols != 0 && lane_cols != 1 && lane_cols != 2 && lane_cols != 4)
         return bfail(b, QLA_EINVAL, "qla_batch_set_tuning: lane_cols %d", lane_cols);
     if (rows != 0 && (rows < 32 || rows > (1 << 20)))
         return bfail(b, QLA_EINVAL, "qla_batch_set_tuning: rows %d (0 or >= 32)", rows);
@@ -655,7 +671,7 @@ qla_status qla_batch_autotune(qla_batch *b, int trial_steps, int *chosen_lane_co
     s = align_pending(b, &n);
     if (s != QLA_OK) return s;
     const bool two = b->prec == QLA_FP32 && b->P == 3;
-    const int lxs[2] = {2, 4};
+    const int lxs[2] = {1, 2};
     const int rowss[3] = {64, 128, 256};
     float best = 1e30f;
     int best_lx = 2, best_rows = 256;

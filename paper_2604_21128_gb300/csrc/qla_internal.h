@@ -440,6 +440,13 @@ constexpr int DIV_TERMS = 6;
 cudaError_t launch_divergence(qla_ctx *c);
 cudaError_t launch_probe(qla_ctx *c, int count, const int *ij_dev, double *out_dev);
 cudaError_t launch_step_tile(qla_ctx *c, const void *in, void *out, bool vin);
+// Domain decomposition: copy a rectangle of the stored state (every live
+// plane) into a contiguous buffer (to_box) or back; the energy of a
+// rectangle into c->result; a packet on a window of a larger lattice.
+cudaError_t launch_box_copy(qla_ctx *c, int i0, int j0, int w, int h, void *box, bool to_box);
+cudaError_t launch_energy_box(qla_ctx *c, int i0, int j0, int w, int h);
+cudaError_t launch_packet_window(qla_ctx *c, const qla_packet &p, int i0, int j0, int gnx,
+                                 int gny);
 cudaError_t launch_step_march(qla_ctx *c, const void *in, void *out, bool vin);
 bool march_supported(const qla_ctx *c);
 int march_lane_cols(const qla_ctx *c);

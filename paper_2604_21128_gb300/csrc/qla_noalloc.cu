@@ -55,7 +55,9 @@ __device__ __forceinline__ double na_block_sum(double v) {
 }
 
 // Block b sums q^2 over sites [b*S, (b+1)*S) of every plane, S =
-// QLA_NOALLOC_SITES_PER_PARTIAL, in a fixed order.
+// QLA_NOALLOC_SITES_PER_PARTIAL, in a fixed order: row by row (the block's
+// range splits into whole rows plus a partial first and last row), the
+// threads striding along each row.
 template <typename T>
 __global__ void __launch_bounds__(NA_THREADS)
 k_na_partial(const T *__restrict__ q, int planes, int nx, long long sites, long long pitch,
@@ -64,12 +66,17 @@ k_na_partial(const T *__restrict__ q, int planes, int nx, long long sites, long 
     long long s1 = s0 + QLA_NOALLOC_SITES_PER_PARTIAL;
     if (s1 > sites) s1 = sites;
     double acc = 0.0;
-    for (long long t = s0 + threadIdx.x; t < s1; t += NA_THREADS) {
-        const long long j = t / nx, i = t - j * nx;
-        const long long g = j * pitch + i;
-        for (int p = 0; p < planes; ++p) {
-            const double v = double(q[p * stride + g]);
-            acc = fma(v, v, acc);
+    const long long j0 = s0 / nx, j1 = (s1 - 1) / nx;
+    for (long long j = j0; j <= j1; ++j) {
+        const long long rs = j * nx;
+        const long long a = (s0 > rs ? s0 : rs) - rs;
+        const long long b = (s1 < rs + nx ? s1 : rs + nx) - rs;
+        const T *row = q + j * pitch;
+        for (long long i = a + threadIdx.x; i < b; i += NA_THREADS) {
+            for (int p = 0; p < planes; ++p) {
+                const double v = double(row[p * stride + i]);
+                acc = fma(v, v, acc);
+            }
         }
     }
     acc = na_block_sum(acc);
@@ -103,6 +110,10 @@ extern "C" qla_status qla_energy_noalloc(const void *planes, int precision, int 
     if (cudaGetDevice(&dev) != cudaSuccess) return QLA_ECUDA;
     double *partials = nullptr;
     if (scratch_for(dev, &partials) != cudaSuccess) return QLA_ECUDA;
+    // An error another caller left pending is not ours to report or clear:
+    // refuse without launching and leave it in place.  Any error after the
+    // launches below is then this call's own.
+    if (cudaPeekAtLastError() != cudaSuccess) return QLA_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (precision == QLA_FP64)
         k_na_partial<double><<<int(blocks), NA_THREADS, 0, st>>>(

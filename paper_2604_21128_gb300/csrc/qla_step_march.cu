@@ -28,7 +28,7 @@
 // cp.async copies (no registers held while the loads fly); the next row's
 // records are looked up one iteration early.  The march loop is unrolled by
 // four so that every ring slot is a fixed register or buffer.
-#include "qla_march.cuh"
+#include "qla_march2.cuh"
 
 namespace qla {
 namespace {
@@ -55,6 +55,28 @@ k_step_march(const T *__restrict__ in, T *__restrict__ out, const uint32_t *__re
              const MedRec<T> *__restrict__ table, int nx, int ny, int pitch, size_t plane,
              int seg_h, int n_wx, int n_items) {
     using M = March<T, P, LX, VM, VIN>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename M::Slot *ring =
+        reinterpret_cast<typename M::Slot *>(smem_raw) + (threadIdx.x >> 5) * NSLOT;
+    M m;
+    m.in = in;
+    m.out = out;
+    m.midx = midx;
+    m.table = table;
+    m.pitch = pitch;
+    m.plane = uint32_t(plane);
+    m.total = uint32_t(ny) * uint32_t(pitch);
+    const int item = blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (item < n_items) m.run_item(nx, ny, seg_h, n_wx, item, ring);
+}
+
+// The packed-pair variant (FP32 E_z; see qla_march2.cuh): same arguments.
+template <int VM, bool VIN, typename PO>
+__global__ void __launch_bounds__(32 * WARPS, 4)
+k_step_march2(const float *__restrict__ in, float *__restrict__ out,
+              const uint32_t *__restrict__ midx, const MedRec<float> *__restrict__ table,
+              int nx, int ny, int pitch, size_t plane, int seg_h, int n_wx, int n_items) {
+    using M = March2<VM, VIN, PO>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     typename M::Slot *ring =
         reinterpret_cast<typename M::Slot *>(smem_raw) + (threadIdx.x >> 5) * NSLOT;
@@ -102,11 +124,28 @@ inline int pick_segment(int ny, int n_wx, long long resident_warps) {
     return best;
 }
 
+// Kernel, staged-row size and stored columns per window of a variant; LX = 1
+// selects the packed-pair kernel (FP32 E_z).
+template <typename T, int P, int LX, int VM, bool VIN> struct Variant {
+    static constexpr int WOUT = 32 * LX - 8;
+    static constexpr size_t SLOT = sizeof(typename March<T, P, LX, VM, VIN>::Slot);
+    static constexpr auto kern = k_step_march<T, P, LX, VM, VIN>;
+};
+template <typename PO, int VM, bool VIN> struct Variant2 {
+    static constexpr int WOUT = March2<VM, VIN, PO>::WOUT;
+    static constexpr size_t SLOT = sizeof(typename March2<VM, VIN, PO>::Slot);
+    static constexpr auto kern = k_step_march2<VM, VIN, PO>;
+};
+template <int VM, bool VIN> struct Variant<float, 3, 1, VM, VIN> : Variant2<PairF2, VM, VIN> {};
+template <int VM, bool VIN> struct Variant<float, 3, 5, VM, VIN> : Variant2<PairB64, VM, VIN> {};
+template <int VM, bool VIN> struct Variant<float, 3, 6, VM, VIN> : Variant2<PairMix, VM, VIN> {};
+
 template <typename T, int P, int LX, int VM, bool VIN>
 cudaError_t launch_t(qla_ctx *c, const void *in, void *out, const void *table) {
-    constexpr int WOUT = 32 * LX - 8;
-    auto kern = k_step_march<T, P, LX, VM, VIN>;
-    const size_t smem = sizeof(typename March<T, P, LX, VM, VIN>::Slot) * NSLOT * WARPS;
+    using V = Variant<T, P, LX, VM, VIN>;
+    constexpr int WOUT = V::WOUT;
+    auto kern = V::kern;
+    const size_t smem = V::SLOT * NSLOT * WARPS;
     // per instantiation, per process; initialised once (thread-safe)
     struct Occ { cudaError_t err; int per_sm; };
     static const Occ occ = [&] {
@@ -172,17 +211,22 @@ cudaError_t launch_ds(qla_ctx *c, const void *in, void *out, bool vin) {
 
 }  // namespace
 
-// Columns per lane: 2 or 4 for FP32 E_z contexts (tunable, default 2: at
-// 128 registers four warps per scheduler stay resident, which outweighs the
-// wider window's smaller halo), 2 otherwise.
+// Column layout for FP32 E_z contexts: 1, 5, 6 = the packed-pair kernel
+// (two columns 32 apart per lane, FP32x2 arithmetic) in its three pair
+// forms (PairF2, PairB64, PairMix), or 2 or 4 adjacent columns per lane
+// (scalar arithmetic; 2 is the default: at 128 registers four warps per
+// scheduler stay resident, which outweighs the wider window's smaller halo).
+// Other contexts: 2.
 int march_lane_cols(const qla_ctx *c) {
-    if (c->prec == QLA_FP32 && c->P == 3) return c->march_lx == 4 ? 4 : 2;
+    if (c->prec == QLA_FP32 && c->P == 3 && c->march_lx != 0) return c->march_lx;
     return 2;
 }
 
 bool march_supported(const qla_ctx *c) {
     const int lx = march_lane_cols(c);
-    return c->nx % lx == 0 && c->nx >= 32 * lx && c->ny >= 8 &&
+    const bool packed = lx == 1 || lx == 5 || lx == 6;
+    const int align = packed ? 4 : lx, width = packed ? 64 : 32 * lx;
+    return c->nx % align == 0 && c->nx >= width && c->ny >= 8 &&
            c->plane_elems < (size_t(1) << 31) && !(c->tensor && c->P == 6) &&
            c->vmode != V_LCU;
 }
@@ -209,8 +253,13 @@ cudaError_t launch_step_march(qla_ctx *c, const void *in, void *out, bool vin) {
         return c->P == 6 ? launch_vm<double, 6, 2>(c, in, out, vin)
                          : launch_vm<double, 3, 2>(c, in, out, vin);
     if (c->P == 6) return launch_vm<float, 6, 2>(c, in, out, vin);
-    return march_lane_cols(c) == 2 ? launch_vm<float, 3, 2>(c, in, out, vin)
-                                   : launch_vm<float, 3, 4>(c, in, out, vin);
+    switch (march_lane_cols(c)) {
+    case 1: return launch_vm<float, 3, 1>(c, in, out, vin);
+    case 5: return launch_vm<float, 3, 5>(c, in, out, vin);
+    case 6: return launch_vm<float, 3, 6>(c, in, out, vin);
+    case 4: return launch_vm<float, 3, 4>(c, in, out, vin);
+    default: return launch_vm<float, 3, 2>(c, in, out, vin);
+    }
 }
 
 }  // namespace qla

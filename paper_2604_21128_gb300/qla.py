@@ -71,10 +71,17 @@ def load():
                            ("qla_fields", [c_vp] + [c_vp] * 6),
                            ("qla_probe", [c_vp, c_int, c_vp, c_vp, c_vp]),
                            ("qla_set_step_kernel", [c_vp, c_int]),
-                           ("qla_set_march_tuning", [c_vp, c_int, c_int])):
+                           ("qla_set_march_tuning", [c_vp, c_int, c_int]),
+                           ("qla_set_packet_window", [c_vp, ctypes.POINTER(qla_packet), c_int,
+                                                      c_int, c_int, c_int]),
+                           ("qla_pack_box", [c_vp, c_int, c_int, c_int, c_int, c_vp]),
+                           ("qla_unpack_box", [c_vp, c_int, c_int, c_int, c_int, c_vp]),
+                           ("qla_energy_box", [c_vp, c_int, c_int, c_int, c_int, _DP])):
             getattr(lib, name).argtypes = args
             getattr(lib, name).restype = c_int
         lib.qla_init_grid.restype = c_int
+        lib.qla_box_bytes.argtypes = [c_vp, c_int, c_int]
+        lib.qla_box_bytes.restype = c_sz
         lib.qla3_workspace_bytes.argtypes = [c_int, c_int, c_int, c_int, c_u]
         lib.qla3_workspace_bytes.restype = c_sz
         lib.qla3_init.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, c_int, ctypes.c_double,
@@ -253,6 +260,34 @@ def qla_probe(ctx, i, j):
 
 
 
+def qla_set_packet_window(ctx, i0, j0, gnx, gny, x0, y0, angle, k0, width,
+                          transverse_width=0.0, amplitude=1.0):
+    p = qla_packet(float(x0), float(y0), float(angle), float(k0), float(width),
+                   float(transverse_width), float(amplitude))
+    _check(ctx, load().qla_set_packet_window(ctx, ctypes.byref(p), int(i0), int(j0), int(gnx),
+                                             int(gny)))
+
+
+def qla_box_bytes(ctx, w, h):
+    return int(load().qla_box_bytes(ctx, int(w), int(h)))
+
+
+def qla_pack_box(ctx, i0, j0, w, h, dst_dev_ptr):
+    _check(ctx, load().qla_pack_box(ctx, int(i0), int(j0), int(w), int(h),
+                                    ctypes.c_void_p(dst_dev_ptr)))
+
+
+def qla_unpack_box(ctx, i0, j0, w, h, src_dev_ptr):
+    _check(ctx, load().qla_unpack_box(ctx, int(i0), int(j0), int(w), int(h),
+                                      ctypes.c_void_p(src_dev_ptr)))
+
+
+def qla_energy_box(ctx, i0, j0, w, h):
+    v = ctypes.c_double()
+    _check(ctx, load().qla_energy_box(ctx, int(i0), int(j0), int(w), int(h), ctypes.byref(v)))
+    return v.value
+
+
 def qla_set_step_kernel(ctx, kernel):
     _check(ctx, load().qla_set_step_kernel(ctx, int(kernel)))
 
@@ -373,6 +408,44 @@ class Grid:
 
     def set_march_tuning(self, lane_cols=0, rows=0):
         qla_set_march_tuning(self._ctx, lane_cols, rows)
+
+    # domain decomposition (qla_set_packet_window, qla_*_box)
+    def set_packet_window(self, i0, j0, gnx, gny, x0, y0, angle, k0, width,
+                          transverse_width=0.0, amplitude=1.0):
+        with self._dev():
+            qla_set_packet_window(self._ctx, i0, j0, gnx, gny, x0, y0, angle, k0, width,
+                                  transverse_width, amplitude)
+
+    def box_dtype(self):
+        import torch
+        return torch.float64 if self.precision == QLA_FP64 else torch.float32
+
+    def pack_box(self, i0, j0, w, h, out=None):
+        """The stored values of a rectangle as a device tensor (planes, h, w)."""
+        import torch
+        planes = 3 if self.flags & QLA_TE_ONLY else 6
+        if out is None:
+            out = torch.empty((planes, h, w), dtype=self.box_dtype(), device=self.device)
+        if not out.is_contiguous() or out.device != self.device or out.numel() != planes * h * w \
+                or out.dtype != self.box_dtype():
+            raise ValueError("pack_box: out must be a contiguous (%d, %d, %d) %s tensor on %s"
+                             % (planes, h, w, self.box_dtype(), self.device))
+        with self._dev():
+            qla_pack_box(self._ctx, i0, j0, w, h, out.data_ptr())
+        return out
+
+    def unpack_box(self, i0, j0, w, h, src):
+        planes = 3 if self.flags & QLA_TE_ONLY else 6
+        if not src.is_contiguous() or src.device != self.device or src.numel() != planes * h * w \
+                or src.dtype != self.box_dtype():
+            raise ValueError("unpack_box: src must be a contiguous (%d, %d, %d) %s tensor on %s"
+                             % (planes, h, w, self.box_dtype(), self.device))
+        with self._dev():
+            qla_unpack_box(self._ctx, i0, j0, w, h, src.data_ptr())
+
+    def energy_box(self, i0, j0, w, h):
+        with self._dev():
+            return qla_energy_box(self._ctx, i0, j0, w, h)
 
 
     @property

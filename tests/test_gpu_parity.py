@@ -18,6 +18,11 @@ from paper_2604_21128_gb300 import inputs, qla
 
 pytestmark = pytest.mark.gpu
 
+# Full-size FP32 runs of 16-24 steps, sampled sites against the oracle: the
+# absolute error per amplitude (packet amplitude 1; q2 = n E_z up to 2 inside
+# the dielectric).  Each step rounds ~18 rotations at ~2^-24 relative.
+FP32_SITE_BOUND = 2e-5
+
 
 @pytest.fixture(scope="module", autouse=True)
 def _setup():
@@ -194,18 +199,21 @@ def test_fp32_ellipse_256_400_steps():
     assert abs(e / oracle.energy(want) - 1) <= 1e-5
 
 
-def test_fp32_ten_thousand_steps_error_budget():
-    """FP32 against the FP64 oracle after 10^4 steps: relative L2 <= 1e-5
-    (the ellipse workload scaled to 128^2, so the packet crosses the box and
-    the dielectric many times)."""
-    w = inputs.scaled(inputs.ellipse_256(), 128, 128, 10000)
+@pytest.mark.parametrize("side", [128, 256])
+def test_fp32_ten_thousand_steps_error_budget(side):
+    """FP32 against the FP64 oracle after 10^4 steps: relative L2 <= 1e-5 and
+    energy drift <= 1e-5, on the 256^2 ellipse workload itself and on the
+    same geometry scaled to 128^2 (where the packet crosses the box and the
+    dielectric twice as often).  Prints the margin under the bound."""
+    w = inputs.scaled(inputs.ellipse_256(), side, side, 10000)
     n = w.medium()
     pk = w.packet.as_dict()
     want = oracle.run(oracle.packet(n, w.delta, **pk), n, w.delta, w.steps)
     got, e = gpu_run(n, w.delta, w.steps, packet=pk, precision="fp32", te=True)
     err = rel_l2(got, want)
     drift = e / oracle.energy(want) - 1
-    print("fp32 1e4 steps: rel L2 %.3e, energy drift %.3e" % (err, drift))
+    print("fp32 1e4 steps, %d^2: rel L2 %.3e (%.0f%% of the 1e-5 bound), energy drift %.3e"
+          % (side, err, 100 * err / 1e-5, drift))
     assert err <= 1e-5
     assert abs(drift) <= 1e-5
 
@@ -276,9 +284,13 @@ def test_full_size_8192_sampled_sites():
         got = g.probe(ii, jj)
         e = g.energy()
     half = oracle.reach_per_step() * steps + 2
+    worst = 0.0
     for k in range(len(ii)):
         want = oracle.run_window(n, w.delta, pk, steps, (int(ii[k]), int(jj[k])), half)
-        assert np.max(np.abs(got[k] - want)) <= 2e-5, (ii[k], jj[k], got[k], want)
+        d = float(np.max(np.abs(got[k] - want)))
+        worst = max(worst, d)
+        assert d <= FP32_SITE_BOUND, (ii[k], jj[k], got[k], want)
+    print("8192^2 FP32, %d steps: worst sampled site error %.2e" % (steps, worst))
     assert np.all(got[:, [0, 1, 5]] == 0)
     assert math.isfinite(e) and e > 0
 
@@ -305,9 +317,13 @@ def test_full_size_16384_bubble_sampled_sites():
         g.step(steps)
         got = g.probe(ii, jj)
     half = oracle.reach_per_step() * steps + 2
+    worst = 0.0
     for k in range(len(ii)):
         want = oracle.run_window(n, w.delta, pk, steps, (int(ii[k]), int(jj[k])), half)
-        assert np.max(np.abs(got[k] - want)) <= 2e-5, (ii[k], jj[k], got[k], want)
+        d = float(np.max(np.abs(got[k] - want)))
+        worst = max(worst, d)
+        assert d <= FP32_SITE_BOUND, (ii[k], jj[k], got[k], want)
+    print("16384^2 FP32, %d steps: worst sampled site error %.2e" % (steps, worst))
     assert np.any(np.abs(got[:6, 2]) > 1e-3)      # the packet is in the sample
 
 

@@ -11,6 +11,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_2604_21128_gb300 import build as qbuild
 from paper_2604_21128_gb300 import inputs, qla
 
@@ -54,6 +55,12 @@ def test_energy_noalloc_matches_qla_energy_on_two_calls():
         torch.cuda.synchronize()
         e = out.item()
         assert abs(e / e_ref - 1) <= 1e-12, (prec, e, e_ref)
+        # and against the oracle's energy (Eq. A13) of the same state, at the
+        # precision the planes were stored in
+        stored = planes.double().cpu().numpy()
+        full = np.zeros((6, ny, nx))
+        full[live] = stored
+        assert abs(e / oracle.energy(full) - 1) <= 1e-12, (prec, e)
         results.append(e)
     assert results[0] != results[1]
 
