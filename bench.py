@@ -344,10 +344,10 @@ def reference_arm(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def kernel_traffic(k, sites, record="traffic.json"):
+def kernel_traffic(k, sites, record):
     """DRAM bytes per step-kernel launch (per step for the 3D passes) from a
-    committed ncu record, if it was taken on the current kernel sources;
-    else None."""
+    committed ncu record of this workload, if it was taken on the current
+    kernel sources with the same steps per launch; else None."""
     path = os.path.join(ROOT, "profiles", record)
     try:
         with open(path) as f:
@@ -439,9 +439,12 @@ def gpu_arm(args):
     k_used = S * args.steps / max(step_launches, 1)
     per_launch_s = step_time / max(step_launches, 1)
     kernel_su_per_s = sites * k_used / per_launch_s
-    # the committed DRAM record is of the FP32 E_z step kernel
-    traffic = (kernel_traffic(int(round(k_used)), sites)
-               if args.precision == "fp32" and te else None)
+    # the committed DRAM records are of the FP32 E_z step kernel, one per
+    # workload, taken with the default marching tuning
+    traffic = (kernel_traffic(int(round(k_used)), sites,
+                              "traffic_%s_fp32_ez.json" % args.workload)
+               if args.precision == "fp32" and te and not ds and not args.lane_cols
+               and not args.rows else None)
     g.close()
 
     e2e = None

@@ -312,10 +312,10 @@ qla_status qla_energy_noalloc(const void *planes, int precision, int n_planes, i
 /* Tuning of the marching kernel: lane_cols = the column layout of a warp's
  * window (0 = library choice).  For FP32 E_z contexts: 1 = packed pairs
  * (each lane holds two columns 32 apart and rotates both with FP32x2
- * instructions; 64-column windows; nx a multiple of 4; 5 and 6 are the
- * same kernel with other register forms of the pairs),
- * 2 or 4 = that many adjacent columns per lane (scalar FP32; 2 is the
- * default).  Other contexts always use 2.  rows = rows per work
+ * instructions; 64-column windows; nx a multiple of 4), 5 = packed pairs
+ * with U_x of row J + 1 interleaved with U_y of row J (two independent
+ * chains per warp), 2 or 4 = that many adjacent columns per lane (scalar
+ * FP32; 2 is the default).  Other contexts always use 2.  rows = rows per work
  * item (0 = chosen from the occupancy so one wave of items fills the GPU;
  * else rounded up to a multiple of 4).  Results do not depend on either.
  * QLA_EINVAL for other values. */

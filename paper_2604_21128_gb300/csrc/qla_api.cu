@@ -601,9 +601,8 @@ qla_status qla_set_step_kernel(qla_ctx *c, int kernel) {
 qla_status qla_set_march_tuning(qla_ctx *c, int lane_cols, int rows) {
     qla_status s = usable(c);
     if (s != QLA_OK) return s;
-    if (lane_cols != 0 && lane_cols != 1 && lane_cols != 2 && lane_cols != 4 && lane_cols != 5 &&
-        lane_cols != 6)
-        return fail(c, QLA_EINVAL, "qla_set_march_tuning: lane_cols %d not 0, 1, 2 or 4",
+    if (lane_cols != 0 && lane_cols != 1 && lane_cols != 2 && lane_cols != 4 && lane_cols != 5)
+        return fail(c, QLA_EINVAL, "qla_set_march_tuning: lane_cols %d not 0, 1, 2, 4 or 5",
                     lane_cols);
     if (rows < 0 || rows > (1 << 20))
         return fail(c, QLA_EINVAL, "qla_set_march_tuning: rows %d", rows);

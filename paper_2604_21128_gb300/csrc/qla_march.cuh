@@ -387,6 +387,13 @@ struct March {
                 for (int c = 0; c < 2; ++c)
 #pragma unroll
                     for (int x = 0; x < LX; ++x) carry[a][b][c][x] = T(0);
+        // the coefficient slots of the rows before J0 are read by the first
+        // iterations (their results reach halo rows only); they must hold
+        // defined values, or the compiler may substitute any register
+#pragma unroll
+        for (int a = 0; a < LAG; ++a)
+#pragma unroll
+            for (int x = 0; x < LX; ++x) kring[a][x] = CC{};
         // rows y_lo-4 .. y_hi+3 enter; rows y_lo .. y_hi-1 are stored by the
         // lanes whose columns are all inside [4, W - 4) and below nx
         const int J0 = y_lo - LAG;

@@ -28,17 +28,11 @@
 namespace qla {
 namespace march {
 
-// Pair arithmetic.  Three forms of the same operations (one rounding per
-// fma.rn / mul.rn on each half, so the results are bitwise equal):
-//   PairF2: float2 values and the packed intrinsics (negation of an operand
-//           is folded into the instruction);
-//   PairB64: 64-bit registers and inline fma.rn.f32x2 / mul.rn.f32x2 (a pair
-//           stays in one aligned register pair for its whole life); PTX has
-//           no packed negation, so the sine pairs are kept in both signs;
-//   PairMix: 64-bit storage, intrinsic arithmetic on float2 views.
+// Pair arithmetic: float2 values and the packed intrinsics (one rounding
+// per fma.rn / mul.rn on each half; negation of an operand is folded into
+// the instruction).
 struct PairF2 {
     using T = float2;
-    static constexpr bool NEG_RING = false;
     __device__ static __forceinline__ T make(float lo, float hi) { return make_float2(lo, hi); }
     __device__ static __forceinline__ float lo(T v) { return v.x; }
     __device__ static __forceinline__ float hi(T v) { return v.y; }
@@ -47,68 +41,16 @@ struct PairF2 {
     __device__ static __forceinline__ T neg(T a) { return make_float2(-a.x, -a.y); }
 };
 
-struct PairB64 {
-    using T = unsigned long long;
-    static constexpr bool NEG_RING = true;
-    __device__ static __forceinline__ T make(float lo, float hi) {
-        T r;
-        asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-        return r;
-    }
-    __device__ static __forceinline__ float lo(T v) {
-        float a, b;
-        asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-        return a;
-    }
-    __device__ static __forceinline__ float hi(T v) {
-        float a, b;
-        asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-        return b;
-    }
-    __device__ static __forceinline__ T fma(T a, T b, T c) {
-        T d;
-        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-        return d;
-    }
-    __device__ static __forceinline__ T mul(T a, T b) {
-        T d;
-        asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-        return d;
-    }
-    __device__ static __forceinline__ T neg(T a) { return a ^ 0x8000000080000000ull; }
-};
-
-struct PairMix {
-    using T = unsigned long long;
-    static constexpr bool NEG_RING = false;
-    __device__ static __forceinline__ float2 f2(T v) {
-        float2 r;
-        asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-        return r;
-    }
-    __device__ static __forceinline__ T u(float2 v) {
-        T r;
-        asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
-        return r;
-    }
-    __device__ static __forceinline__ T make(float lo, float hi) { return u(make_float2(lo, hi)); }
-    __device__ static __forceinline__ float lo(T v) { return f2(v).x; }
-    __device__ static __forceinline__ float hi(T v) { return f2(v).y; }
-    __device__ static __forceinline__ T fma(T a, T b, T c) {
-        return u(__ffma2_rn(f2(a), f2(b), f2(c)));
-    }
-    __device__ static __forceinline__ T mul(T a, T b) { return u(__fmul2_rn(f2(a), f2(b))); }
-    __device__ static __forceinline__ T neg(T a) {
-        const float2 v = f2(a);
-        return u(make_float2(-v.x, -v.y));
-    }
-};
-
 // Two-word collision coefficients of two columns: (c_hi, s_hi, c_lo, s_lo)
-// of Coef<float>, one column per half; with NEG_RING also -s_hi, -s_lo.
+// of Coef<float>, one column per half.
 template <typename PO> struct K2 {
     typename PO::T ch, sh, cl, sl;
-    typename PO::T nsh, nsl;   // used with NEG_RING only
+    __device__ __forceinline__ void copy_from(const K2 &o) {
+        ch = o.ch;
+        sh = o.sh;
+        cl = o.cl;
+        sl = o.sl;
+    }
 };
 
 // (a, b) <- [[c, -G s], [G s, c]] (a, b) on both halves: per element the
@@ -116,22 +58,24 @@ template <typename PO> struct K2 {
 template <typename PO, int G>
 __device__ __forceinline__ void rotate2(typename PO::T &a, typename PO::T &b, const K2<PO> &k) {
     using T = typename PO::T;
-    T shp, slp, shn, sln;   // G s and -G s, high and low words
-    if constexpr (PO::NEG_RING) {
-        shp = G > 0 ? k.sh : k.nsh;
-        slp = G > 0 ? k.sl : k.nsl;
-        shn = G > 0 ? k.nsh : k.sh;
-        sln = G > 0 ? k.nsl : k.sl;
-    } else {
-        shp = G > 0 ? k.sh : PO::neg(k.sh);
-        slp = G > 0 ? k.sl : PO::neg(k.sl);
-        shn = PO::neg(shp);
-        sln = PO::neg(slp);
-    }
+    // G s and -G s, high and low words
+    const T shp = G > 0 ? k.sh : PO::neg(k.sh), slp = G > 0 ? k.sl : PO::neg(k.sl);
+    const T shn = PO::neg(shp), sln = PO::neg(slp);
     const T na = PO::fma(k.ch, a, PO::fma(shn, b, PO::fma(k.cl, a, PO::mul(sln, b))));
     const T nb = PO::fma(k.ch, b, PO::fma(shp, a, PO::fma(k.cl, b, PO::mul(slp, a))));
     a = na;
     b = nb;
+}
+
+// mask ? a : b for a mask of all ones or all zeros, as one bit operation:
+// the seam selects of the bond layers take no predicate register (several
+// predicates live across the whole march otherwise crowd the predicate file).
+__device__ __forceinline__ float bitsel(uint32_t mask, float a, float b) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, 0xE4;"
+        : "=r"(d)
+        : "r"(__float_as_uint(a)), "r"(__float_as_uint(b)), "r"(mask));
+    return __uint_as_float(d);
 }
 
 template <typename PO, int G>
@@ -141,7 +85,7 @@ __device__ __forceinline__ void bond_rot2(typename PO::T &u, typename PO::T &m, 
     else rotate2<PO, G>(u, m, k);
 }
 
-template <int VM, bool VIN, typename PO = PairF2>
+template <int VM, bool VIN, typename PO = PairF2, bool ILV = false>
 struct March2 {
     using T2 = typename PO::T;
     static constexpr int W = 64;        // window columns (lane l: l and l + 32)
@@ -160,7 +104,7 @@ struct March2 {
     int pitch;
     Slot *ring;
     int lane, prev, next;    // this lane, the lanes before and after it (mod 32)
-    bool first, last;        // lane 0, lane 31
+    uint32_t first, last;    // all ones on lane 0 / lane 31, else zero
     // the lane's two staging copies: global sources at row 0, shared
     // destinations as byte offsets inside a slot
     const char *src0, *src1;
@@ -169,8 +113,14 @@ struct March2 {
     T2 carry[4][2];          // U_y neighbour layers: [layer][value]
     K2<PO> kring[LAG];       // collision coefficients of the rows in flight
     float4 vlo, vhi;         // row J+1's potential coefficients (low, high column)
-    bool vlive_lo, vlive_hi; // row J+1's sites have their own records
+    // row J+1's sites have their own records (0 or 1; integers, like the
+    // other per-lane flags, so that no predicate stays live across the march)
+    uint32_t vlive_lo, vlive_hi;
     uint32_t o_in, o_now, o_out;
+    // interleaved march (ILV): row J + 1's coefficients, and q2, q3 of row J
+    // after U_x, carried into the iteration that runs U_y on row J
+    K2<PO> knext;
+    T2 p2, p3;
 
     __device__ __forceinline__ uint32_t next_row(uint32_t o) const {
         o += uint32_t(pitch);
@@ -186,28 +136,31 @@ struct March2 {
         o_in = next_row(o_in);
     }
 
-    // Row J + 1's records (staging slot S) into coefficient ring slot K and
+    // The records of the row in staging slot S into the coefficients kd and
     // the potential coefficients.
-    template <int S, int K>
-    __device__ __forceinline__ void lookup_next() {
+    template <int S>
+    __device__ __forceinline__ void lookup_into(K2<PO> &kd) {
         const uint32_t il = ring[S].idx[lane], ih = ring[S].idx[lane + 32];
         const MedRec<float> *rl = table + il, *rh = table + ih;
-        const float4 cl = rl->c, chh = rh->c;
-        kring[K].ch = PO::make(cl.x, chh.x);
-        kring[K].sh = PO::make(cl.y, chh.y);
-        kring[K].cl = PO::make(cl.z, chh.z);
-        kring[K].sl = PO::make(cl.w, chh.w);
-        if constexpr (PO::NEG_RING) {
-            kring[K].nsh = PO::make(-cl.y, -chh.y);
-            kring[K].nsl = PO::make(-cl.w, -chh.w);
-        }
+        // one word per load, straight into its pair: a pair holds the same
+        // coefficient of two records, and 16-byte loads of whole records
+        // would leave the halves in registers that are not a pair (the
+        // compiler then rebuilds the pair at every use)
+        const float *wl = reinterpret_cast<const float *>(&rl->c);
+        const float *wh = reinterpret_cast<const float *>(&rh->c);
+        kd.ch = PO::make(__ldg(wl + 0), __ldg(wh + 0));
+        kd.sh = PO::make(__ldg(wl + 1), __ldg(wh + 1));
+        kd.cl = PO::make(__ldg(wl + 2), __ldg(wh + 2));
+        kd.sl = PO::make(__ldg(wl + 3), __ldg(wh + 3));
         if constexpr (VIN) {
-            vlive_lo = il >= uint32_t(UNIFORM_SLOTS);
-            vlive_hi = ih >= uint32_t(UNIFORM_SLOTS);
+            vlive_lo = il >= uint32_t(UNIFORM_SLOTS) ? 1u : 0u;
+            vlive_hi = ih >= uint32_t(UNIFORM_SLOTS) ? 1u : 0u;
             if (vlive_lo) vlo = rl->v;
             if (vlive_hi) vhi = rh->v;
         }
     }
+    template <int S, int K>
+    __device__ __forceinline__ void lookup_next() { lookup_into<S>(kring[K]); }
 
     // The pending V_x, V_y at one column (the E_z triple).
     __device__ __forceinline__ void potential(float &q2, float &q3, float &q4, float4 kv) {
@@ -223,22 +176,22 @@ struct March2 {
     __device__ __forceinline__ T2 take_left(T2 m) const {
         const float ml = PO::lo(m), mh = PO::hi(m);
         return PO::make(__shfl_sync(0xffffffffu, ml, prev),
-                        __shfl_sync(0xffffffffu, last ? ml : mh, prev));
+                        __shfl_sync(0xffffffffu, bitsel(last, ml, mh), prev));
     }
     __device__ __forceinline__ T2 give_right(T2 mm) const {
         const float ml = PO::lo(mm), mh = PO::hi(mm);
-        return PO::make(__shfl_sync(0xffffffffu, first ? mh : ml, next),
+        return PO::make(__shfl_sync(0xffffffffu, bitsel(first, mh, ml), next),
                         __shfl_sync(0xffffffffu, mh, next));
     }
     __device__ __forceinline__ T2 take_right(T2 m) const {
         const float ml = PO::lo(m), mh = PO::hi(m);
-        return PO::make(__shfl_sync(0xffffffffu, first ? mh : ml, next),
+        return PO::make(__shfl_sync(0xffffffffu, bitsel(first, mh, ml), next),
                         __shfl_sync(0xffffffffu, mh, next));
     }
     __device__ __forceinline__ T2 give_left(T2 mm) const {
         const float ml = PO::lo(mm), mh = PO::hi(mm);
         return PO::make(__shfl_sync(0xffffffffu, ml, prev),
-                        __shfl_sync(0xffffffffu, last ? ml : mh, prev));
+                        __shfl_sync(0xffffffffu, bitsel(last, ml, mh), prev));
     }
 
     // U_x layer L on the pair (q2, q4) (Eq. 2e3; q4 is the S14 mover).
@@ -301,8 +254,8 @@ struct March2 {
     }
 
     template <int PH>
-    __device__ __forceinline__ void iter(int J, int st_lo, unsigned st_n, bool lo_ok,
-                                         bool hi_ok, float *out_lo, float *out_hi) {
+    __device__ __forceinline__ void iter(int J, int st_lo, unsigned st_n, uint32_t lo_ok,
+                                         uint32_t hi_ok, float *out_lo, float *out_hi) {
         constexpr int S0 = PH, S1 = (PH + 3) & 3, S2 = (PH + 2) & 3, S3 = (PH + 1) & 3;
         // every lane is done with the slot of row J - 1 before it is refilled
         __syncwarp();
@@ -362,6 +315,92 @@ struct March2 {
         o_out = next_row(o_out);
     }
 
+    // The row in staging slot S, with the pending V applied (VIN).
+    // The reads are volatile: a value read here may only be used in the next
+    // iteration (q3 waits there for U_y), and the read must not sink past the
+    // next iteration's copy into this slot.
+    template <int S>
+    __device__ __forceinline__ void load_row(T2 &q2, T2 &q3, T2 &q4) {
+        const volatile float(*sq)[W] = ring[S].q;
+        float l2 = sq[0][lane], h2 = sq[0][lane + 32];
+        float l3 = sq[1][lane], h3 = sq[1][lane + 32];
+        float l4 = sq[2][lane], h4 = sq[2][lane + 32];
+        if constexpr (VIN) {
+            if (vlive_lo) potential(l2, l3, l4, vlo);
+            if (vlive_hi) potential(h2, h3, h4, vhi);
+        }
+        q2 = PO::make(l2, h2);
+        q3 = PO::make(l3, h3);
+        q4 = PO::make(l4, h4);
+    }
+
+    __device__ __forceinline__ void store_q4(bool row_in, uint32_t lo_ok, uint32_t hi_ok,
+                                             float *out_lo, float *out_hi, T2 q4) {
+        if (row_in) {
+            if (lo_ok) out_lo[2 * plane + o_now] = PO::lo(q4);
+            if (hi_ok) out_hi[2 * plane + o_now] = PO::hi(q4);
+        }
+        o_now = next_row(o_now);
+    }
+
+    // Interleaved march, iteration J (PH = (J - J0) mod 4): U_x of row J + 1
+    // and U_y of row J are independent, and their layers alternate in the
+    // instruction stream, so each warp has two dependent chains to issue
+    // from (a bond layer's shuffles no longer stall the warp).  Rows are
+    // staged four ahead; on entry knext holds row J + 1's coefficients and
+    // (p2, p3) row J after U_x.
+    template <int PH>
+    __device__ __forceinline__ void iter_ilv(int J, int st_lo, unsigned st_n, uint32_t lo_ok,
+                                             uint32_t hi_ok, float *out_lo, float *out_hi) {
+        constexpr int S0 = PH, S1 = (PH + 3) & 3, S2 = (PH + 2) & 3, S3 = (PH + 1) & 3;
+        // row J's slot was last read in the previous iteration: stage row
+        // J + 4 into it
+        __syncwarp();
+        stage<PH>();
+        cp_async_wait<NSLOT - 2>();
+        // rows J + 1 and J + 2, copied by all lanes, are complete and visible
+        __syncwarp();
+        T2 n2, n3, n4;
+        load_row<(PH + 1) & 3>(n2, n3, n4);
+
+        ux_layer<0>(n2, n4, knext);
+        uy_local<0>(p2, p3, kring[S0]);                  // L1, row J
+        ux_layer<1>(n2, n4, knext);
+        uy_neighbour<1>(p2, p3, carry[0], kring[S0]);    // L2 -> row J-1
+        ux_layer<2>(n2, n4, knext);
+        uy_local<2>(p2, p3, kring[S1]);                  // L3, row J-1
+        ux_layer<3>(n2, n4, knext);
+        uy_neighbour<3>(p2, p3, carry[1], kring[S2]);    // L4 -> row J-2
+        ux_layer<4>(n2, n4, knext);
+        uy_local<4>(p2, p3, kring[S2]);                  // L5, row J-2
+        ux_layer<5>(n2, n4, knext);
+        uy_neighbour<5>(p2, p3, carry[2], kring[S3]);    // L6 -> row J-3
+        ux_layer<6>(n2, n4, knext);
+        uy_local<6>(p2, p3, kring[S3]);                  // L7, row J-3
+        ux_layer<7>(n2, n4, knext);
+        uy_neighbour<7>(p2, p3, carry[3], kring[S3]);    // L8 -> row J-4
+
+        // q4 of row J + 1 is final after U_x; q2, q3 of row J - 4 after U_y
+        store_q4(unsigned(J + 1 - st_lo) < st_n, lo_ok, hi_ok, out_lo, out_hi, n4);
+        if (unsigned(J - LAG - st_lo) < st_n) {
+            if (lo_ok) {
+                out_lo[o_out] = PO::lo(p2);
+                out_lo[plane + o_out] = PO::lo(p3);
+            }
+            if (hi_ok) {
+                out_hi[o_out] = PO::hi(p2);
+                out_hi[plane + o_out] = PO::hi(p3);
+            }
+        }
+        o_out = next_row(o_out);
+        // row J - 3's slot is free: row J + 1's coefficients move in (they
+        // are the next iteration's S0); row J + 2's are looked up
+        kring[S3].copy_from(knext);
+        lookup_into<(PH + 2) & 3>(knext);
+        p2 = n2;
+        p3 = n3;
+    }
+
     // Work item `item`: window item % n_wx, row segment item / n_wx.
     // Needs nx a multiple of 4 (16-byte chunks stay inside a row) and >= 64.
     __device__ __forceinline__ void run_item(int nx, int ny, int seg_h, int n_wx, int item,
@@ -369,8 +408,8 @@ struct March2 {
         lane = threadIdx.x & 31;
         prev = (lane + 31) & 31;
         next = (lane + 1) & 31;
-        first = lane == 0;
-        last = lane == 31;
+        first = lane == 0 ? 0xffffffffu : 0u;
+        last = lane == 31 ? 0xffffffffu : 0u;
         ring = warp_ring;
         const int wx = item % n_wx, wy = item / n_wx;
         const int x0 = wx * WOUT - 4;   // window columns [x0, x0 + 64), periodic
@@ -385,8 +424,8 @@ struct March2 {
         dst1 = uint32_t(a1 * W * 4 + 16 * h);
         // output columns: window columns [4, 60) inside the lattice
         const int xlo = x0 + lane, xhi = x0 + 32 + lane;
-        const bool lo_ok = lane >= 4 && xlo < nx;
-        const bool hi_ok = lane < 28 && xhi < nx;
+        const uint32_t lo_ok = lane >= 4 && xlo < nx ? 1u : 0u;
+        const uint32_t hi_ok = lane < 28 && xhi < nx ? 1u : 0u;
         float *out_lo = out + wrap(xlo, nx);
         float *out_hi = out + wrap(xhi, nx);
         const int y_lo = wy * seg_h;
@@ -396,8 +435,16 @@ struct March2 {
             carry[a][0] = PO::make(0.0f, 0.0f);
             carry[a][1] = PO::make(0.0f, 0.0f);
         }
+        // the ring slots of the rows before J0 are read by the first
+        // iterations (their results only reach halo rows, never stored
+        // ones); they must hold defined values all the same, or the
+        // compiler may substitute any register for them
+#pragma unroll
+        for (int a = 0; a < LAG; ++a) {
+            kring[a].ch = kring[a].sh = kring[a].cl = kring[a].sl = PO::make(0.0f, 0.0f);
+        }
         if constexpr (VIN) {
-            vlive_lo = vlive_hi = false;
+            vlive_lo = vlive_hi = 0u;
         }
         const int J0 = y_lo - LAG;
         const int J1 = y_hi + LAG;  // exclusive
@@ -405,17 +452,47 @@ struct March2 {
         o_in = uint32_t(wrap(J0, ny)) * uint32_t(pitch);
         o_now = o_in;
         o_out = uint32_t(wrap(J0 - LAG, ny)) * uint32_t(pitch);
-        stage<0>();
-        stage<1>();
-        stage<2>();
-        cp_async_wait<2>();
-        __syncwarp();
-        lookup_next<0, 0>();
-        for (int J = J0; J < J1; J += 4) {
-            iter<0>(J + 0, y_lo, st_n, lo_ok, hi_ok, out_lo, out_hi);
-            iter<1>(J + 1, y_lo, st_n, lo_ok, hi_ok, out_lo, out_hi);
-            iter<2>(J + 2, y_lo, st_n, lo_ok, hi_ok, out_lo, out_hi);
-            iter<3>(J + 3, y_lo, st_n, lo_ok, hi_ok, out_lo, out_hi);
+        if constexpr (ILV) {
+            // rows J0 .. J0 + 3 in flight; U_x of row J0 before the loop
+            stage<0>();
+            stage<1>();
+            stage<2>();
+            stage<3>();
+            cp_async_wait<2>();
+            __syncwarp();
+            lookup_into<0>(knext);
+            T2 n4;
+            load_row<0>(p2, p3, n4);
+            ux_layer<0>(p2, n4, knext);
+            ux_layer<1>(p2, n4, knext);
+            ux_layer<2>(p2, n4, knext);
+            ux_layer<3>(p2, n4, knext);
+            ux_layer<4>(p2, n4, knext);
+            ux_layer<5>(p2, n4, knext);
+            ux_layer<6>(p2, n4, knext);
+            ux_layer<7>(p2, n4, knext);
+            store_q4(unsigned(J0 - y_lo) < st_n, lo_ok, hi_ok, out_lo, out_hi, n4);
+            kring[0].copy_from(knext);
+            lookup_into<1>(knext);
+            for (int J = J0; J < J1; J += 4) {
+                iter_ilv<0>(J + 0, y_lo, st_n, lo_ok, hi_ok, out_lo, out_hi);
+                iter_ilv<1>(J + 1, y_lo, st_n, lo_ok, hi_ok, out_lo, out_hi);
+                iter_ilv<2>(J + 2, y_lo, st_n, lo_ok, hi_ok, out_lo, out_hi);
+                iter_ilv<3>(J + 3, y_lo, st_n, lo_ok, hi_ok, out_lo, out_hi);
+            }
+        } else {
+            stage<0>();
+            stage<1>();
+            stage<2>();
+            cp_async_wait<2>();
+            __syncwarp();
+            lookup_next<0, 0>();
+            for (int J = J0; J < J1; J += 4) {
+                iter<0>(J + 0, y_lo, st_n, lo_ok, hi_ok, out_lo, out_hi);
+                iter<1>(J + 1, y_lo, st_n, lo_ok, hi_ok, out_lo, out_hi);
+                iter<2>(J + 2, y_lo, st_n, lo_ok, hi_ok, out_lo, out_hi);
+                iter<3>(J + 3, y_lo, st_n, lo_ok, hi_ok, out_lo, out_hi);
+            }
         }
         cp_async_wait<0>();
         __syncwarp();

@@ -71,12 +71,12 @@ k_step_march(const T *__restrict__ in, T *__restrict__ out, const uint32_t *__re
 }
 
 // The packed-pair variant (FP32 E_z; see qla_march2.cuh): same arguments.
-template <int VM, bool VIN, typename PO>
-__global__ void __launch_bounds__(32 * WARPS, 4)
+template <int VM, bool VIN, typename PO, int MINB = 4, bool ILV = false>
+__global__ void __launch_bounds__(32 * WARPS, MINB)
 k_step_march2(const float *__restrict__ in, float *__restrict__ out,
               const uint32_t *__restrict__ midx, const MedRec<float> *__restrict__ table,
               int nx, int ny, int pitch, size_t plane, int seg_h, int n_wx, int n_items) {
-    using M = March2<VM, VIN, PO>;
+    using M = March2<VM, VIN, PO, ILV>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     typename M::Slot *ring =
         reinterpret_cast<typename M::Slot *>(smem_raw) + (threadIdx.x >> 5) * NSLOT;
@@ -131,14 +131,13 @@ template <typename T, int P, int LX, int VM, bool VIN> struct Variant {
     static constexpr size_t SLOT = sizeof(typename March<T, P, LX, VM, VIN>::Slot);
     static constexpr auto kern = k_step_march<T, P, LX, VM, VIN>;
 };
-template <typename PO, int VM, bool VIN> struct Variant2 {
-    static constexpr int WOUT = March2<VM, VIN, PO>::WOUT;
-    static constexpr size_t SLOT = sizeof(typename March2<VM, VIN, PO>::Slot);
-    static constexpr auto kern = k_step_march2<VM, VIN, PO>;
+template <typename PO, int VM, bool VIN, int MINB = 4, bool ILV = false> struct Variant2 {
+    static constexpr int WOUT = March2<VM, VIN, PO, ILV>::WOUT;
+    static constexpr size_t SLOT = sizeof(typename March2<VM, VIN, PO, ILV>::Slot);
+    static constexpr auto kern = k_step_march2<VM, VIN, PO, MINB, ILV>;
 };
 template <int VM, bool VIN> struct Variant<float, 3, 1, VM, VIN> : Variant2<PairF2, VM, VIN> {};
-template <int VM, bool VIN> struct Variant<float, 3, 5, VM, VIN> : Variant2<PairB64, VM, VIN> {};
-template <int VM, bool VIN> struct Variant<float, 3, 6, VM, VIN> : Variant2<PairMix, VM, VIN> {};
+template <int VM, bool VIN> struct Variant<float, 3, 5, VM, VIN> : Variant2<PairF2, VM, VIN, 4, true> {};
 
 template <typename T, int P, int LX, int VM, bool VIN>
 cudaError_t launch_t(qla_ctx *c, const void *in, void *out, const void *table) {
@@ -211,11 +210,12 @@ cudaError_t launch_ds(qla_ctx *c, const void *in, void *out, bool vin) {
 
 }  // namespace
 
-// Column layout for FP32 E_z contexts: 1, 5, 6 = the packed-pair kernel
-// (two columns 32 apart per lane, FP32x2 arithmetic) in its three pair
-// forms (PairF2, PairB64, PairMix), or 2 or 4 adjacent columns per lane
-// (scalar arithmetic; 2 is the default: at 128 registers four warps per
-// scheduler stay resident, which outweighs the wider window's smaller halo).
+// Column layout for FP32 E_z contexts: 1 = the packed-pair kernel (two
+// columns 32 apart per lane, FP32x2 arithmetic), 5 = the same with U_x of
+// the next row interleaved with U_y of the current one, or 2 or 4 adjacent
+// columns per lane (scalar arithmetic; 2 is the default: at 128 registers
+// four warps per scheduler stay resident, which outweighs the wider
+// window's smaller halo, and the packed forms measured no faster).
 // Other contexts: 2.
 int march_lane_cols(const qla_ctx *c) {
     if (c->prec == QLA_FP32 && c->P == 3 && c->march_lx != 0) return c->march_lx;
@@ -224,7 +224,7 @@ int march_lane_cols(const qla_ctx *c) {
 
 bool march_supported(const qla_ctx *c) {
     const int lx = march_lane_cols(c);
-    const bool packed = lx == 1 || lx == 5 || lx == 6;
+    const bool packed = lx == 1 || lx == 5;
     const int align = packed ? 4 : lx, width = packed ? 64 : 32 * lx;
     return c->nx % align == 0 && c->nx >= width && c->ny >= 8 &&
            c->plane_elems < (size_t(1) << 31) && !(c->tensor && c->P == 6) &&
@@ -256,7 +256,6 @@ cudaError_t launch_step_march(qla_ctx *c, const void *in, void *out, bool vin) {
     switch (march_lane_cols(c)) {
     case 1: return launch_vm<float, 3, 1>(c, in, out, vin);
     case 5: return launch_vm<float, 3, 5>(c, in, out, vin);
-    case 6: return launch_vm<float, 3, 6>(c, in, out, vin);
     case 4: return launch_vm<float, 3, 4>(c, in, out, vin);
     default: return launch_vm<float, 3, 2>(c, in, out, vin);
     }

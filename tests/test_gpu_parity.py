@@ -108,7 +108,8 @@ def test_march_and_tile_kernels_agree_bitwise(shape, te, precision):
     assert ea == eb
 
 
-@pytest.mark.parametrize("lane_cols,rows", [(2, 0), (4, 0), (2, 36), (4, 12)])
+@pytest.mark.parametrize("lane_cols,rows", [(2, 0), (4, 0), (2, 36), (4, 12), (1, 0), (1, 36),
+                                           (5, 0), (5, 12)])
 def test_march_tunings_agree_bitwise(lane_cols, rows):
     """Lane width and segment height change the work split, not the result."""
     nx, ny = 256, 100
