@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--qla-steps", type=int, default=100)
     ap.add_argument("--lane-cols", type=int, default=0, help="marching kernel tuning")
     ap.add_argument("--rows", type=int, default=0, help="marching kernel tuning")
+    ap.add_argument("--step-kernel", choices=["auto", "march", "march_plain", "tile"],
+                    default="auto", help="step kernel (march_plain: no plateau split)")
     ap.add_argument("--double-single", action="store_true",
                     help="FP64 contexts stepped in double-single arithmetic (QLA_DOUBLE_SINGLE)")
     ap.add_argument("--six-planes", action="store_true",
@@ -392,6 +394,7 @@ def gpu_arm(args):
     ds = bool(args.double_single and args.precision == "fp64")
     g = qla.Grid(w.nx, w.ny, w.delta, args.precision, te_only=te, stream=stream,
                  double_single=ds)
+    g.set_step_kernel(args.step_kernel)
     g.set_march_tuning(args.lane_cols, args.rows)
     g.set_medium(n_host)
     g.set_packet(**pk)
@@ -425,6 +428,7 @@ def gpu_arm(args):
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
     launches = g.launches - launches0
+    plan = g.march_plan
     elapsed = start.elapsed_time(stop) / 1e3
     step_time = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     elapsed = max_over_ranks(world, elapsed)
@@ -444,7 +448,7 @@ def gpu_arm(args):
     traffic = (kernel_traffic(int(round(k_used)), sites,
                               "traffic_%s_fp32_ez.json" % args.workload)
                if args.precision == "fp32" and te and not ds and not args.lane_cols
-               and not args.rows else None)
+               and not args.rows and args.step_kernel == "auto" else None)
     g.close()
 
     e2e = None
@@ -487,6 +491,9 @@ def gpu_arm(args):
                        "qla_steps_per_bench_step": S, "planes": P,
                        "potential": "rotation", "time_block": k_used,
                        "lane_cols": args.lane_cols or "auto", "rows": args.rows or "auto",
+                       "step_kernel": args.step_kernel,
+                       "plateau_items": "%d of %d work items, %d plateaus" % (plan[1], plan[0],
+                                                                             plan[2]),
                        "energy_drift": drift,
                        "l2": "state %.0f MB > 129 MB L2, no flush" % (2 * P * elt * sites / 2e6)},
             "roofline": roofline(P, elt, kernel_su_per_s, traffic,
@@ -518,6 +525,7 @@ def e2e_run(args, w, te, n_host, pk, world, dev):
     ez = torch.empty((w.ny, w.nx), dtype=torch.float64).pin_memory()
     g = qla.Grid(w.nx, w.ny, w.delta, args.precision, te_only=te, stream=stream,
                  double_single=bool(args.double_single and args.precision == "fp64"))
+    g.set_step_kernel(args.step_kernel)
     g.set_march_tuning(args.lane_cols, args.rows)
     S = args.qla_steps
     barrier(world)

@@ -60,6 +60,15 @@ Layout layout_for(int nx, int ny, int prec, unsigned flags) {
     if ((flags & QLA_DOUBLE_SINGLE) && prec == QLA_FP64) {
         L.dstable = off; off += align256((UNIFORM_SLOTS + sites) * sizeof(MedRec<dsf>));
     }
+    // FP32 E_z: the plateau-split step's unit list (int4 entries): three
+    // units per 120-column window and segment of at least 16 rows, plus
+    // whole-block padding
+    L.items = L.items_cap = 0;
+    if (prec == QLA_FP32 && P == 3) {
+        L.items_cap = 3 * size_t((nx + 119) / 120) * size_t((ny + 15) / 16) +
+                      size_t(UNI_SETS + 1) * 4;
+        L.items = off; off += align256(L.items_cap * 16);
+    }
     L.total = off;
     return L;
 }
@@ -202,6 +211,10 @@ qla_status qla_init_grid(qla_ctx **out, int nx, int ny, double delta, int precis
         if (c->P == 6) c->ttable = c->ws + L.ttable;
     }
     if (flags & QLA_DOUBLE_SINGLE) c->dstable = c->ws + L.dstable;
+    if (L.items_cap) {
+        c->items = reinterpret_cast<int *>(c->ws + L.items);
+        c->items_cap = L.items_cap;
+    }
     // both state buffers start at zero (pad columns included)
     if (cudaMemsetAsync(c->ws + L.state[0], 0, L.midx - L.state[0], c->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -251,6 +264,7 @@ qla_status qla_set_medium_tensor(qla_ctx *c, const double *n_x, const double *n_
              "qla_set_medium_tensor: clear");
     QLA_CUDA(c, cudaMemsetAsync(c->counter, 0, 4, c->stream), "qla_set_medium_tensor: clear");
     QLA_CUDA(c, launch_medium(c), "qla_set_medium_tensor: kernel");
+    c->medium_gen++;
     if (c->P == 6) QLA_CUDA(c, launch_medium_tensor(c), "qla_set_medium_tensor: records");
     QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_set_medium_tensor: sync");
     c->has_medium = true;
@@ -275,6 +289,7 @@ qla_status qla_set_medium(qla_ctx *c, const double *n_host) {
     QLA_CUDA(c, cudaMemsetAsync(c->keys, 0, UNIFORM_SLOTS * 8, c->stream), "qla_set_medium: clear");
     QLA_CUDA(c, cudaMemsetAsync(c->counter, 0, 4, c->stream), "qla_set_medium: clear");
     QLA_CUDA(c, launch_medium(c), "qla_set_medium: kernel");
+    c->medium_gen++;
     c->has_medium = true;
     return QLA_OK;
 }
@@ -481,6 +496,7 @@ qla_status qla_step(qla_ctx *c, long long n_steps) {
         return QLA_OK;
     }
     const bool march = c->step_kernel == QLA_KERNEL_MARCH ||
+                       c->step_kernel == QLA_KERNEL_MARCH_PLAIN ||
                        (c->step_kernel == QLA_KERNEL_AUTO && march_ok(c));
     for (long long k = 0; k < n_steps; ++k) {
         const bool vin = c->pending_v;
@@ -585,12 +601,13 @@ qla_status qla_probe(qla_ctx *c, int count, const int *i, const int *j, double *
 qla_status qla_set_step_kernel(qla_ctx *c, int kernel) {
     qla_status s = usable(c);
     if (s != QLA_OK) return s;
-    if (kernel < QLA_KERNEL_AUTO || kernel > QLA_KERNEL_MARCH)
+    if (kernel < QLA_KERNEL_AUTO || kernel > QLA_KERNEL_MARCH_PLAIN)
         return fail(c, QLA_EINVAL, "qla_set_step_kernel: unknown kernel %d", kernel);
-    if (kernel == QLA_KERNEL_MARCH && ((c->tensor && c->P == 6) || c->vmode == V_LCU))
+    const bool march = kernel == QLA_KERNEL_MARCH || kernel == QLA_KERNEL_MARCH_PLAIN;
+    if (march && ((c->tensor && c->P == 6) || c->vmode == V_LCU))
         return fail(c, QLA_EINVAL, "qla_set_step_kernel: six-plane tensor media and the LCU "
                                    "potential use the tile kernel");
-    if (kernel == QLA_KERNEL_MARCH && !march_ok(c))
+    if (march && !march_ok(c))
         return fail(c, QLA_EINVAL, "qla_set_step_kernel: the marching kernel needs nx a multiple "
                                    "of its lane width (4 for the packed-pair layout), a window "
                                    "of columns and ny >= 8");
@@ -612,6 +629,16 @@ qla_status qla_set_march_tuning(qla_ctx *c, int lane_cols, int rows) {
 }
 
 long long qla_launch_count(const qla_ctx *c) { return c ? c->launches : 0; }
+
+qla_status qla_march_plan(const qla_ctx *c, int *n_items, int *n_plateau_items, int *n_sets) {
+    if (!c) return QLA_EINVAL;
+    const auto &u = c->uplan;
+    const bool live = u.gen == c->medium_gen && u.sets.n_sets > 0;
+    if (n_items) *n_items = live ? u.n_items : 0;
+    if (n_plateau_items) *n_plateau_items = live ? u.n_uniform : 0;
+    if (n_sets) *n_sets = live ? u.sets.n_sets : 0;
+    return QLA_OK;
+}
 
 const char *qla_last_error(const qla_ctx *c) { return c ? c->err.c_str() : "null context"; }
 

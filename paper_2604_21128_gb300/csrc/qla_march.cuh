@@ -208,7 +208,13 @@ __device__ __forceinline__ void cp_async_wait() {
 
 constexpr int NSLOT = 4;   // rows staged per warp: the current one and 3 ahead
 
-template <typename T, int P, int LX, int VM, bool VIN>
+// UNI: a work item whose every entering site shares one record (a plateau
+// of the medium, where the four neighbours of each site carry its n): the
+// collision coefficients are one warp-uniform value `ku` instead of the
+// register ring (no index rows staged, no record lookups, and no potential
+// step: V is the identity on shared-record sites).  Given the coefficients
+// from the constant bank, the rotations read one register operand fewer.
+template <typename T, int P, int LX, int VM, bool VIN, bool UNI = false>
 struct March {
     using CC = typename Coef<T>::C;
     using CV = typename Coef<T>::V;
@@ -247,6 +253,17 @@ struct March {
     // FP64 slower the other way round)
     static constexpr bool EARLY = std::is_same<T, double>::value;
     CC knext[EARLY ? LX : 1];
+    CC ku[UNI ? LX : 1];    // UNI: the item's coefficients, copies of one value
+    __device__ __forceinline__ void set_uniform(CC k) {
+#pragma unroll
+        for (int x = 0; x < (UNI ? LX : 1); ++x) ku[x] = k;
+    }
+    // coefficients of the row in ring slot S
+    template <int S>
+    __device__ __forceinline__ const CC (&ring_coef() const)[LX] {
+        if constexpr (UNI) return ku;
+        else return kring[S];
+    }
     // row offsets: next row to stage, the two output rows
     uint32_t o_in, o_now, o_out;
 
@@ -255,19 +272,20 @@ struct March {
         return o == total ? 0u : o;
     }
 
-    // Stage the row at offset o_in into slot S (one commit group).
-    template <int S>
-    __device__ __forceinline__ void stage() {
+    // Stage the row at offset o_in into slot `sl` (one commit group).
+    __device__ __forceinline__ void stage_into(Slot &sl) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             const int p = plane_of<P>(c);
             if (p >= 0)
-                cp_async<LX * sizeof(T)>(&ring[S].q[slot_of<P>(c)][lc], in + p * plane + o_in);
+                cp_async<LX * sizeof(T)>(&sl.q[slot_of<P>(c)][lc], in + p * plane + o_in);
         }
-        cp_async<LX * 4>(&ring[S].idx[lc], midx + o_in);
+        if constexpr (!UNI) cp_async<LX * 4>(&sl.idx[lc], midx + o_in);
         cp_async_commit();
         o_in = next_row(o_in);
     }
+    template <int S>
+    __device__ __forceinline__ void stage() { stage_into(ring[S]); }
 
     // Row J + 1's records (staging slot S) into ring slot K of the collision
     // coefficients and into vnext.
@@ -292,24 +310,39 @@ struct March {
     // fall in [st_lo, st_lo + st_n).
     template <int PH>
     __device__ __forceinline__ void iter(int J, int st_lo, unsigned st_n) {
+        iter_body<PH>(J, st_lo, st_n, ring[PH], ring[(PH + 3) & (NSLOT - 1)]);
+    }
+    // UNI: the same with the staging slots chosen at run time (phase ph of
+    // row J), so that the march loop need not be unrolled four times: the
+    // four-column body is large, and four copies of it overflow the
+    // instruction cache
+    __device__ __forceinline__ void iter_rt(int J, int st_lo, unsigned st_n, int ph) {
+        static_assert(UNI, "only plateau items have no ring slots to name");
+        iter_body<0>(J, st_lo, st_n, ring[ph], ring[(ph + 3) & (NSLOT - 1)]);
+    }
+    // cur: row J's staging slot; nxt: the slot row J - 1 used, refilled with
+    // row J + 3
+    template <int PH>
+    __device__ __forceinline__ void iter_body(int J, int st_lo, unsigned st_n, Slot &cur,
+                                              Slot &nxt) {
         constexpr int S0 = PH, S1 = (PH + 3) & 3, S2 = (PH + 2) & 3, S3 = (PH + 1) & 3;
         // stage row J + 3 into the slot row J - 1 used; wait for row J + 1
-        stage<(PH + 3) & (NSLOT - 1)>();
+        stage_into(nxt);
         cp_async_wait<NSLOT - 2>();
         T q[6][LX];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             if (plane_of<P>(c) >= 0) {
 #pragma unroll
-                for (int x = 0; x < LX; ++x) q[c][x] = ring[PH].q[slot_of<P>(c)][lc + x];
+                for (int x = 0; x < LX; ++x) q[c][x] = cur.q[slot_of<P>(c)][lc + x];
             }
         }
-        if constexpr (EARLY) {
+        if constexpr (EARLY && !UNI) {
 #pragma unroll
             for (int x = 0; x < LX; ++x) kring[S0][x] = knext[x];
         }
         // the previous step's V_x, V_y on the entering row
-        if constexpr (VIN) {
+        if constexpr (VIN && !UNI) {
 #pragma unroll
             for (int x = 0; x < LX; ++x) {
                 if (!vlive[x]) continue;
@@ -323,9 +356,9 @@ struct March {
             }
         }
         // (FP64) row J + 1's records fly while this row computes
-        if constexpr (EARLY) lookup_next<(PH + 1) & (NSLOT - 1), S3>();
+        if constexpr (EARLY && !UNI) lookup_next<(PH + 1) & (NSLOT - 1), S3>();
 
-        apply_ux<T, P, LX>(q, kring[S0]);                          // U_x, row J
+        apply_ux<T, P, LX>(q, ring_coef<S0>());                    // U_x, row J
 
         // planes U_y does not touch are final for row J now
         if (unsigned(J - st_lo) < st_n) {
@@ -337,17 +370,17 @@ struct March {
         }
         o_now = next_row(o_now);
 
-        uy_local<T, P, LX, 0>(q, kring[S0]);                       // L1, row J
-        uy_neighbour<T, P, LX, 1>(q, carry[0], kring[S0]);         // L2 -> row J-1
-        uy_local<T, P, LX, 2>(q, kring[S1]);                       // L3, row J-1
-        uy_neighbour<T, P, LX, 3>(q, carry[1], kring[S2]);         // L4 -> row J-2
-        uy_local<T, P, LX, 4>(q, kring[S2]);                       // L5, row J-2
-        uy_neighbour<T, P, LX, 5>(q, carry[2], kring[S3]);         // L6 -> row J-3
-        uy_local<T, P, LX, 6>(q, kring[S3]);                       // L7, row J-3
-        uy_neighbour<T, P, LX, 7>(q, carry[3], kring[S3]);         // L8 -> row J-4
+        uy_local<T, P, LX, 0>(q, ring_coef<S0>());                 // L1, row J
+        uy_neighbour<T, P, LX, 1>(q, carry[0], ring_coef<S0>());   // L2 -> row J-1
+        uy_local<T, P, LX, 2>(q, ring_coef<S1>());                 // L3, row J-1
+        uy_neighbour<T, P, LX, 3>(q, carry[1], ring_coef<S2>());   // L4 -> row J-2
+        uy_local<T, P, LX, 4>(q, ring_coef<S2>());                 // L5, row J-2
+        uy_neighbour<T, P, LX, 5>(q, carry[2], ring_coef<S3>());   // L6 -> row J-3
+        uy_local<T, P, LX, 6>(q, ring_coef<S3>());                 // L7, row J-3
+        uy_neighbour<T, P, LX, 7>(q, carry[3], ring_coef<S3>());   // L8 -> row J-4
         // row J - 3's coefficients (slot S3) are dead: row J + 1's records
         // go straight into that slot
-        if constexpr (!EARLY) lookup_next<(PH + 1) & (NSLOT - 1), S3>();
+        if constexpr (!EARLY && !UNI) lookup_next<(PH + 1) & (NSLOT - 1), S3>();
 
         // the U_y planes of row J - 4 are final
         if (unsigned(J - LAG - st_lo) < st_n) {
@@ -365,20 +398,27 @@ struct March {
     // warp's staging buffer.
     __device__ __forceinline__ void run_item(int nx, int ny, int seg_h, int n_wx, int item,
                                              Slot *warp_ring) {
+        const int wx = item % n_wx, wy = item / n_wx;
+        const int x_out = wx * WOUT;
+        run_unit(nx, ny, x_out, min(WOUT, nx - x_out), wy * seg_h, min(ny, wy * seg_h + seg_h),
+                 warp_ring);
+    }
+
+    // The same for an explicit unit: store columns [x_out, x_out + w_out)
+    // (w_out <= WOUT, x_out + w_out <= nx, both multiples of LX) of rows
+    // [y_lo, y_hi); the window starts 4 columns left of x_out (periodic).
+    __device__ __forceinline__ void run_unit(int nx, int ny, int x_out, int w_out, int y_lo,
+                                             int y_hi, Slot *warp_ring) {
         const int lane = threadIdx.x & 31;
         ring = warp_ring;
         lc = lane * LX;
-        const int wx = item % n_wx, wy = item / n_wx;
-        // window columns [x0, x0 + W), x0 = wx*WOUT - 4 (periodic)
-        int xl = wx * WOUT - 4 + lane * LX;
-        const bool lane_store_ok = xl >= 0 ? xl < nx : true;
+        // window columns [x0, x0 + W), x0 = x_out - 4 (periodic)
+        int xl = x_out - 4 + lane * LX;
         xl %= nx;
         if (xl < 0) xl += nx;
         in += xl;
         out += xl;
         midx += xl;
-        const int y_lo = wy * seg_h;
-        const int y_hi = min(ny, y_lo + seg_h);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -395,10 +435,10 @@ struct March {
 #pragma unroll
             for (int x = 0; x < LX; ++x) kring[a][x] = CC{};
         // rows y_lo-4 .. y_hi+3 enter; rows y_lo .. y_hi-1 are stored by the
-        // lanes whose columns are all inside [4, W - 4) and below nx
+        // lanes whose columns are all inside [4, 4 + w_out)
         const int J0 = y_lo - LAG;
         const int J1 = y_hi + LAG;  // exclusive
-        const bool lane_out = lc >= 4 && lc + LX <= W - 4 && lane_store_ok;
+        const bool lane_out = lc >= 4 && lc + LX <= 4 + w_out;
         const unsigned st_n = lane_out ? unsigned(y_hi - y_lo) : 0u;
         o_in = uint32_t(wrap(J0, ny)) * uint32_t(pitch);
         o_now = o_in;
@@ -408,12 +448,17 @@ struct March {
         stage<1>();
         stage<2>();
         cp_async_wait<2>();
-        lookup_next<0, 0>();
-        for (int J = J0; J < J1; J += 4) {
-            iter<0>(J + 0, y_lo, st_n);
-            iter<1>(J + 1, y_lo, st_n);
-            iter<2>(J + 2, y_lo, st_n);
-            iter<3>(J + 3, y_lo, st_n);
+        if constexpr (UNI && LX == 4) {
+#pragma unroll 1
+            for (int J = J0; J < J1; ++J) iter_rt(J, y_lo, st_n, (J - J0) & (NSLOT - 1));
+        } else {
+            if constexpr (!UNI) lookup_next<0, 0>();
+            for (int J = J0; J < J1; J += 4) {
+                iter<0>(J + 0, y_lo, st_n);
+                iter<1>(J + 1, y_lo, st_n);
+                iter<2>(J + 2, y_lo, st_n);
+                iter<3>(J + 3, y_lo, st_n);
+            }
         }
         cp_async_wait<0>();
     }

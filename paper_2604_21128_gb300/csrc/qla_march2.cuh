@@ -85,8 +85,12 @@ __device__ __forceinline__ void bond_rot2(typename PO::T &u, typename PO::T &m, 
     else rotate2<PO, G>(u, m, k);
 }
 
-template <int VM, bool VIN, typename PO = PairF2, bool ILV = false>
+// UNI: a plateau item (see March in qla_march.cuh): one coefficient set
+// `ku` for every row and column, no index rows, no lookups, no potential
+// step.  Not combined with ILV.
+template <int VM, bool VIN, typename PO = PairF2, bool ILV = false, bool UNI = false>
 struct March2 {
+    static_assert(!(ILV && UNI), "the interleaved march has no plateau form");
     using T2 = typename PO::T;
     static constexpr int W = 64;        // window columns (lane l: l and l + 32)
     static constexpr int WOUT = W - 8;  // stored columns
@@ -109,9 +113,22 @@ struct March2 {
     // destinations as byte offsets inside a slot
     const char *src0, *src1;
     uint32_t dst0, dst1;
+    bool idx_lane;           // the lane's second copy is of the index row
 
     T2 carry[4][2];          // U_y neighbour layers: [layer][value]
     K2<PO> kring[LAG];       // collision coefficients of the rows in flight
+    K2<PO> ku;               // UNI: the item's coefficients on both halves
+    template <int S>
+    __device__ __forceinline__ const K2<PO> &ring_coef() const {
+        if constexpr (UNI) return ku;
+        else return kring[S];
+    }
+    __device__ __forceinline__ void set_uniform(float4 k) {
+        ku.ch = PO::make(k.x, k.x);
+        ku.sh = PO::make(k.y, k.y);
+        ku.cl = PO::make(k.z, k.z);
+        ku.sl = PO::make(k.w, k.w);
+    }
     float4 vlo, vhi;         // row J+1's potential coefficients (low, high column)
     // row J+1's sites have their own records (0 or 1; integers, like the
     // other per-lane flags, so that no predicate stays live across the march)
@@ -131,7 +148,7 @@ struct March2 {
     __device__ __forceinline__ void stage() {
         unsigned char *base = reinterpret_cast<unsigned char *>(ring + S);
         cp_async<16>(base + dst0, src0 + 4ull * o_in);
-        cp_async<16>(base + dst1, src1 + 4ull * o_in);
+        if (!UNI || !idx_lane) cp_async<16>(base + dst1, src1 + 4ull * o_in);
         cp_async_commit();
         o_in = next_row(o_in);
     }
@@ -267,13 +284,13 @@ struct March2 {
         float l2 = sl.q[0][lane], h2 = sl.q[0][lane + 32];
         float l3 = sl.q[1][lane], h3 = sl.q[1][lane + 32];
         float l4 = sl.q[2][lane], h4 = sl.q[2][lane + 32];
-        if constexpr (VIN) {
+        if constexpr (VIN && !UNI) {
             if (vlive_lo) potential(l2, l3, l4, vlo);
             if (vlive_hi) potential(h2, h3, h4, vhi);
         }
         T2 q2 = PO::make(l2, h2), q3 = PO::make(l3, h3), q4 = PO::make(l4, h4);
 
-        const K2<PO> &k0 = kring[S0];
+        const K2<PO> &k0 = ring_coef<S0>();
         ux_layer<0>(q2, q4, k0);
         ux_layer<1>(q2, q4, k0);
         ux_layer<2>(q2, q4, k0);
@@ -290,16 +307,16 @@ struct March2 {
         }
         o_now = next_row(o_now);
 
-        uy_local<0>(q2, q3, kring[S0]);                  // L1, row J
-        uy_neighbour<1>(q2, q3, carry[0], kring[S0]);    // L2 -> row J-1
-        uy_local<2>(q2, q3, kring[S1]);                  // L3, row J-1
-        uy_neighbour<3>(q2, q3, carry[1], kring[S2]);    // L4 -> row J-2
-        uy_local<4>(q2, q3, kring[S2]);                  // L5, row J-2
-        uy_neighbour<5>(q2, q3, carry[2], kring[S3]);    // L6 -> row J-3
-        uy_local<6>(q2, q3, kring[S3]);                  // L7, row J-3
-        uy_neighbour<7>(q2, q3, carry[3], kring[S3]);    // L8 -> row J-4
+        uy_local<0>(q2, q3, ring_coef<S0>());                  // L1, row J
+        uy_neighbour<1>(q2, q3, carry[0], ring_coef<S0>());    // L2 -> row J-1
+        uy_local<2>(q2, q3, ring_coef<S1>());                  // L3, row J-1
+        uy_neighbour<3>(q2, q3, carry[1], ring_coef<S2>());    // L4 -> row J-2
+        uy_local<4>(q2, q3, ring_coef<S2>());                  // L5, row J-2
+        uy_neighbour<5>(q2, q3, carry[2], ring_coef<S3>());    // L6 -> row J-3
+        uy_local<6>(q2, q3, ring_coef<S3>());                  // L7, row J-3
+        uy_neighbour<7>(q2, q3, carry[3], ring_coef<S3>());    // L8 -> row J-4
         // row J - 3's coefficients are dead: row J + 1's go into that slot
-        lookup_next<(PH + 1) & (NSLOT - 1), S3>();
+        if constexpr (!UNI) lookup_next<(PH + 1) & (NSLOT - 1), S3>();
 
         // q2, q3 of row J - 4 are final
         if (unsigned(J - LAG - st_lo) < st_n) {
@@ -422,6 +439,7 @@ struct March2 {
                        : reinterpret_cast<const char *>(in + size_t(a1) * plane + gc);
         dst0 = uint32_t(a0 * W * 4 + 16 * h);
         dst1 = uint32_t(a1 * W * 4 + 16 * h);
+        idx_lane = a1 == 3;
         // output columns: window columns [4, 60) inside the lattice
         const int xlo = x0 + lane, xhi = x0 + 32 + lane;
         const uint32_t lo_ok = lane >= 4 && xlo < nx ? 1u : 0u;
@@ -486,7 +504,7 @@ struct March2 {
             stage<2>();
             cp_async_wait<2>();
             __syncwarp();
-            lookup_next<0, 0>();
+            if constexpr (!UNI) lookup_next<0, 0>();
             for (int J = J0; J < J1; J += 4) {
                 iter<0>(J + 0, y_lo, st_n, lo_ok, hi_ok, out_lo, out_hi);
                 iter<1>(J + 1, y_lo, st_n, lo_ok, hi_ok, out_lo, out_hi);

@@ -25,7 +25,7 @@ QLA_POTENTIAL_NONE = 4
 QLA_ANISOTROPIC = 8
 QLA_POTENTIAL_LCU = 16
 QLA_DOUBLE_SINGLE = 32
-QLA_KERNEL_AUTO, QLA_KERNEL_TILE, QLA_KERNEL_MARCH = 0, 1, 2
+QLA_KERNEL_AUTO, QLA_KERNEL_TILE, QLA_KERNEL_MARCH, QLA_KERNEL_MARCH_PLAIN = 0, 1, 2, 3
 
 STATUS = {0: "QLA_OK", 1: "QLA_EINVAL", 2: "QLA_ESTATE", 3: "QLA_ENOMEM",
           4: "QLA_ECUDA", 5: "QLA_ETIMEOUT", 6: "QLA_ENONFINITE"}
@@ -72,6 +72,7 @@ def load():
                            ("qla_probe", [c_vp, c_int, c_vp, c_vp, c_vp]),
                            ("qla_set_step_kernel", [c_vp, c_int]),
                            ("qla_set_march_tuning", [c_vp, c_int, c_int]),
+                           ("qla_march_plan", [c_vp, c_vp, c_vp, c_vp]),
                            ("qla_set_packet_window", [c_vp, ctypes.POINTER(qla_packet), c_int,
                                                       c_int, c_int, c_int]),
                            ("qla_pack_box", [c_vp, c_int, c_int, c_int, c_int, c_vp]),
@@ -300,6 +301,13 @@ def qla_launch_count(ctx):
     return int(load().qla_launch_count(ctx))
 
 
+def qla_march_plan(ctx):
+    """(work items, plateau items, plateau records) of the marching plan."""
+    a, b, n = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(ctx, load().qla_march_plan(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
+    return a.value, b.value, n.value
+
+
 def qla_last_error(ctx):
     return load().qla_last_error(ctx).decode()
 
@@ -402,8 +410,9 @@ class Grid:
             return qla_probe(self._ctx, i, j)
 
     def set_step_kernel(self, kernel):
-        """"auto", "tile" or "march" (see qla_set_step_kernel)."""
-        k = {"auto": QLA_KERNEL_AUTO, "tile": QLA_KERNEL_TILE, "march": QLA_KERNEL_MARCH}
+        """"auto", "tile", "march" or "march_plain" (see qla_set_step_kernel)."""
+        k = {"auto": QLA_KERNEL_AUTO, "tile": QLA_KERNEL_TILE, "march": QLA_KERNEL_MARCH,
+             "march_plain": QLA_KERNEL_MARCH_PLAIN}
         qla_set_step_kernel(self._ctx, k.get(kernel, kernel))
 
     def set_march_tuning(self, lane_cols=0, rows=0):
@@ -451,6 +460,11 @@ class Grid:
     @property
     def launches(self):
         return qla_launch_count(self._ctx)
+
+    @property
+    def march_plan(self):
+        """(work items, plateau items, plateau records) of the last marching step."""
+        return qla_march_plan(self._ctx)
 
     def close(self):
         if getattr(self, "_borrowed", False):

@@ -121,6 +121,75 @@ def test_march_tunings_agree_bitwise(lane_cols, rows):
     assert np.array_equal(ref, got)
 
 
+def plateau_medium(nx, ny):
+    """Three plateaus of n with sharp edges (n = 2 background, n = 1 inside an
+    ellipse, n = 3 in a band) and a patch of random n: work items of every
+    kind for the plateau split."""
+    y, x = np.mgrid[0:ny, 0:nx]
+    n = np.full((ny, nx), 2.0)
+    n[:, : nx // 3] = 3.0
+    n[((x - nx / 2) / (nx / 6)) ** 2 + ((y - ny / 2) / (ny / 4)) ** 2 < 1.0] = 1.0
+    n[-40:, -70:] = np.random.default_rng(3).uniform(1.2, 2.8, (40, 70))
+    return n
+
+
+def fp32_run(n, steps, q0, kernel, rows=0, potential="rotation", lane_cols=0):
+    ny, nx = n.shape
+    with qla.Grid(nx, ny, 1.0, "fp32", te_only=True, potential=potential) as g:
+        g.set_step_kernel(kernel)
+        g.set_march_tuning(lane_cols, rows)
+        g.set_medium(n)
+        g.set_state(q0)
+        g.step(steps)
+        return g.get_state(), g.energy(), g.march_plan
+
+
+@pytest.mark.parametrize("lane_cols,rows,potential",
+                         [(0, 0, "rotation"), (0, 16, "rotation"), (0, 40, "literal"),
+                          (0, 20, "none"), (2, 36, "rotation")])
+def test_plateau_split_agrees_bitwise(lane_cols, rows, potential):
+    """Work items on plateaus of n run with the plateau's coefficients as a
+    block-uniform argument (no record lookups, no potential step); the state
+    and the energy are those of the unsplit marching kernel and of the tile
+    kernel bit for bit, next to the plateaus' edges too."""
+    nx, ny = 1024, 384
+    n = plateau_medium(nx, ny)
+    q0 = inputs.random_state(nx, ny, seed=31, planes=3)
+    split = fp32_run(n, 11, q0, "march", rows, potential, lane_cols)
+    items, plateau, sets = split[2]
+    assert 2 <= sets <= 3 and 0 < plateau < items, split[2]
+    for kernel in ("march_plain", "tile"):
+        other = fp32_run(n, 11, q0, kernel, rows, potential, lane_cols)
+        assert other[2] == (0, 0, 0)
+        assert np.array_equal(split[0], other[0]), kernel
+        assert split[1] == other[1], kernel
+
+
+def test_plateau_plan_follows_the_medium():
+    """A new medium (or tuning) replaces the plan at the next step: a lattice
+    without plateaus then runs every item on the general path."""
+    nx, ny = 1024, 384
+    q0 = inputs.random_state(nx, ny, seed=32, planes=3)
+    rough = inputs.random_medium(nx, ny, seed=33, lo=1.0, hi=2.5)
+    with qla.Grid(nx, ny, 1.0, "fp32", te_only=True) as g:
+        g.set_medium(plateau_medium(nx, ny))
+        g.set_state(q0)
+        g.step(3)
+        assert g.march_plan[1] > 0
+        g.set_march_tuning(0, 16)
+        assert g.march_plan[1] > 0      # kept until the next step rebuilds it
+        g.step(1)
+        assert g.march_plan[0] == ((nx + 119) // 120) * (ny // 16)  # 9 windows x 24 segments
+        g.set_medium(rough)
+        assert g.march_plan == (0, 0, 0)
+        g.set_state(q0)
+        g.step(5)
+        got = g.get_state()
+        assert g.march_plan == (0, 0, 0)
+    want, _, _ = fp32_run(rough, 5, q0, "tile")
+    assert np.array_equal(got, want)
+
+
 def test_medium_with_more_distinct_values_than_shared_slots():
     """4356 plateaus of distinct n: more keys than the 4096 shared-record
     slots, so part of the uniform sites take their own records."""
