@@ -314,8 +314,8 @@ struct March {
     }
     // UNI: the same with the staging slots chosen at run time (phase ph of
     // row J), so that the march loop need not be unrolled four times: the
-    // four-column body is large, and four copies of it overflow the
-    // instruction cache
+    // four-column body is large, and four copies of it overflowed the
+    // instruction cache (no-instruction stalls 1.49 per issue)
     __device__ __forceinline__ void iter_rt(int J, int st_lo, unsigned st_n, int ph) {
         static_assert(UNI, "only plateau items have no ring slots to name");
         iter_body<0>(J, st_lo, st_n, ring[ph], ring[(ph + 3) & (NSLOT - 1)]);
@@ -449,7 +449,10 @@ struct March {
         stage<2>();
         cp_async_wait<2>();
         if constexpr (UNI && LX == 4) {
-#pragma unroll 1
+            // two rows per loop body (all-plateau 16384^2 lattice, 256-row
+            // segments: 1.43 ms per step against 1.50 ms with one row and
+            // 1.47 ms with four rows on compile-time slots)
+#pragma unroll 2
             for (int J = J0; J < J1; ++J) iter_rt(J, y_lo, st_n, (J - J0) & (NSLOT - 1));
         } else {
             if constexpr (!UNI) lookup_next<0, 0>();

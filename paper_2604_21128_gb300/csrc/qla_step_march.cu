@@ -322,8 +322,10 @@ cudaError_t build_plateau_plan(qla_ctx *c, int seg) {
 template <int VM, bool VIN>
 cudaError_t launch_split(qla_ctx *c, const void *in, void *out) {
     auto kern = k_step_march_split<VM, VIN>;
-    // the four-column ring of four warps
-    const size_t smem = sizeof(typename March<float, 3, 4, VM, VIN, true>::Slot) * NSLOT * WARPS;
+    // the larger staging ring of four warps
+    constexpr size_t slot = std::max(sizeof(typename March<float, 3, 4, VM, VIN, true>::Slot),
+                                     sizeof(typename March<float, 3, 2, VM, VIN, false>::Slot));
+    const size_t smem = slot * NSLOT * WARPS;
     static const cudaError_t attr =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (attr != cudaSuccess) return attr;
