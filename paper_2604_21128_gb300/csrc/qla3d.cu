@@ -808,6 +808,12 @@ __global__ void k3_dedup(const double *__restrict__ n, int nx, int ny, int nz, i
             unsigned h = unsigned(mix64(key)) & (UNIFORM_SLOTS - 1);
             bool placed = false;
             for (int probe = 0; probe < UNIFORM_SLOTS; ++probe) {
+                // found with a plain read once placed (no contended atomic)
+                if (__ldcg(&keys[h]) == key) {
+                    id = h;
+                    placed = true;
+                    break;
+                }
                 const unsigned long long prev = atomicCAS(&keys[h], 0ull, key);
                 if (prev == 0ull || prev == key) {
                     owner = prev == 0ull;
