@@ -165,6 +165,27 @@ def test_plateau_split_agrees_bitwise(lane_cols, rows, potential):
         assert split[1] == other[1], kernel
 
 
+def test_plateau_split_limits():
+    """More plateau records than the launch has block ranges for (12 bands:
+    8 take the plateau path, the rest the general one), and lattices the
+    split does not take (nx not a multiple of 4, narrower than a 128-column
+    window): all bitwise equal to the tile kernel."""
+    nx, ny = 12 * 256, 192
+    n = np.repeat(1.0 + 0.125 * np.arange(12), 256)[None, :].repeat(ny, axis=0)
+    q0 = inputs.random_state(nx, ny, seed=34, planes=3)
+    split = fp32_run(n, 7, q0, "march")
+    assert split[2][2] == 8 and 0 < split[2][1] < split[2][0], split[2]
+    tile = fp32_run(n, 7, q0, "tile")
+    assert np.array_equal(split[0], tile[0]) and split[1] == tile[1]
+    for nx2 in (1030, 100):
+        n2 = plateau_medium(nx2, 160)
+        q2 = inputs.random_state(nx2, 160, seed=35, planes=3)
+        a = fp32_run(n2, 5, q2, "march")
+        assert a[2] == (0, 0, 0), nx2
+        b = fp32_run(n2, 5, q2, "tile")
+        assert np.array_equal(a[0], b[0]), nx2
+
+
 def test_plateau_plan_follows_the_medium():
     """A new medium (or tuning) replaces the plan at the next step: a lattice
     without plateaus then runs every item on the general path."""
