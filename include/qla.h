@@ -265,15 +265,15 @@ qla_status qla_set_packet_window(qla_ctx *ctx, const qla_packet *p, int i0, int 
  * lattice, including one whose live planes exceed its 32-bit element
  * offsets: planes x ny x padded nx > 2^32).  Both compute the same operator sequence; FP64 results agree to
  * rounding order.
- * Plateau split (FP32 E_z contexts, two columns per lane): the marching
- * step runs work items whose entering sites all share one record -- a
- * plateau of n where every site's four neighbours carry its n -- with that
- * record's collision coefficients as a block-uniform kernel argument (no
- * index rows, no record lookups, no potential step, which is the identity
- * there), up to 8 distinct plateaus per lattice; all other items take the
- * general path.  Results are bitwise those of the unsplit kernel.  The
- * first marching step after qla_set_medium or a tuning change classifies
- * the items (one small kernel and one synchronisation of the context's
+ * Plateau split (FP32 E_z contexts, two columns per lane, nx a multiple of
+ * 4 and at least 128): the marching step runs work items whose entering
+ * sites all share one record -- a plateau of n where every site's four
+ * neighbours carry its n -- four columns per lane with that record's
+ * collision coefficients (no index rows, no record lookups, no potential
+ * step, which is the identity there); all other items take the general
+ * path.  Results are bitwise those of the unsplit kernel.  The first
+ * marching step after qla_set_medium or a tuning change classifies the
+ * items (one small kernel and one synchronisation of the context's
  * stream), so it must not be the first call inside a stream capture.
  * QLA_KERNEL_MARCH_PLAIN = the marching kernel without the split. */
 typedef enum {
@@ -597,10 +597,11 @@ long long qla_launch_count(const qla_ctx *ctx);
 
 /* The plateau plan of the FP32 E_z marching step (see qla_set_step_kernel),
  * as built for the current medium and tuning by the last marching step:
- * work items per step, items run on the plateau path, and plateau records
- * with their own block range.  All zero when no plan is in use (other
- * contexts, another kernel, or no step since the medium or the tuning
- * changed).  Any output pointer may be NULL.  QLA_EINVAL for a null ctx. */
+ * work items (128-column windows x row segments) per step, items run on the
+ * plateau path, and distinct plateau records among them.  All zero when no
+ * plan is in use (other contexts, another kernel, no plateau item, or no
+ * step since the medium or the tuning changed).  Any output pointer may be
+ * NULL.  QLA_EINVAL for a null ctx. */
 qla_status qla_march_plan(const qla_ctx *ctx, int *n_items, int *n_plateau_items, int *n_sets);
 
 /* Text of the last error on this context ("" if none); valid until the next

@@ -61,12 +61,10 @@ Layout layout_for(int nx, int ny, int prec, unsigned flags) {
         L.dstable = off; off += align256((UNIFORM_SLOTS + sites) * sizeof(MedRec<dsf>));
     }
     // FP32 E_z: the plateau-split step's unit list (int4 entries): three
-    // units per 120-column window and segment of at least 16 rows, plus
-    // whole-block padding
+    // units per 120-column window and segment of at least 16 rows
     L.items = L.items_cap = 0;
     if (prec == QLA_FP32 && P == 3) {
-        L.items_cap = 3 * size_t((nx + 119) / 120) * size_t((ny + 15) / 16) +
-                      size_t(UNI_SETS + 1) * 4;
+        L.items_cap = 3 * size_t((nx + 119) / 120) * size_t((ny + 15) / 16);
         L.items = off; off += align256(L.items_cap * 16);
     }
     L.total = off;
@@ -633,10 +631,10 @@ long long qla_launch_count(const qla_ctx *c) { return c ? c->launches : 0; }
 qla_status qla_march_plan(const qla_ctx *c, int *n_items, int *n_plateau_items, int *n_sets) {
     if (!c) return QLA_EINVAL;
     const auto &u = c->uplan;
-    const bool live = u.gen == c->medium_gen && u.sets.n_sets > 0;
+    const bool live = u.gen == c->medium_gen && u.n_uniform > 0;
     if (n_items) *n_items = live ? u.n_items : 0;
     if (n_plateau_items) *n_plateau_items = live ? u.n_uniform : 0;
-    if (n_sets) *n_sets = live ? u.sets.n_sets : 0;
+    if (n_sets) *n_sets = live ? u.n_sets : 0;
     return QLA_OK;
 }
 

@@ -344,21 +344,6 @@ __host__ __device__ inline int wrap(int i, int n) {
 // ----------------------------------------------------------------------------
 // Context.
 // ----------------------------------------------------------------------------
-// Plateau plan of the FP32 E_z marching step.  A work item whose entering
-// sites all share one record (a plateau of n, with every neighbour of each
-// site on it) needs no record lookups and no potential step, and its
-// collision coefficients are the same for every lane; the plan lists such
-// items first, grouped by record into whole blocks, so that the kernel
-// takes a block's coefficients from its arguments (a block-uniform value).
-constexpr int UNI_SETS = 8;          // records with their own block range
-struct UniSets {
-    int n_sets;                       // sets in use
-    int block_start[UNI_SETS];        // set s runs from this block to the next set's start
-                                      // (the last to the grid's end); earlier blocks run
-                                      // the other items
-    float4 k[UNI_SETS];               // MedRec<float>::c of each set's record
-};
-
 struct qla_ctx {
     int nx = 0, ny = 0, pitch = 0;  // pitch: elements per stored row
     double delta = 1.0;
@@ -408,8 +393,7 @@ struct qla_ctx {
     size_t items_cap = 0;
     struct {
         long long gen = -1;
-        int seg = 0, n_items = 0, n_list = 0, n_uniform = 0;
-        UniSets sets{};
+        int seg = 0, n_items = 0, n_list = 0, n_uniform = 0, n_sets = 0;
     } uplan;
     qla_status sticky = QLA_OK;
     std::string err;

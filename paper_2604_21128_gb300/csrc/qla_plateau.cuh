@@ -1,0 +1,138 @@
+// Plateau work units of the FP32 E_z marching step (single lattices and
+// batches).
+//
+// In the workloads' media most sites sit on plateaus of n on which every
+// site's four neighbours carry its n: those share one record (see MedRec),
+// their potential step is the identity and their collision coefficients
+// are the same everywhere on the plateau.  A work item whose entering sites
+// all share one record -- a plateau item -- therefore needs no index rows,
+// no record lookups and no potential step; without the record ring the
+// march holds four columns per lane (128-column windows, 8 of 128 columns
+// recomputed instead of 8 of 64) in the register budget of the two-column
+// march.  Every other item runs the two-column march with its record ring.
+//
+// A unit is one warp's work: int4 (x_out, w_out | (rec + 1) << 8, y_lo,
+// y_hi) = store columns [x_out, x_out + w_out) of rows [y_lo, y_hi); rec is
+// the plateau record (>= 0: the four-column plateau march with that
+// record's coefficients) or -1 (the two-column march, w_out <= 56).
+// w_out = 0 marks an idle warp.
+#pragma once
+
+#include <algorithm>
+#include <vector>
+
+#include "qla_march.cuh"
+
+namespace qla {
+namespace march {
+
+constexpr int PW = 128, PWOUT = 120;   // plateau windows: columns, stored columns
+constexpr int GWOUT = 56;              // stored columns of a two-column window
+
+__host__ __device__ inline int4 plateau_unit(int x_out, int w_out, int rec, int y_lo, int y_hi) {
+    return make_int4(x_out, w_out | ((rec + 1) << 8), y_lo, y_hi);
+}
+
+// Run unit u of a lattice (arrays in/out/midx/table of its size and pitch);
+// smem: this warp's staging ring (room for the four-column ring).
+template <int VM, bool VIN>
+__device__ __forceinline__ void run_plateau_unit(const float *in, float *out, const uint32_t *midx,
+                                                 const MedRec<float> *table, int nx, int ny,
+                                                 int pitch, uint32_t plane, const int4 &u,
+                                                 unsigned char *smem) {
+    const int w_out = u.y & 0xff, rec = (u.y >> 8) - 1;
+    if (w_out == 0) return;
+    if (rec >= 0) {
+        using M = March<float, 3, 4, VM, VIN, true>;
+        M m;
+        m.in = in;
+        m.out = out;
+        m.midx = midx;
+        m.table = table;
+        m.pitch = pitch;
+        m.plane = plane;
+        m.total = uint32_t(ny) * uint32_t(pitch);
+        // the same 16 bytes in every lane
+        m.set_uniform(__ldg(&table[rec].c));
+        m.run_unit(nx, ny, u.x, w_out, u.z, u.w, reinterpret_cast<typename M::Slot *>(smem));
+    } else {
+        using M = March<float, 3, 2, VM, VIN, false>;
+        M m;
+        m.in = in;
+        m.out = out;
+        m.midx = midx;
+        m.table = table;
+        m.pitch = pitch;
+        m.plane = plane;
+        m.total = uint32_t(ny) * uint32_t(pitch);
+        m.run_unit(nx, ny, u.x, w_out, u.z, u.w, reinterpret_cast<typename M::Slot *>(smem));
+    }
+}
+
+// Bytes of one warp's staging ring for either march.
+template <int VM, bool VIN> constexpr size_t plateau_ring_bytes() {
+    return std::max(sizeof(typename March<float, 3, 4, VM, VIN, true>::Slot),
+                    sizeof(typename March<float, 3, 2, VM, VIN, false>::Slot)) *
+           NSLOT;
+}
+
+namespace {
+
+// The record shared by all entering sites of each plateau-window item
+// (columns [x0, x0 + 128) and rows [y_lo - 4, y_hi + 4), periodic, with
+// x0 = 120 wx - 4), or -1 where they differ or the record is a site's own:
+// one warp per item.
+__global__ void k_classify_items(const uint32_t *__restrict__ midx, int nx, int ny, int pitch,
+                                 int seg_h, int n_wx, int n_items, int *__restrict__ cls) {
+    const int item = int(blockIdx.x) * WARPS + int(threadIdx.x >> 5);
+    if (item >= n_items) return;   // the whole warp
+    const int lane = threadIdx.x & 31;
+    const int wx = item % n_wx, wy = item / n_wx;
+    const int x0 = wx * PWOUT - 4 + 4 * lane;
+    int col[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) col[k] = wrap(x0 + k, nx);
+    const int y_lo = wy * seg_h, y_hi = min(ny, y_lo + seg_h);
+    uint32_t lo = 0xffffffffu, hi = 0u;
+    for (int J = y_lo - LAG; J < y_hi + LAG; ++J) {
+        const uint32_t *row = midx + size_t(wrap(J, ny)) * size_t(pitch);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t v = __ldg(row + col[k]);
+            lo = min(lo, v);
+            hi = max(hi, v);
+        }
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) cls[item] = lo == hi && lo < uint32_t(UNIFORM_SLOTS) ? int(lo) : -1;
+}
+
+}  // namespace
+
+// The units of one lattice from its item classes (n_wx plateau windows per
+// row of items, segments of seg rows): every plateau item as one unit, every
+// other item as two-column units of at most 56 columns.  Appends the other
+// units to `other` and the plateau units to `plat`; returns the number of
+// plateau items.
+inline int plateau_units(const std::vector<int> &cls, int nx, int ny, int seg,
+                         std::vector<int4> &other, std::vector<int4> &plat) {
+    const int n_wx = (nx + PWOUT - 1) / PWOUT;
+    int n_plateau = 0;
+    for (size_t i = 0; i < cls.size(); ++i) {
+        const int wx = int(i) % n_wx, wy = int(i) / n_wx;
+        const int x_out = wx * PWOUT, w_out = std::min(PWOUT, nx - x_out);
+        const int y_lo = wy * seg, y_hi = std::min(ny, y_lo + seg);
+        if (cls[i] >= 0) {
+            plat.push_back(plateau_unit(x_out, w_out, cls[i], y_lo, y_hi));
+            ++n_plateau;
+        } else {
+            for (int x = x_out; x < x_out + w_out; x += GWOUT)
+                other.push_back(plateau_unit(x, std::min(GWOUT, x_out + w_out - x), -1, y_lo, y_hi));
+        }
+    }
+    return n_plateau;
+}
+
+}  // namespace march
+}  // namespace qla

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "qla_march2.cuh"
+#include "qla_plateau.cuh"
 
 namespace qla {
 namespace {
@@ -96,93 +97,21 @@ k_step_march2(const float *__restrict__ in, float *__restrict__ out,
     if (item < n_items) m.run_item(nx, ny, seg_h, n_wx, item, ring);
 }
 
-// The plateau-split step (FP32 E_z).  Warp w of block b runs the unit
-// units[4b + w] = (x_out, w_out, y_lo, y_hi): columns [x_out, x_out + w_out)
-// of rows [y_lo, y_hi) (w_out = 0: an idle warp).  Blocks from
-// us.block_start[s] on (up to the next set's start) run plateau units of
-// set s: four columns per lane (128-column windows) with the set's
-// coefficients from the kernel arguments -- the set index depends on
-// blockIdx and the arguments only, so the coefficients are the same value
-// in every lane (a uniform operand of the rotations).  The blocks before
-// us.block_start[0] run the other units with two columns per lane and the
-// record ring.  Without the ring the four-column march fits the register
-// budget of the two-column one (about 100 registers), and its wider
-// window recomputes 8 of 128 columns instead of 8 of 64.
+// The plateau-split step (FP32 E_z; see qla_plateau.cuh): warp w of block b
+// runs units[4 b + w].  The other units come first in the list, so the
+// slower two-column work starts early and the plateau units fill the tail.
 template <int VM, bool VIN>
 __global__ void __launch_bounds__(32 * WARPS, 4)
 k_step_march_split(const float *__restrict__ in, float *__restrict__ out,
                    const uint32_t *__restrict__ midx, const MedRec<float> *__restrict__ table,
                    int nx, int ny, int pitch, size_t plane, const int4 *__restrict__ units,
-                   int n_units, const __grid_constant__ UniSets us) {
+                   int n_units) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    int set = -1;
-#pragma unroll
-    for (int i = 0; i < UNI_SETS; ++i)
-        set += (i < us.n_sets && int(blockIdx.x) >= us.block_start[i]) ? 1 : 0;
-    const int li = int(blockIdx.x) * WARPS + int(threadIdx.x >> 5);
-    if (li >= n_units) return;   // the whole warp: units are per warp
-    const int4 u = units[li];
-    if (u.y <= 0) return;
     const int warp = threadIdx.x >> 5;
-    if (set >= 0) {
-        using M = March<float, 3, 4, VM, VIN, true>;
-        M m;
-        m.in = in;
-        m.out = out;
-        m.midx = midx;
-        m.table = table;
-        m.pitch = pitch;
-        m.plane = uint32_t(plane);
-        m.total = uint32_t(ny) * uint32_t(pitch);
-        m.set_uniform(us.k[set]);
-        m.run_unit(nx, ny, u.x, u.y, u.z, u.w,
-                   reinterpret_cast<typename M::Slot *>(smem_raw) + warp * NSLOT);
-    } else {
-        using M = March<float, 3, 2, VM, VIN, false>;
-        M m;
-        m.in = in;
-        m.out = out;
-        m.midx = midx;
-        m.table = table;
-        m.pitch = pitch;
-        m.plane = uint32_t(plane);
-        m.total = uint32_t(ny) * uint32_t(pitch);
-        m.run_unit(nx, ny, u.x, u.y, u.z, u.w,
-                   reinterpret_cast<typename M::Slot *>(smem_raw) + warp * NSLOT);
-    }
-}
-
-// Plateau windows: 128 columns, 120 stored.
-constexpr int PW = 128, PWOUT = 120;
-
-// The record shared by all entering sites of each plateau-window item
-// (columns [x0, x0 + 128) and rows [y_lo - 4, y_hi + 4), periodic, with
-// x0 = 120 wx - 4), or -1 where they differ or the record is a site's own:
-// one warp per item.
-__global__ void k_classify_items(const uint32_t *__restrict__ midx, int nx, int ny, int pitch,
-                                 int seg_h, int n_wx, int n_items, int *__restrict__ cls) {
-    const int item = int(blockIdx.x) * WARPS + int(threadIdx.x >> 5);
-    if (item >= n_items) return;   // the whole warp
-    const int lane = threadIdx.x & 31;
-    const int wx = item % n_wx, wy = item / n_wx;
-    const int x0 = wx * PWOUT - 4 + 4 * lane;
-    int col[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) col[k] = wrap(x0 + k, nx);
-    const int y_lo = wy * seg_h, y_hi = min(ny, y_lo + seg_h);
-    uint32_t lo = 0xffffffffu, hi = 0u;
-    for (int J = y_lo - LAG; J < y_hi + LAG; ++J) {
-        const uint32_t *row = midx + size_t(wrap(J, ny)) * size_t(pitch);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t v = __ldg(row + col[k]);
-            lo = min(lo, v);
-            hi = max(hi, v);
-        }
-    }
-    lo = __reduce_min_sync(0xffffffffu, lo);
-    hi = __reduce_max_sync(0xffffffffu, hi);
-    if (lane == 0) cls[item] = lo == hi && lo < uint32_t(UNIFORM_SLOTS) ? int(lo) : -1;
+    const int li = int(blockIdx.x) * WARPS + warp;
+    if (li >= n_units) return;   // the whole warp: units are per warp
+    run_plateau_unit<VM, VIN>(in, out, midx, table, nx, ny, pitch, uint32_t(plane), units[li],
+                              smem_raw + warp * plateau_ring_bytes<VM, VIN>());
 }
 
 // Segment height: about two work items per resident warp slot (measured
@@ -233,18 +162,16 @@ template <int VM, bool VIN> struct Variant<float, 3, 1, VM, VIN> : Variant2<Pair
 template <int VM, bool VIN> struct Variant<float, 3, 5, VM, VIN> : Variant2<PairF2, VM, VIN, 4, true> {};
 
 // The plateau plan for segments of `seg` rows: classify the plateau-window
-// items, keep the UNI_SETS records with the most plateau items, and write
-// the unit list to c->items: first the other items as two-column units of
-// at most 56 columns, then each set's items, each kind in whole blocks.
-// Synchronises the context's stream once.
+// items and write the unit list to c->items (the other items' units first,
+// then the plateau units).  Synchronises the context's stream once.
 cudaError_t build_plateau_plan(qla_ctx *c, int seg) {
     auto &u = c->uplan;
     u.gen = -1;
-    u.sets.n_sets = 0;
+    u.n_uniform = 0;
     const int n_wx = (c->nx + PWOUT - 1) / PWOUT;
     const int n_items = n_wx * ((c->ny + seg - 1) / seg);
-    // capacity: three units per item at most, plus whole-block padding
-    if (size_t(3) * n_items + size_t(UNI_SETS + 1) * WARPS > c->items_cap) return cudaSuccess;
+    // capacity: three units per item at most
+    if (size_t(3) * n_items > c->items_cap) return cudaSuccess;
     int *cls_dev = reinterpret_cast<int *>(c->items);
     k_classify_items<<<(n_items + WARPS - 1) / WARPS, 32 * WARPS, 0, c->stream>>>(
         c->midx, c->nx, c->ny, c->pitch, seg, n_wx, n_items, cls_dev);
@@ -255,85 +182,40 @@ cudaError_t build_plateau_plan(qla_ctx *c, int seg) {
                         c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return e;
-    std::map<int, int> count;
+    std::vector<int4> list, plat;
+    list.reserve(size_t(3) * n_items);
+    const int n_plateau = plateau_units(cls, c->nx, c->ny, seg, list, plat);
+    list.insert(list.end(), plat.begin(), plat.end());
+    std::vector<int> recs;
     for (int v : cls)
-        if (v >= 0) count[v]++;
-    std::vector<std::pair<int, int>> by;   // (items, record)
-    for (const auto &kv : count) by.emplace_back(kv.second, kv.first);
-    std::sort(by.begin(), by.end(), [](const std::pair<int, int> &a, const std::pair<int, int> &b) {
-        return a.first != b.first ? a.first > b.first : a.second < b.second;
-    });
-    if (by.size() > size_t(UNI_SETS)) by.resize(UNI_SETS);
-    std::map<int, int> set_of;
-    for (size_t s = 0; s < by.size(); ++s) set_of[by[s].second] = int(s);
-    std::vector<int4> list;
-    list.reserve(size_t(3) * n_items + size_t(UNI_SETS + 1) * WARPS);
-    auto pad = [&] {
-        while (list.size() % WARPS) list.push_back(make_int4(0, 0, 0, 0));
-    };
-    auto item_box = [&](int i, int &x_out, int &w_out, int &y_lo, int &y_hi) {
-        const int wx = i % n_wx, wy = i / n_wx;
-        x_out = wx * PWOUT;
-        w_out = std::min(PWOUT, c->nx - x_out);
-        y_lo = wy * seg;
-        y_hi = std::min(c->ny, y_lo + seg);
-    };
-    int x_out, w_out, y_lo, y_hi;
-    for (int i = 0; i < n_items; ++i) {
-        if (cls[i] >= 0 && set_of.count(cls[i])) continue;
-        item_box(i, x_out, w_out, y_lo, y_hi);
-        for (int x = x_out; x < x_out + w_out; x += 56)
-            list.push_back(make_int4(x, std::min(56, x_out + w_out - x), y_lo, y_hi));
-    }
-    pad();
-    UniSets us{};
-    us.n_sets = int(by.size());
-    int n_uniform = 0;
-    for (size_t s = 0; s < by.size(); ++s) {
-        us.block_start[s] = int(list.size() / WARPS);
-        for (int i = 0; i < n_items; ++i) {
-            if (cls[i] != by[s].second) continue;
-            item_box(i, x_out, w_out, y_lo, y_hi);
-            list.push_back(make_int4(x_out, w_out, y_lo, y_hi));
-        }
-        pad();
-        n_uniform += by[s].first;
-    }
-    std::vector<MedRec<float>> rec(by.size() + 1);
-    const MedRec<float> *table = static_cast<const MedRec<float> *>(c->table);
-    for (size_t s = 0; s < by.size() && e == cudaSuccess; ++s)
-        e = cudaMemcpyAsync(&rec[s], table + by[s].second, sizeof(MedRec<float>),
-                            cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->items, list.data(), list.size() * sizeof(int4),
-                            cudaMemcpyHostToDevice, c->stream);
+        if (v >= 0) recs.push_back(v);
+    std::sort(recs.begin(), recs.end());
+    const int n_recs = int(std::unique(recs.begin(), recs.end()) - recs.begin());
+    e = cudaMemcpyAsync(c->items, list.data(), list.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                        c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return e;
-    for (size_t s = 0; s < by.size(); ++s) us.k[s] = rec[s].c;
     u.gen = c->medium_gen;
     u.seg = seg;
     u.n_items = n_items;
     u.n_list = int(list.size());
-    u.n_uniform = n_uniform;
-    u.sets = us;
+    u.n_uniform = n_plateau;
+    u.n_sets = n_recs;
     return cudaSuccess;
 }
 
 template <int VM, bool VIN>
 cudaError_t launch_split(qla_ctx *c, const void *in, void *out) {
     auto kern = k_step_march_split<VM, VIN>;
-    // the larger staging ring of four warps
-    constexpr size_t slot = std::max(sizeof(typename March<float, 3, 4, VM, VIN, true>::Slot),
-                                     sizeof(typename March<float, 3, 2, VM, VIN, false>::Slot));
-    const size_t smem = slot * NSLOT * WARPS;
+    const size_t smem = plateau_ring_bytes<VM, VIN>() * WARPS;
     static const cudaError_t attr =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (attr != cudaSuccess) return attr;
     const auto &u = c->uplan;
-    kern<<<u.n_list / WARPS, 32 * WARPS, smem, c->stream>>>(
+    kern<<<(u.n_list + WARPS - 1) / WARPS, 32 * WARPS, smem, c->stream>>>(
         static_cast<const float *>(in), static_cast<float *>(out), c->midx,
         static_cast<const MedRec<float> *>(c->table), c->nx, c->ny, c->pitch, c->plane_elems,
-        reinterpret_cast<const int4 *>(c->items), u.n_list, u.sets);
+        reinterpret_cast<const int4 *>(c->items), u.n_list);
     return cudaGetLastError();
 }
 
@@ -391,7 +273,7 @@ cudaError_t launch_t(qla_ctx *c, const void *in, void *out, const void *table) {
                 const cudaError_t e = build_plateau_plan(c, pseg);
                 if (e != cudaSuccess) return e;
             }
-            if (u.gen == c->medium_gen && u.seg == pseg && u.sets.n_sets > 0)
+            if (u.gen == c->medium_gen && u.seg == pseg && u.n_uniform > 0)
                 return launch_split<VM, VIN>(c, in, out);
         }
     }

@@ -148,8 +148,8 @@ def fp32_run(n, steps, q0, kernel, rows=0, potential="rotation", lane_cols=0):
                          [(0, 0, "rotation"), (0, 16, "rotation"), (0, 40, "literal"),
                           (0, 20, "none"), (2, 36, "rotation")])
 def test_plateau_split_agrees_bitwise(lane_cols, rows, potential):
-    """Work items on plateaus of n run with the plateau's coefficients as a
-    block-uniform argument (no record lookups, no potential step); the state
+    """Work items on plateaus of n run four columns per lane with the
+    plateau's coefficients (no record lookups, no potential step); the state
     and the energy are those of the unsplit marching kernel and of the tile
     kernel bit for bit, next to the plateaus' edges too."""
     nx, ny = 1024, 384
@@ -166,15 +166,14 @@ def test_plateau_split_agrees_bitwise(lane_cols, rows, potential):
 
 
 def test_plateau_split_limits():
-    """More plateau records than the launch has block ranges for (12 bands:
-    8 take the plateau path, the rest the general one), and lattices the
-    split does not take (nx not a multiple of 4, narrower than a 128-column
-    window): all bitwise equal to the tile kernel."""
+    """Many plateau records (12 bands, each with its own coefficients), and
+    lattices the split does not take (nx not a multiple of 4, narrower than
+    a 128-column window): all bitwise equal to the tile kernel."""
     nx, ny = 12 * 256, 192
     n = np.repeat(1.0 + 0.125 * np.arange(12), 256)[None, :].repeat(ny, axis=0)
     q0 = inputs.random_state(nx, ny, seed=34, planes=3)
     split = fp32_run(n, 7, q0, "march")
-    assert split[2][2] == 8 and 0 < split[2][1] < split[2][0], split[2]
+    assert split[2][2] == 12 and 0 < split[2][1] < split[2][0], split[2]
     tile = fp32_run(n, 7, q0, "tile")
     assert np.array_equal(split[0], tile[0]) and split[1] == tile[1]
     for nx2 in (1030, 100):
