@@ -21,6 +21,7 @@
 
 #include "qla_limits.h"
 #include "qla_march2.cuh"
+#include "qla_plateau.cuh"
 
 namespace qla {
 namespace {
@@ -39,6 +40,13 @@ struct BatchInst {
 
 struct BatchItem {
     int inst, item;
+};
+
+// A unit of the plateau-split FP32 E_z kernel (qla_plateau.cuh) and its
+// instance.
+struct BatchUnit {
+    int4 u;
+    int inst, pad0, pad1, pad2;
 };
 
 struct Barrier {
@@ -135,6 +143,38 @@ k_batch_march(const BatchInst *__restrict__ insts, const BatchItem *__restrict__
     }
 }
 
+// The same for FP32 E_z batches split by plateaus: every warp takes units
+// (a plateau item four columns per lane, or a two-column unit of another
+// item) from the shared counter; the other items' units come first.
+template <int VM>
+__global__ void __launch_bounds__(32 * WARPS)
+k_batch_plateau(const BatchInst *__restrict__ insts, const BatchUnit *__restrict__ units,
+                int n_units, int n_steps, int step0, Barrier *bar, long long budget,
+                int skip_block) {
+    constexpr bool VIN = VM != V_NONE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *ring = smem_raw + (threadIdx.x >> 5) * plateau_ring_bytes<VM, VIN>();
+    const int lane = threadIdx.x & 31;
+    if (*static_cast<volatile int *>(&bar->err)) return;
+    for (int s = 0; s < n_steps; ++s) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) bar->next[(s + 1) & 1] = 0;
+        for (;;) {
+            int it = 0;
+            if (lane == 0) it = int(atomicAdd(&bar->next[s & 1], 1u));
+            it = __shfl_sync(0xffffffffu, it, 0);
+            if (it >= n_units) break;
+            const BatchUnit bu = units[it];
+            const BatchInst &I = insts[bu.inst];
+            const int src = (I.cur + step0 + s) & 1;
+            run_plateau_unit<VM, VIN>(static_cast<const float *>(I.buf[src]),
+                                      static_cast<float *>(I.buf[src ^ 1]), I.midx,
+                                      static_cast<const MedRec<float> *>(I.table), I.nx, I.ny,
+                                      I.pitch, I.plane, bu.u, ring);
+        }
+        if (!grid_barrier(bar, budget, s == 0 && int(blockIdx.x) == skip_block)) return;
+    }
+}
+
 // Energy of every instance (as qla_energy): block (b, k) sums part b of
 // instance k; the state is the buffer after `steps` steps of this run.
 template <typename T, int P, int VM>
@@ -199,8 +239,8 @@ struct qla_batch {
     char *ws = nullptr;
     std::vector<qla_ctx *> inst;
     BatchInst *d_insts = nullptr;
-    BatchItem *d_items = nullptr;
-    size_t items_cap = 0;
+    BatchItem *d_items = nullptr;   // the work list (BatchItem or BatchUnit entries)
+    size_t items_cap = 0, units_cap = 0;
     Barrier *d_bar = nullptr;
     double *d_partials = nullptr, *d_energy = nullptr;
     int lane_cols = 0, rows = 0;
@@ -234,13 +274,29 @@ bool lattice_ok(int nx, int ny, int planes) {
            offsets32_ok(size_t(planes), padded_plane(nx, ny));
 }
 
-size_t tail_bytes(int count, const int *nx, const int *ny) {
+// Work-list capacity (rows per item >= 32): items of the two-column
+// layout, or units of the plateau split (three per 120-column item).
+size_t items_of(int count, const int *nx, const int *ny) {
     size_t items = 0;
     for (int k = 0; k < count; ++k)
         items += size_t((nx[k] + 55) / 56) * size_t((ny[k] + 31) / 32);
+    return items;
+}
+size_t units_of(int count, const int *nx, const int *ny) {
+    size_t units = 0;
+    for (int k = 0; k < count; ++k)
+        units += 3 * size_t((nx[k] + PWOUT - 1) / PWOUT) * size_t((ny[k] + 31) / 32);
+    return units;
+}
+size_t list_bytes(int count, const int *nx, const int *ny) {
+    return std::max(sizeof(BatchItem) * items_of(count, nx, ny),
+                    sizeof(BatchUnit) * units_of(count, nx, ny));
+}
+
+size_t tail_bytes(int count, const int *nx, const int *ny) {
     size_t t = 0;
     t += align256(sizeof(BatchInst) * count);
-    t += align256(sizeof(BatchItem) * items);
+    t += align256(list_bytes(count, nx, ny));
     t += align256(sizeof(Barrier));
     t += align256(sizeof(double) * count * ENERGY_BLOCKS);
     t += align256(sizeof(double) * count * ENERGY_ROWS);
@@ -252,14 +308,22 @@ struct Kern {
     const void *march;
     size_t slot_bytes;
     const void *epart;
+    bool plateau;   // the plateau-split kernel (units instead of items)
 };
 
 template <typename T, int P, int LX, int VM>
 Kern kern_t() {
-    using M = typename MarchOf<T, P, LX, VM, VM != V_NONE>::type;
-    return Kern{reinterpret_cast<const void *>(&k_batch_march<T, P, LX, VM>),
-                sizeof(typename M::Slot),
-                reinterpret_cast<const void *>(&k_batch_energy_partial<T, P, VM>)};
+    if constexpr (std::is_same<T, float>::value && P == 3 && LX == 2) {
+        // FP32 E_z, two columns per lane: split by plateaus
+        return Kern{reinterpret_cast<const void *>(&k_batch_plateau<VM>),
+                    plateau_ring_bytes<VM, VM != V_NONE>() / NSLOT,
+                    reinterpret_cast<const void *>(&k_batch_energy_partial<T, P, VM>), true};
+    } else {
+        using M = typename MarchOf<T, P, LX, VM, VM != V_NONE>::type;
+        return Kern{reinterpret_cast<const void *>(&k_batch_march<T, P, LX, VM>),
+                    sizeof(typename M::Slot),
+                    reinterpret_cast<const void *>(&k_batch_energy_partial<T, P, VM>), false};
+    }
 }
 
 template <typename T, int P, int LX>
@@ -287,9 +351,102 @@ int lane_cols_of(const qla_batch *b) {
 
 int window_out(int lx) { return lx == 1 ? 56 : 32 * lx - 8; }
 
+// Interleave per-instance lists so that each wave mixes lattices.
+template <typename E>
+void interleave(const std::vector<std::vector<E>> &per, std::vector<E> &out) {
+    std::vector<size_t> pos(per.size(), 0);
+    for (bool any = true; any;) {
+        any = false;
+        for (size_t k = 0; k < per.size(); ++k)
+            if (pos[k] < per[k].size()) {
+                out.push_back(per[k][pos[k]++]);
+                any = true;
+            }
+    }
+}
+
+// Units of the plateau-split kernel (segments of `seg` rows, capped at each
+// lattice's height): every instance's items classified on the GPU (into the
+// batch's work list, which the units then replace; the instances' own unit
+// lists belong to their single-lattice steps), then the other items' units
+// of all instances, interleaved, followed by the plateau units, interleaved.
+qla_status build_units(qla_batch *b, int rows, int *n_units, std::vector<BatchInst> &hinst) {
+    std::vector<int> segs(b->count), nwx(b->count), nitems(b->count);
+    std::vector<size_t> at(b->count + 1, 0);
+    for (int k = 0; k < b->count; ++k) {
+        qla_ctx *c = b->inst[k];
+        // 128-row segments by default (256 instances of sides 512-2048:
+        // 1.64e11 site-updates/s at 64 or 128 rows, 1.52e11 at 256)
+        int seg = rows > 0 ? rows : 128;
+        seg = (seg + 3) / 4 * 4;
+        if (seg > c->ny) seg = (c->ny + 3) / 4 * 4;
+        segs[k] = seg;
+        nwx[k] = (c->nx + PWOUT - 1) / PWOUT;
+        nitems[k] = nwx[k] * ((c->ny + seg - 1) / seg);
+        at[k + 1] = at[k] + size_t(nitems[k]);
+    }
+    if (at[b->count] > b->units_cap)   // classes take 4 of a unit's 32 bytes
+        return bfail(b, QLA_EINVAL, "qla_batch: %zu items exceed the workspace's %zu",
+                     at[b->count], b->units_cap);
+    int *cls_dev = reinterpret_cast<int *>(b->d_items);
+    for (int k = 0; k < b->count; ++k) {
+        qla_ctx *c = b->inst[k];
+        k_classify_items<<<(nitems[k] + WARPS - 1) / WARPS, 32 * WARPS, 0, b->stream>>>(
+            c->midx, c->nx, c->ny, c->pitch, segs[k], nwx[k], nitems[k], cls_dev + at[k]);
+        BCUDA(b, cudaGetLastError(), "qla_batch: classify");
+    }
+    std::vector<int> all(at[b->count]);
+    BCUDA(b, cudaMemcpyAsync(all.data(), cls_dev, all.size() * 4, cudaMemcpyDeviceToHost,
+                             b->stream), "qla_batch: classes");
+    BCUDA(b, cudaStreamSynchronize(b->stream), "qla_batch: classes");
+    std::vector<std::vector<int>> cls(b->count);
+    for (int k = 0; k < b->count; ++k)
+        cls[k].assign(all.begin() + at[k], all.begin() + at[k + 1]);
+    std::vector<std::vector<BatchUnit>> other(b->count), plat(b->count);
+    for (int k = 0; k < b->count; ++k) {
+        qla_ctx *c = b->inst[k];
+        std::vector<int4> o, p;
+        plateau_units(cls[k], c->nx, c->ny, segs[k], o, p);
+        for (const int4 &u : o) other[k].push_back(BatchUnit{u, k, 0, 0, 0});
+        for (const int4 &u : p) plat[k].push_back(BatchUnit{u, k, 0, 0, 0});
+    }
+    std::vector<BatchUnit> list;
+    interleave(other, list);
+    interleave(plat, list);
+    if (list.size() > b->units_cap)
+        return bfail(b, QLA_EINVAL, "qla_batch: %zu units exceed the workspace's %zu",
+                     list.size(), b->units_cap);
+    BCUDA(b, cudaMemcpyAsync(b->d_items, list.data(), list.size() * sizeof(BatchUnit),
+                             cudaMemcpyHostToDevice, b->stream), "qla_batch: units");
+    hinst.resize(b->count);
+    for (int k = 0; k < b->count; ++k) {
+        qla_ctx *c = b->inst[k];
+        BatchInst &I = hinst[k];
+        I.buf[0] = c->state[0];
+        I.buf[1] = c->state[1];
+        I.midx = c->midx;
+        I.table = c->table;
+        I.nx = c->nx;
+        I.ny = c->ny;
+        I.pitch = c->pitch;
+        I.seg = segs[k];
+        I.n_wx = nwx[k];
+        I.plane = uint32_t(c->plane_elems);
+        I.total = uint32_t(c->ny) * uint32_t(c->pitch);
+        I.cur = c->cur;
+        I.vin = c->pending_v ? 1 : 0;
+    }
+    BCUDA(b, cudaMemcpyAsync(b->d_insts, hinst.data(), hinst.size() * sizeof(BatchInst),
+                             cudaMemcpyHostToDevice, b->stream), "qla_batch: instances");
+    BCUDA(b, cudaStreamSynchronize(b->stream), "qla_batch: upload");
+    *n_units = int(list.size());
+    return QLA_OK;
+}
+
 // Work items for the current tiling; returns the item count.
 qla_status build_items(qla_batch *b, int lx, int rows, int *n_items,
                        std::vector<BatchInst> &hinst) {
+    if (kernels(b, lx).plateau) return build_units(b, rows, n_items, hinst);
     const int wout = window_out(lx);
     std::vector<BatchItem> items;
     hinst.resize(b->count);
@@ -431,7 +588,10 @@ qla_status read_err(qla_batch *b) {
 }
 
 // Step all instances n_steps (after align_pending); no synchronisation.
-qla_status step_persistent(qla_batch *b, long long n_steps, int lx, int rows) {
+// e0 (if given) is recorded on the stream once the work list is built, so
+// that a timing around the call sees the launches only.
+qla_status step_persistent(qla_batch *b, long long n_steps, int lx, int rows,
+                           cudaEvent_t e0 = nullptr) {
     std::vector<BatchInst> hinst;
     int n_items = 0;
     qla_status s = build_items(b, lx, rows, &n_items, hinst);
@@ -441,6 +601,7 @@ qla_status step_persistent(qla_batch *b, long long n_steps, int lx, int rows) {
     size_t smem = 0;
     s = grid_for(b, k, &blocks, &smem);
     if (s != QLA_OK) return s;
+    if (e0) BCUDA(b, cudaEventRecord(e0, b->stream), "qla_batch: event");
     for (long long done = 0; done < n_steps;) {
         const int chunk = int(std::min<long long>(QLA_BATCH_CHUNK, n_steps - done));
         s = launch_chunk(b, b->stream, k, blocks, smem, n_items, chunk, int(done & 1));
@@ -518,14 +679,12 @@ qla_status qla_batch_create(qla_batch **out, int count, const int *nx, const int
         }
         off += align256(sz);
     }
-    size_t items = 0;
-    for (int k = 0; k < count; ++k)
-        items += size_t((nx[k] + 55) / 56) * size_t((ny[k] + 31) / 32);
     b->d_insts = reinterpret_cast<BatchInst *>(b->ws + off);
     off += align256(sizeof(BatchInst) * count);
     b->d_items = reinterpret_cast<BatchItem *>(b->ws + off);
-    b->items_cap = items;
-    off += align256(sizeof(BatchItem) * items);
+    b->items_cap = items_of(count, nx, ny);
+    b->units_cap = units_of(count, nx, ny);
+    off += align256(list_bytes(count, nx, ny));
     b->d_bar = reinterpret_cast<Barrier *>(b->ws + off);
     off += align256(sizeof(Barrier));
     b->d_partials = reinterpret_cast<double *>(b->ws + off);
@@ -684,8 +843,7 @@ qla_status qla_batch_autotune(qla_batch *b, int trial_steps, int *chosen_lane_co
             const int lx = two ? lxs[li] : 2;
             long long steps = trial_steps - (li == 0 && ri == 0 ? used : 0);
             if (steps <= 0) steps = 1;
-            cudaEventRecord(e0, b->stream);
-            s = step_persistent(b, steps, lx, rowss[ri]);
+            s = step_persistent(b, steps, lx, rowss[ri], e0);
             cudaEventRecord(e1, b->stream);
             if (s != QLA_OK) break;
             if (cudaEventSynchronize(e1) != cudaSuccess) { s = QLA_ECUDA; break; }
