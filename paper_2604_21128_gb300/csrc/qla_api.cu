@@ -66,6 +66,10 @@ Layout layout_for(int nx, int ny, int prec, unsigned flags) {
     if (prec == QLA_FP32 && P == 3) {
         L.items_cap = 3 * size_t((nx + 119) / 120) * size_t((ny + 15) / 16);
         L.items = off; off += align256(L.items_cap * 16);
+    } else if (prec == QLA_FP64 && P == 3 && (flags & QLA_DOUBLE_SINGLE)) {
+        // double-single E_z: one unit per 56-column window and segment
+        L.items_cap = size_t((nx + 55) / 56) * size_t((ny + 15) / 16);
+        L.items = off; off += align256(L.items_cap * 16);
     }
     L.total = off;
     return L;

@@ -1,5 +1,5 @@
-// Plateau work units of the FP32 E_z marching step (single lattices and
-// batches).
+// Plateau work units of the E_z marching steps: FP32 (single lattices and
+// batches) and double-single.
 //
 // In the workloads' media most sites sit on plateaus of n on which every
 // site's four neighbours carry its n: those share one record (see MedRec),
@@ -69,6 +69,42 @@ __device__ __forceinline__ void run_plateau_unit(const float *in, float *out, co
     }
 }
 
+// The same for double-single steps (FP64 state in word pairs): both kinds
+// of unit are 64-column windows (two columns per lane); a plateau unit
+// drops the record ring -- 64 registers of three-word coefficients -- and
+// takes its record's coefficients once.
+template <int VM, bool VIN>
+__device__ __forceinline__ void run_ds_unit(const dsf *in, dsf *out, const uint32_t *midx,
+                                            const MedRec<dsf> *table, int nx, int ny, int pitch,
+                                            uint32_t plane, const int4 &u, unsigned char *smem) {
+    const int w_out = u.y & 0xff, rec = (u.y >> 8) - 1;
+    if (w_out == 0) return;
+    if (rec >= 0) {
+        using M = March<dsf, 3, 2, VM, VIN, true>;
+        M m;
+        m.in = in;
+        m.out = out;
+        m.midx = midx;
+        m.table = table;
+        m.pitch = pitch;
+        m.plane = plane;
+        m.total = uint32_t(ny) * uint32_t(pitch);
+        m.set_uniform(table[rec].c);   // the same 32 bytes in every lane
+        m.run_unit(nx, ny, u.x, w_out, u.z, u.w, reinterpret_cast<typename M::Slot *>(smem));
+    } else {
+        using M = March<dsf, 3, 2, VM, VIN, false>;
+        M m;
+        m.in = in;
+        m.out = out;
+        m.midx = midx;
+        m.table = table;
+        m.pitch = pitch;
+        m.plane = plane;
+        m.total = uint32_t(ny) * uint32_t(pitch);
+        m.run_unit(nx, ny, u.x, w_out, u.z, u.w, reinterpret_cast<typename M::Slot *>(smem));
+    }
+}
+
 // Bytes of one warp's staging ring for either march.
 template <int VM, bool VIN> constexpr size_t plateau_ring_bytes() {
     return std::max(sizeof(typename March<float, 3, 4, VM, VIN, true>::Slot),
@@ -78,26 +114,29 @@ template <int VM, bool VIN> constexpr size_t plateau_ring_bytes() {
 
 namespace {
 
-// The record shared by all entering sites of each plateau-window item
-// (columns [x0, x0 + 128) and rows [y_lo - 4, y_hi + 4), periodic, with
-// x0 = 120 wx - 4), or -1 where they differ or the record is a site's own:
-// one warp per item.
-__global__ void k_classify_items(const uint32_t *__restrict__ midx, int nx, int ny, int pitch,
-                                 int seg_h, int n_wx, int n_items, int *__restrict__ cls) {
+// The record shared by all entering sites of each item of a window layout
+// (CPL columns per lane: columns [x0, x0 + 32 CPL) and rows [y_lo - 4,
+// y_hi + 4), periodic, with x0 = (32 CPL - 8) wx - 4), or -1 where they
+// differ or the record is a site's own: one warp per item.  CPL = 4: the
+// plateau windows of FP32 E_z steps; 2: the 64-column windows of
+// double-single steps.
+template <int CPL>
+__global__ void k_classify(const uint32_t *__restrict__ midx, int nx, int ny, int pitch,
+                           int seg_h, int n_wx, int n_items, int *__restrict__ cls) {
     const int item = int(blockIdx.x) * WARPS + int(threadIdx.x >> 5);
     if (item >= n_items) return;   // the whole warp
     const int lane = threadIdx.x & 31;
     const int wx = item % n_wx, wy = item / n_wx;
-    const int x0 = wx * PWOUT - 4 + 4 * lane;
-    int col[4];
+    const int x0 = wx * (32 * CPL - 8) - 4 + CPL * lane;
+    int col[CPL];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) col[k] = wrap(x0 + k, nx);
+    for (int k = 0; k < CPL; ++k) col[k] = wrap(x0 + k, nx);
     const int y_lo = wy * seg_h, y_hi = min(ny, y_lo + seg_h);
     uint32_t lo = 0xffffffffu, hi = 0u;
     for (int J = y_lo - LAG; J < y_hi + LAG; ++J) {
         const uint32_t *row = midx + size_t(wrap(J, ny)) * size_t(pitch);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < CPL; ++k) {
             const uint32_t v = __ldg(row + col[k]);
             lo = min(lo, v);
             hi = max(hi, v);
@@ -107,6 +146,7 @@ __global__ void k_classify_items(const uint32_t *__restrict__ midx, int nx, int 
     hi = __reduce_max_sync(0xffffffffu, hi);
     if (lane == 0) cls[item] = lo == hi && lo < uint32_t(UNIFORM_SLOTS) ? int(lo) : -1;
 }
+constexpr auto k_classify_items = k_classify<4>;
 
 }  // namespace
 

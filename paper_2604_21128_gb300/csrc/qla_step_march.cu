@@ -114,6 +114,26 @@ k_step_march_split(const float *__restrict__ in, float *__restrict__ out,
                               smem_raw + warp * plateau_ring_bytes<VM, VIN>());
 }
 
+// The double-single plateau split (E_z): the same units at 64-column
+// windows.  The record-ring march of the other units needs 194 registers;
+// holding the kernel to 3 or 4 blocks per SM made those units spill and the
+// step slower (8192^2 ellipse: 3.37 and 3.40 ms against 2.59 ms at 2 blocks
+// and 2.69 ms unsplit).
+template <int VM, bool VIN>
+__global__ void __launch_bounds__(32 * WARPS, 2)
+k_step_march_split_ds(const dsf *__restrict__ in, dsf *__restrict__ out,
+                      const uint32_t *__restrict__ midx, const MedRec<dsf> *__restrict__ table,
+                      int nx, int ny, int pitch, size_t plane, const int4 *__restrict__ units,
+                      int n_units) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    const int li = int(blockIdx.x) * WARPS + warp;
+    if (li >= n_units) return;
+    constexpr size_t ring = sizeof(typename March<dsf, 3, 2, VM, VIN, false>::Slot) * NSLOT;
+    run_ds_unit<VM, VIN>(in, out, midx, table, nx, ny, pitch, uint32_t(plane), units[li],
+                         smem_raw + warp * ring);
+}
+
 // Segment height: about two work items per resident warp slot (measured
 // on the 8192^2 lattice: one exact wave leaves the schedulers less slack
 // than two), rows a multiple of 4 and at least 32.  Within 25% of that
@@ -204,6 +224,66 @@ cudaError_t build_plateau_plan(qla_ctx *c, int seg) {
     return cudaSuccess;
 }
 
+// The double-single plan: items of 64-column windows (56 stored columns),
+// one unit each, the other items first.  Synchronises the stream once.
+cudaError_t build_plateau_plan_ds(qla_ctx *c, int seg) {
+    auto &u = c->uplan;
+    u.gen = -1;
+    u.n_uniform = 0;
+    const int n_wx = (c->nx + GWOUT - 1) / GWOUT;
+    const int n_items = n_wx * ((c->ny + seg - 1) / seg);
+    if (size_t(n_items) > c->items_cap) return cudaSuccess;
+    int *cls_dev = reinterpret_cast<int *>(c->items);
+    k_classify<2><<<(n_items + WARPS - 1) / WARPS, 32 * WARPS, 0, c->stream>>>(
+        c->midx, c->nx, c->ny, c->pitch, seg, n_wx, n_items, cls_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    std::vector<int> cls(n_items);
+    e = cudaMemcpyAsync(cls.data(), cls_dev, size_t(n_items) * 4, cudaMemcpyDeviceToHost,
+                        c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return e;
+    std::vector<int4> list, plat;
+    std::vector<int> recs;
+    for (int i = 0; i < n_items; ++i) {
+        const int wx = i % n_wx, wy = i / n_wx;
+        const int x_out = wx * GWOUT, w_out = std::min(GWOUT, c->nx - x_out);
+        const int y_lo = wy * seg, y_hi = std::min(c->ny, y_lo + seg);
+        (cls[i] >= 0 ? plat : list).push_back(plateau_unit(x_out, w_out, cls[i], y_lo, y_hi));
+        if (cls[i] >= 0) recs.push_back(cls[i]);
+    }
+    const int n_plateau = int(plat.size());
+    list.insert(list.end(), plat.begin(), plat.end());
+    std::sort(recs.begin(), recs.end());
+    const int n_recs = int(std::unique(recs.begin(), recs.end()) - recs.begin());
+    e = cudaMemcpyAsync(c->items, list.data(), list.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                        c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return e;
+    u.gen = c->medium_gen;
+    u.seg = seg;
+    u.n_items = n_items;
+    u.n_list = int(list.size());
+    u.n_uniform = n_plateau;
+    u.n_sets = n_recs;
+    return cudaSuccess;
+}
+
+template <int VM, bool VIN>
+cudaError_t launch_split_ds(qla_ctx *c, const void *in, void *out) {
+    auto kern = k_step_march_split_ds<VM, VIN>;
+    const size_t smem = sizeof(typename March<dsf, 3, 2, VM, VIN, false>::Slot) * NSLOT * WARPS;
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (attr != cudaSuccess) return attr;
+    const auto &u = c->uplan;
+    kern<<<(u.n_list + WARPS - 1) / WARPS, 32 * WARPS, smem, c->stream>>>(
+        static_cast<const dsf *>(in), static_cast<dsf *>(out), c->midx,
+        static_cast<const MedRec<dsf> *>(c->dstable), c->nx, c->ny, c->pitch, c->plane_elems,
+        reinterpret_cast<const int4 *>(c->items), u.n_list);
+    return cudaGetLastError();
+}
+
 template <int VM, bool VIN>
 cudaError_t launch_split(qla_ctx *c, const void *in, void *out) {
     auto kern = k_step_march_split<VM, VIN>;
@@ -275,6 +355,24 @@ cudaError_t launch_t(qla_ctx *c, const void *in, void *out, const void *table) {
             }
             if (u.gen == c->medium_gen && u.seg == pseg && u.n_uniform > 0)
                 return launch_split<VM, VIN>(c, in, out);
+        }
+    }
+    if constexpr (std::is_same<T, dsf>::value && P == 3 && LX == 2) {
+        if (c->items && c->step_kernel != QLA_KERNEL_MARCH_PLAIN && table == c->dstable) {
+            // about four items per resident warp slot (2 blocks per SM): the
+            // other items take longer than plateau items, and one wave of
+            // mixed items leaves a tail (8192^2 ellipse: 2.59 ms per step at
+            // 256-row segments, 3.46 ms at the unsplit kernel's 512)
+            const int dseg = c->march_seg > 0
+                                 ? seg
+                                 : pick_segment(c->ny, n_wx, 4LL * WARPS * c->num_sms);
+            const auto &u = c->uplan;
+            if (dseg >= 16 && (u.gen != c->medium_gen || u.seg != dseg)) {
+                const cudaError_t e = build_plateau_plan_ds(c, dseg);
+                if (e != cudaSuccess) return e;
+            }
+            if (u.gen == c->medium_gen && u.seg == dseg && u.n_uniform > 0)
+                return launch_split_ds<VM, VIN>(c, in, out);
         }
     }
     const int blocks = (n_items + WARPS - 1) / WARPS;

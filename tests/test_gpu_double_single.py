@@ -173,3 +173,34 @@ def test_3d_rejected_configurations(kw):
     args.update(kw)
     with pytest.raises(qla.QLAError):
         qla.Grid3(args["nx"], args["ny"], args["nz"], 1.0, args["precision"], double_single=True)
+
+
+@pytest.mark.parametrize("rows,potential", [(0, "rotation"), (24, "rotation"), (16, "none")])
+def test_plateau_split_bitwise(rows, potential):
+    """E_z double-single steps split by plateaus (64-column plateau items
+    without the record ring) give the bits of the unsplit kernel; the 256^2
+    ellipse-like medium with sharp plateaus and a rough patch has items of
+    both kinds."""
+    nx, ny = 512, 320
+    y, x = np.mgrid[0:ny, 0:nx]
+    n = np.full((ny, nx), 2.0)
+    n[((x - nx / 2) / (nx / 5)) ** 2 + ((y - ny / 2) / (ny / 4)) ** 2 < 1.0] = 1.0
+    n[-40:, -70:] = np.random.default_rng(7).uniform(1.2, 2.8, (40, 70))
+    q0 = inputs.random_state(nx, ny, seed=41, planes=3)
+    out = {}
+    for kernel in ("march", "march_plain"):
+        with qla.Grid(nx, ny, 1.0, "fp64", te_only=True, potential=potential,
+                      double_single=True) as g:
+            g.set_step_kernel(kernel)
+            g.set_march_tuning(0, rows)
+            g.set_medium(n)
+            g.set_state(q0)
+            g.step(9)
+            out[kernel] = (g.get_state(), g.energy(), g.march_plan)
+    items, plateau, recs = out["march"][2]
+    assert recs == 2 and 0 < plateau < items, out["march"][2]
+    assert out["march_plain"][2] == (0, 0, 0)
+    assert np.array_equal(out["march"][0], out["march_plain"][0])
+    assert out["march"][1] == out["march_plain"][1]
+    want = oracle.run(q0, n, 1.0, 9, potential)
+    assert rel_l2(out["march"][0], want) <= 1e-12
