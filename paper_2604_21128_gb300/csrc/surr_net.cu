@@ -311,7 +311,10 @@ qla_status backward(surr_net *n, int B) {
 qla_status tc_waits_ok(surr_net *n) {
     int flag = 0;
     NCUDA(n, conv_tc_error(&flag, true), "surrogate: wait flag");
-    if (flag) return nfail(n, QLA_ETIMEOUT, "surrogate: a tensor-core wait ran out");
+    if (flag)
+        return nfail(n, QLA_ETIMEOUT,
+                     "surrogate: a tensor-core wait ran out; results of tensor-core launches "
+                     "are undefined until the network is rebuilt");
     return QLA_OK;
 }
 
