@@ -120,6 +120,22 @@ def test_init_rejects_bad_arguments_before_any_device_call(lib, args):
     assert e.value.status == 1
 
 
+def test_march_plan_of_a_null_context_host_only(lib):
+    assert lib.qla_march_plan(None, None, None, None) == 1   # QLA_EINVAL
+
+
+def test_plateau_unit_workspace_host_only(lib):
+    """FP32 E_z and double-single E_z contexts hold a plateau unit list;
+    its size grows with the lattice, not with the tuning."""
+    te = qla.QLA_TE_ONLY
+    a = qla.qla_workspace_bytes(1024, 512, qla.QLA_FP32, te)
+    b = qla.qla_workspace_bytes(1024, 1024, qla.QLA_FP32, te)
+    assert b > a > 0
+    ds = qla.QLA_DOUBLE_SINGLE
+    assert qla.qla_workspace_bytes(1024, 512, qla.QLA_FP64, te | ds) > \
+        qla.qla_workspace_bytes(1024, 512, qla.QLA_FP64, te)
+
+
 def test_status_strings(lib):
     lib.qla_status_string.restype = ctypes.c_char_p
     assert lib.qla_status_string(0) == b"QLA_OK"
