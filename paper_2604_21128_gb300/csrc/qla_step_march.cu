@@ -143,6 +143,10 @@ k_step_march_split_ds(const dsf *__restrict__ in, dsf *__restrict__ out,
 inline int pick_segment(int ny, int n_wx, long long resident_warps, int min_seg = 32) {
     if (resident_warps < 1) resident_warps = 1;
     long long target = 2 * resident_warps / n_wx;
+    // more segments than min_seg-row ones all give the same height (and the
+    // search below runs once per step launch: small lattices with large
+    // targets cost ~15 us of host time per step before this cap)
+    target = std::min<long long>(target, (ny + min_seg - 1) / min_seg);
     if (target < 1) target = 1;
     auto seg_for = [&](long long n_wy) {
         int seg = int((ny + n_wy - 1) / n_wy);
@@ -344,7 +348,11 @@ cudaError_t launch_t(qla_ctx *c, const void *in, void *out, const void *table) {
             int pseg = c->march_seg;
             if (pseg <= 0) {
                 const int n_pwx = (c->nx + PWOUT - 1) / PWOUT;
-                pseg = pick_segment(c->ny, n_pwx, 4LL * blocks_per_sm * WARPS * c->num_sms, 64);
+                const long long slots = (long long)blocks_per_sm * WARPS * c->num_sms;
+                // lattices with less than a wave of 64-row items (256^2: 12)
+                // are latency-bound: shorter segments give more warps
+                const int min_seg = (long long)((c->ny + 63) / 64) * n_pwx >= slots ? 64 : 16;
+                pseg = pick_segment(c->ny, n_pwx, 4 * slots, min_seg);
             } else {
                 pseg = (pseg + 3) / 4 * 4;
             }
