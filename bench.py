@@ -43,8 +43,11 @@ def parse():
     ap.add_argument("--qla-steps", type=int, default=100)
     ap.add_argument("--lane-cols", type=int, default=0, help="marching kernel tuning")
     ap.add_argument("--rows", type=int, default=0, help="marching kernel tuning")
-    ap.add_argument("--step-kernel", choices=["auto", "march", "march_plain", "tile"],
-                    default="auto", help="step kernel (march_plain: no plateau split)")
+    ap.add_argument("--step-kernel",
+                    choices=["auto", "march", "march_plain", "march_step", "march_flow", "tile"],
+                    default="auto",
+                    help="step kernel (march_plain: no plateau split; march_step: plateau split, "
+                         "one launch per step; march_flow: dataflow launches on any lattice)")
     ap.add_argument("--double-single", action="store_true",
                     help="FP64 contexts stepped in double-single arithmetic (QLA_DOUBLE_SINGLE)")
     ap.add_argument("--six-planes", action="store_true",
@@ -429,6 +432,7 @@ def gpu_arm(args):
     clocks = sampler.stop()
     launches = g.launches - launches0
     plan = g.march_plan
+    flow_rows = g.flow_plan
     elapsed = start.elapsed_time(stop) / 1e3
     step_time = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     elapsed = max_over_ranks(world, elapsed)
@@ -489,11 +493,13 @@ def gpu_arm(args):
                        + ("_ds" if ds else "") + ("_ez" if te else "_6planes"),
                        "nx": w.nx, "ny": w.ny, "delta": w.delta,
                        "qla_steps_per_bench_step": S, "planes": P,
-                       "potential": "rotation", "time_block": k_used,
+                       "potential": "rotation", "steps_per_launch": k_used,
                        "lane_cols": args.lane_cols or "auto", "rows": args.rows or "auto",
                        "step_kernel": args.step_kernel,
                        "plateau_items": "%d of %d work items, %d plateaus" % (plan[1], plan[0],
                                                                              plan[2]),
+                       "dataflow": ("%d-row segments, %d steps per launch" % (flow_rows, k_used)
+                                    if flow_rows else None),
                        "energy_drift": drift,
                        "l2": "state %.0f MB > 129 MB L2, no flush" % (2 * P * elt * sites / 2e6)},
             "roofline": roofline(P, elt, kernel_su_per_s, traffic,

@@ -275,14 +275,47 @@ qla_status qla_set_packet_window(qla_ctx *ctx, const qla_packet *p, int i0, int 
  * marching step after qla_set_medium or a tuning change classifies the
  * items (one small kernel and one synchronisation of the context's
  * stream), so it must not be the first call inside a stream capture.
- * QLA_KERNEL_MARCH_PLAIN = the marching kernel without the split. */
+ * QLA_KERNEL_MARCH_PLAIN = the marching kernel without the split.
+ * Dataflow steps (plateau split, lattices with at least about three work
+ * items per resident warp: 16384^2 at 192-row segments, 8192^2 at 64): a
+ * qla_step call runs all its steps in one persistent launch (after one
+ * ordinary launch for a first step with no pending potential step).  Blocks
+ * take the work units of every step, four at a time, from one counter in
+ * step order, and a unit of step s
+ * first waits until the items whose stored sites it reads, and those that
+ * read the sites it stores, have finished step s - 1 (each unit reaches
+ * four sites along x and y, Eqs. 2e6 and 2e9); the per-step tail of idle
+ * warps goes away and taller segments (fewer recomputed halo rows) pay.
+ * Results are bitwise those of one launch per step.  Each wait gives up
+ * after about two seconds of SM cycles; the next synchronising read
+ * (qla_energy, qla_energy_box, qla_divergence, qla_probe, qla_fields,
+ * qla_get_state) then returns QLA_ETIMEOUT and the state is undefined until
+ * it is set again (steps launched before that read do no work).
+ * QLA_KERNEL_MARCH_STEP = the plateau split, one launch per step;
+ * QLA_KERNEL_MARCH_FLOW = dataflow steps on every lattice the plateau
+ * split takes (32-row segments unless qla_set_march_tuning sets rows). */
 typedef enum {
     QLA_KERNEL_AUTO = 0,
     QLA_KERNEL_TILE = 1,
     QLA_KERNEL_MARCH = 2,
-    QLA_KERNEL_MARCH_PLAIN = 3
+    QLA_KERNEL_MARCH_PLAIN = 3,
+    QLA_KERNEL_MARCH_STEP = 4,
+    QLA_KERNEL_MARCH_FLOW = 5
 } qla_step_kernel;
 qla_status qla_set_step_kernel(qla_ctx *ctx, int kernel);
+
+/* Segment height (rows) of the current dataflow plan into *segment_rows, 0
+ * if the next steps run one launch each (or no plan is built yet). */
+qla_status qla_flow_plan(const qla_ctx *ctx, int *segment_rows);
+
+/* Test hook for the dataflow waits (never needed in normal use):
+ * budget_cycles > 0 sets each wait's limit in SM clock cycles (0 restores
+ * the default 2^32, about two seconds); withhold_unit >= 0 makes the unit
+ * handed out at that position of each dataflow launch (step-major: step s,
+ * unit k at s * units + k) finish without counting itself, so the units
+ * that depend on it wait out their limit and the next synchronising read
+ * returns QLA_ETIMEOUT with no fault; -1 restores normal. */
+qla_status qla_debug_flow(qla_ctx *ctx, long long budget_cycles, long long withhold_unit);
 
 /* Energy of caller-owned device planes, allocating nothing.
  *

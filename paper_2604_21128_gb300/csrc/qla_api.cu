@@ -116,6 +116,19 @@ struct DeviceGuard {
     ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
 };
 
+// After a synchronisation of the context's stream: QLA_ETIMEOUT if a
+// dataflow step launched since the last check gave up a dependency wait.
+qla_status check_flow(qla_ctx *c, const char *what) {
+    bool t = false;
+    const cudaError_t e = flow_timed_out(c, &t);
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    if (t)
+        return fail(c, QLA_ETIMEOUT,
+                    "%s: a dataflow step's dependency wait ran out; the state is undefined "
+                    "until it is set again", what);
+    return QLA_OK;
+}
+
 qla_status usable(qla_ctx *c) {
     if (!c) return QLA_EINVAL;
     if (c->sticky != QLA_OK) return c->sticky;
@@ -316,6 +329,7 @@ qla_status qla_set_packet(qla_ctx *c, const qla_packet *p) {
     QLA_CUDA(c, launch_packet(c, *p), "qla_set_packet: kernel");
     c->has_state = true;
     c->pending_v = false;
+    c->flow_unchecked = false;
     return QLA_OK;
 }
 
@@ -345,6 +359,7 @@ qla_status qla_set_packet_window(qla_ctx *c, const qla_packet *p, int i0, int j0
     QLA_CUDA(c, launch_packet_window(c, *p, i0, j0, gnx, gny), "qla_set_packet_window: kernel");
     c->has_state = true;
     c->pending_v = false;
+    c->flow_unchecked = false;
     return QLA_OK;
 }
 
@@ -398,6 +413,10 @@ qla_status qla_energy_box(qla_ctx *c, int i0, int j0, int w, int h, double *out)
     QLA_CUDA(c, cudaMemcpyAsync(out, c->result, 8, cudaMemcpyDeviceToHost, c->stream),
              "qla_energy_box: copy");
     QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_energy_box: sync");
+    {
+        const qla_status f = check_flow(c, "qla_energy_box");
+        if (f != QLA_OK) return f;
+    }
     if (!std::isfinite(*out)) return fail(c, QLA_ENONFINITE, "qla_energy_box: energy is %g", *out);
     return QLA_OK;
 }
@@ -433,6 +452,7 @@ qla_status qla_set_state(qla_ctx *c, const double *q_host) {
     QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_set_state: sync");
     c->has_state = true;
     c->pending_v = false;
+    c->flow_unchecked = false;   // a wait that ran out concerned the old state
     return QLA_OK;
 }
 
@@ -455,7 +475,7 @@ qla_status qla_get_state(qla_ctx *c, double *q_host) {
                  "qla_get_state: copy");
         QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_get_state: sync");
     }
-    return QLA_OK;
+    return check_flow(c, "qla_get_state");
 }
 
 qla_status qla_step(qla_ctx *c, long long n_steps) {
@@ -499,7 +519,16 @@ qla_status qla_step(qla_ctx *c, long long n_steps) {
     }
     const bool march = c->step_kernel == QLA_KERNEL_MARCH ||
                        c->step_kernel == QLA_KERNEL_MARCH_PLAIN ||
+                       c->step_kernel == QLA_KERNEL_MARCH_STEP ||
+                       c->step_kernel == QLA_KERNEL_MARCH_FLOW ||
                        (c->step_kernel == QLA_KERNEL_AUTO && march_ok(c));
+    if (march) {
+        // all n steps in persistent dataflow launches where the context
+        // takes them
+        bool done = false;
+        QLA_CUDA(c, launch_step_flow(c, n_steps, &done), "qla_step: dataflow kernel");
+        if (done) return QLA_OK;
+    }
     for (long long k = 0; k < n_steps; ++k) {
         const bool vin = c->pending_v;
         QLA_CUDA(c, march ? launch_step_march(c, c->state[c->cur], c->state[c->cur ^ 1], vin)
@@ -523,6 +552,10 @@ qla_status qla_energy(qla_ctx *c, double *out) {
     QLA_CUDA(c, cudaMemcpyAsync(out, c->result, 8, cudaMemcpyDeviceToHost, c->stream),
              "qla_energy: copy");
     QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_energy: sync");
+    {
+        const qla_status f = check_flow(c, "qla_energy");
+        if (f != QLA_OK) return f;
+    }
     if (!std::isfinite(*out)) return fail(c, QLA_ENONFINITE, "qla_energy: energy is %g", *out);
     return QLA_OK;
 }
@@ -539,6 +572,10 @@ qla_status qla_divergence(qla_ctx *c, double *out) {
     QLA_CUDA(c, cudaMemcpyAsync(out, c->result, 8 * DIV_TERMS, cudaMemcpyDeviceToHost, c->stream),
              "qla_divergence: copy");
     QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_divergence: sync");
+    {
+        const qla_status f = check_flow(c, "qla_divergence");
+        if (f != QLA_OK) return f;
+    }
     for (int k = 0; k < DIV_TERMS; ++k)
         if (!std::isfinite(out[k]))
             return fail(c, QLA_ENONFINITE, "qla_divergence: term %d is %g", k, out[k]);
@@ -562,7 +599,7 @@ qla_status qla_fields(qla_ctx *c, double *Ex, double *Ey, double *Ez, double *Bx
                  "qla_fields: copy");
         QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_fields: sync");
     }
-    return QLA_OK;
+    return check_flow(c, "qla_fields");
 }
 
 qla_status qla_probe(qla_ctx *c, int count, const int *i, const int *j, double *out) {
@@ -597,15 +634,19 @@ qla_status qla_probe(qla_ctx *c, int count, const int *i, const int *j, double *
                                 cudaMemcpyDeviceToHost, c->stream),
              "qla_probe: copy out");
     QLA_CUDA(c, cudaStreamSynchronize(c->stream), "qla_probe: sync");
+    {
+        const qla_status f = check_flow(c, "qla_probe");
+        if (f != QLA_OK) return f;
+    }
     return QLA_OK;
 }
 
 qla_status qla_set_step_kernel(qla_ctx *c, int kernel) {
     qla_status s = usable(c);
     if (s != QLA_OK) return s;
-    if (kernel < QLA_KERNEL_AUTO || kernel > QLA_KERNEL_MARCH_PLAIN)
+    if (kernel < QLA_KERNEL_AUTO || kernel > QLA_KERNEL_MARCH_FLOW)
         return fail(c, QLA_EINVAL, "qla_set_step_kernel: unknown kernel %d", kernel);
-    const bool march = kernel == QLA_KERNEL_MARCH || kernel == QLA_KERNEL_MARCH_PLAIN;
+    const bool march = kernel != QLA_KERNEL_AUTO && kernel != QLA_KERNEL_TILE;
     if (march && ((c->tensor && c->P == 6) || c->vmode == V_LCU))
         return fail(c, QLA_EINVAL, "qla_set_step_kernel: six-plane tensor media and the LCU "
                                    "potential use the tile kernel");
@@ -631,6 +672,24 @@ qla_status qla_set_march_tuning(qla_ctx *c, int lane_cols, int rows) {
 }
 
 long long qla_launch_count(const qla_ctx *c) { return c ? c->launches : 0; }
+
+qla_status qla_flow_plan(const qla_ctx *c, int *segment_rows) {
+    if (!c || !segment_rows) return QLA_EINVAL;
+    const auto &u = c->uplan;
+    *segment_rows = u.gen == c->medium_gen && u.flow && u.n_uniform > 0 ? u.seg : 0;
+    return QLA_OK;
+}
+
+qla_status qla_debug_flow(qla_ctx *c, long long budget_cycles, long long withhold_unit) {
+    qla_status s = usable(c);
+    if (s != QLA_OK) return s;
+    if (budget_cycles < 0 || withhold_unit < -1)
+        return fail(c, QLA_EINVAL, "qla_debug_flow: budget %lld, unit %lld", budget_cycles,
+                    withhold_unit);
+    c->flow_budget = budget_cycles > 0 ? budget_cycles : (1LL << 32);
+    c->flow_withhold = withhold_unit;
+    return QLA_OK;
+}
 
 qla_status qla_march_plan(const qla_ctx *c, int *n_items, int *n_plateau_items, int *n_sets) {
     if (!c) return QLA_EINVAL;

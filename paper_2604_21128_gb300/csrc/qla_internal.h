@@ -394,7 +394,19 @@ struct qla_ctx {
     struct {
         long long gen = -1;
         int seg = 0, n_items = 0, n_list = 0, n_uniform = 0, n_sets = 0;
+        // dataflow plan (units in item order; byte offsets into items of
+        // the two dependency tables and of the counters: the hand-out
+        // counter, then one per item from off_ctr + 16)
+        bool flow = false, want_flow = false;
+        int n_wx = 0, shift = 0;
+        size_t off_xdep = 0, off_ydep = 0, off_ctr = 0;
     } uplan;
+    // dataflow steps: a launch whose wait flag has not been read yet, each
+    // wait's limit in SM cycles, and a test hook (the handed-out unit index
+    // whose completion is withheld, -1 none)
+    bool flow_unchecked = false;
+    long long flow_budget = 1LL << 32;
+    long long flow_withhold = -1;
     qla_status sticky = QLA_OK;
     std::string err;
 };
@@ -459,6 +471,14 @@ cudaError_t launch_energy_box(qla_ctx *c, int i0, int j0, int w, int h);
 cudaError_t launch_packet_window(qla_ctx *c, const qla_packet &p, int i0, int j0, int gnx,
                                  int gny);
 cudaError_t launch_step_march(qla_ctx *c, const void *in, void *out, bool vin);
+// Dataflow steps (FP32 E_z plateau split): n_steps steps of c->state[c->cur]
+// in one persistent launch, leaving the result in state[c->cur ^ (n_steps &
+// 1)].  *done = false (nothing enqueued) where the context does not take
+// them; needs a pending potential step if the context has a potential.
+cudaError_t launch_step_flow(qla_ctx *c, long long n_steps, bool *done);
+// Reads (and clears) the wait flag of the dataflow launches since the last
+// read; the stream must be idle.  Returns true if a wait ran out.
+cudaError_t flow_timed_out(qla_ctx *c, bool *timed_out);
 bool march_supported(const qla_ctx *c);
 int march_lane_cols(const qla_ctx *c);
 }  // namespace qla

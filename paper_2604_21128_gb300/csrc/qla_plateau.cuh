@@ -174,5 +174,113 @@ inline int plateau_units(const std::vector<int> &cls, int nx, int ny, int seg,
     return n_plateau;
 }
 
+// ---------------------------------------------------------------------------
+// Dataflow steps: several steps of the unit list in one persistent launch.
+//
+// Between two steps the only ordering the step needs is local: a unit of
+// step s reads its window of the buffer step s - 1 wrote (four columns and
+// four rows beyond what it stores, Eqs. 2e6 and 2e9) and writes the buffer
+// that step s - 1 read.  So instead of a launch (a grid-wide barrier) per
+// step, warps take units of all steps from one counter in step order, and a
+// unit of step s first waits until every item it depends on has finished
+// step s - 1: those whose stored columns and rows it reads (read after
+// write) and those that read what it stores (write after read).  Dependencies
+// are always handed out earlier than their dependants, and the warp holding
+// the earliest unfinished unit never waits, so the launch cannot deadlock
+// whatever the residency; the warps that finish a step early start on the
+// next one instead of idling at the step's tail.
+//
+// Per item a counter grows by 6 per finished step: a plateau unit adds 6,
+// each of the n two-column units of another item 6 / n (n <= 3).  Step
+// s - 1 of an item is complete when its counter reaches 6 s, since its
+// step-s units wait for that themselves.
+
+constexpr int FLOW_DEPS = 8;   // per axis: a count and up to seven indices
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait (the whole warp) until every item of the x-dependencies of window wx
+// times the y-dependencies of segment wy has a counter >= target.  Each lane
+// polls one dependency with an acquire load, so its later reads see what
+// those items stored.  Gives up after `budget` SM cycles (raising *err) or
+// when another warp has raised it; returns false then.
+__device__ __forceinline__ bool flow_wait(const int *__restrict__ xdep,
+                                          const int *__restrict__ ydep, const unsigned *done,
+                                          int n_wx, int wx, int wy, unsigned target, int *err,
+                                          long long budget) {
+    const int lane = threadIdx.x & 31;
+    const int cx = xdep[wx * FLOW_DEPS], cy = ydep[wy * FLOW_DEPS];
+    const int n = cx * cy;
+    const long long t0 = clock64();
+    for (int base = 0; base < n; base += 32) {
+        const int k = base + lane < n ? base + lane : base;
+        const int d = ydep[wy * FLOW_DEPS + 1 + k / cx] * n_wx + xdep[wx * FLOW_DEPS + 1 + k % cx];
+        for (;;) {
+            const bool ok = ld_acquire_gpu(done + d) >= target;
+            if (__all_sync(0xffffffffu, ok)) break;
+            // decided by a vote, so that the warp leaves together
+            const bool stop = *static_cast<volatile int *>(err) != 0 || clock64() - t0 > budget;
+            if (__any_sync(0xffffffffu, stop)) {
+                if (lane == 0) atomicExch(err, 1);
+                return false;
+            }
+            __nanosleep(256);
+        }
+    }
+    return true;
+}
+
+// The counter increment of unit u (window wx of a lattice nx wide).
+__host__ __device__ inline unsigned flow_increment(const int4 &u, int nx, int wx) {
+    if ((u.y >> 8) - 1 >= 0) return 6u;
+    const int rest = nx - wx * PWOUT, w = rest < PWOUT ? rest : PWOUT;
+    return 6u / unsigned((w + GWOUT - 1) / GWOUT);
+}
+
+// Host: the dependency table of one axis.  Block a of n_blocks stores
+// [a * width, min(len, (a + 1) * width)) of a periodic axis of length len
+// and reads [a * width - lo, read_end(a)).  Entry a * FLOW_DEPS holds the
+// count, then the blocks b (a itself included) for which a's reads meet b's
+// stores or b's reads meet a's stores.  Blocks more than three apart never
+// do: reads reach at most 172 columns past a window's start (120-column
+// windows) or four rows past a segment (at least 16 rows), and only the last
+// block is narrower.  Returns false if a block has more than seven.
+template <typename ReadEnd>
+inline bool flow_axis_deps(long long len, int width, int n_blocks, int lo, ReadEnd read_end,
+                           std::vector<int> &out) {
+    out.assign(size_t(n_blocks) * FLOW_DEPS, 0);
+    auto overlap = [len](long long s1, long long e1, long long s2, long long e2) {
+        if (e1 - s1 >= len || e2 - s2 >= len) return true;
+        for (long long k = -2; k <= 2; ++k)
+            if (s1 + k * len < e2 && s2 < e1 + k * len) return true;
+        return false;
+    };
+    auto ws = [&](int a) { return (long long)a * width; };
+    auto we = [&](int a) { return std::min(len, (long long)a * width + width); };
+    for (int a = 0; a < n_blocks; ++a) {
+        int cand[7], nc = 0;
+        if (n_blocks <= 7) {
+            for (int b = 0; b < n_blocks; ++b) cand[nc++] = b;
+        } else {
+            for (int d = -3; d <= 3; ++d) cand[nc++] = ((a + d) % n_blocks + n_blocks) % n_blocks;
+        }
+        int cnt = 0;
+        for (int t = 0; t < nc; ++t) {
+            const int b = cand[t];
+            if (!overlap(ws(a) - lo, read_end(a), ws(b), we(b)) &&
+                !overlap(ws(b) - lo, read_end(b), ws(a), we(a)))
+                continue;
+            if (cnt == FLOW_DEPS - 1) return false;
+            out[size_t(a) * FLOW_DEPS + 1 + cnt++] = b;
+        }
+        out[size_t(a) * FLOW_DEPS] = cnt;
+    }
+    return true;
+}
+
 }  // namespace march
 }  // namespace qla

@@ -114,6 +114,66 @@ k_step_march_split(const float *__restrict__ in, float *__restrict__ out,
                               smem_raw + warp * plateau_ring_bytes<VM, VIN>());
 }
 
+// Dataflow steps of the plateau split (see flow_wait): n_steps steps of
+// the unit list in one persistent launch, buffers a (the input of even
+// steps) and b.  Blocks take four consecutive units w .. w + 3 (w = s *
+// n_units + k) from the counter ctr[0], one per warp: neighbouring windows
+// of one segment then start together, as the blocks of a per-step launch
+// do, and the sectors they share at their edges are read once from DRAM
+// (warps taking units one by one started them apart in time and read 20%
+// more).  Odd steps start half-way down the lattice (k + shift), so that
+// the first units of a step depend on units handed out half a step earlier
+// rather than on the last ones of the step before.  done = ctr + 4: one
+// counter per item.  A warp whose wait ran out (or that finds *err raised)
+// skips its unit but still counts it, so the launch drains.
+template <int VM>
+__global__ void __launch_bounds__(32 * WARPS, 4)
+k_step_march_flow(float *a, float *b, const uint32_t *__restrict__ midx,
+                  const MedRec<float> *__restrict__ table, int nx, int ny, int pitch,
+                  size_t plane, const int4 *__restrict__ units, int n_units, int seg, int n_wx,
+                  int shift, const int *__restrict__ xdep, const int *__restrict__ ydep,
+                  unsigned *ctr, int *err, int n_steps, long long budget, long long withhold) {
+    constexpr bool VIN = VM != V_NONE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned s_w;
+    __shared__ int s_e;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *ring = smem_raw + warp * plateau_ring_bytes<VM, VIN>();
+    unsigned *done = ctr + 4;
+    const unsigned total = unsigned(n_units) * unsigned(n_steps);
+    for (;;) {
+        __syncthreads();   // every warp has read the previous group
+        if (threadIdx.x == 0) {
+            s_w = atomicAdd(ctr, unsigned(WARPS));
+            s_e = *static_cast<volatile int *>(err);
+        }
+        __syncthreads();
+        if (s_w >= total) break;   // the whole block
+        const unsigned w = s_w + unsigned(warp);
+        if (w >= total) continue;
+        const int s = int(w / unsigned(n_units));
+        int k = int(w - unsigned(s) * unsigned(n_units));
+        if (s & 1) {
+            k += shift;
+            if (k >= n_units) k -= n_units;
+        }
+        const int4 u = units[k];
+        const int wx = u.x / PWOUT, wy = u.z / seg;
+        bool go = s_e == 0;
+        if (go && s > 0)
+            go = flow_wait(xdep, ydep, done, n_wx, wx, wy, 6u * unsigned(s), err, budget);
+        if (go)
+            run_plateau_unit<VM, VIN>((s & 1) ? b : a, (s & 1) ? a : b, midx, table, nx, ny,
+                                      pitch, uint32_t(plane), u, ring);
+        // publish: every lane's stores, then the item's counter
+        __syncwarp();
+        if (lane == 0 && (long long)w != withhold) {
+            __threadfence();
+            atomicAdd(done + (wy * n_wx + wx), flow_increment(u, nx, wx));
+        }
+    }
+}
+
 // The double-single plateau split (E_z): the same units at 64-column
 // windows.  The record-ring march of the other units needs 194 registers;
 // holding the kernel to 3 or 4 blocks per SM made those units spill and the
@@ -187,13 +247,17 @@ template <int VM, bool VIN> struct Variant<float, 3, 5, VM, VIN> : Variant2<Pair
 
 // The plateau plan for segments of `seg` rows: classify the plateau-window
 // items and write the unit list to c->items (the other items' units first,
-// then the plateau units).  Synchronises the context's stream once.
-cudaError_t build_plateau_plan(qla_ctx *c, int seg) {
+// then the plateau units).  With `flow`, the units go in item order (rows of
+// items top to bottom), followed by the dataflow tables; the plan is left
+// unbuilt if they do not fit.  Synchronises the context's stream once.
+cudaError_t build_plateau_plan(qla_ctx *c, int seg, bool flow) {
     auto &u = c->uplan;
     u.gen = -1;
     u.n_uniform = 0;
+    u.flow = false;
     const int n_wx = (c->nx + PWOUT - 1) / PWOUT;
-    const int n_items = n_wx * ((c->ny + seg - 1) / seg);
+    const int n_wy = (c->ny + seg - 1) / seg;
+    const int n_items = n_wx * n_wy;
     // capacity: three units per item at most
     if (size_t(3) * n_items > c->items_cap) return cudaSuccess;
     int *cls_dev = reinterpret_cast<int *>(c->items);
@@ -208,17 +272,71 @@ cudaError_t build_plateau_plan(qla_ctx *c, int seg) {
     if (e != cudaSuccess) return e;
     std::vector<int4> list, plat;
     list.reserve(size_t(3) * n_items);
-    const int n_plateau = plateau_units(cls, c->nx, c->ny, seg, list, plat);
-    list.insert(list.end(), plat.begin(), plat.end());
+    int n_plateau = 0;
+    if (flow) {
+        // item order: each item's units together, rows of items in turn
+        for (int i = 0; i < n_items; ++i) {
+            const int wx = i % n_wx, wy = i / n_wx;
+            const int x_out = wx * PWOUT, w_out = std::min(PWOUT, c->nx - x_out);
+            const int y_lo = wy * seg, y_hi = std::min(c->ny, y_lo + seg);
+            if (cls[i] >= 0) {
+                list.push_back(plateau_unit(x_out, w_out, cls[i], y_lo, y_hi));
+                ++n_plateau;
+            } else {
+                for (int x = x_out; x < x_out + w_out; x += GWOUT)
+                    list.push_back(
+                        plateau_unit(x, std::min(GWOUT, x_out + w_out - x), -1, y_lo, y_hi));
+            }
+        }
+    } else {
+        n_plateau = plateau_units(cls, c->nx, c->ny, seg, list, plat);
+        list.insert(list.end(), plat.begin(), plat.end());
+    }
     std::vector<int> recs;
     for (int v : cls)
         if (v >= 0) recs.push_back(v);
     std::sort(recs.begin(), recs.end());
     const int n_recs = int(std::unique(recs.begin(), recs.end()) - recs.begin());
-    e = cudaMemcpyAsync(c->items, list.data(), list.size() * sizeof(int4), cudaMemcpyHostToDevice,
-                        c->stream);
+    // the bytes uploaded: the unit list, then (flow) the two dependency
+    // tables; the counters follow and are cleared by each launch
+    std::vector<char> blob(list.size() * sizeof(int4));
+    memcpy(blob.data(), list.data(), blob.size());
+    size_t off_xdep = 0, off_ydep = 0, off_ctr = 0;
+    if (flow) {
+        std::vector<int> xd, yd;
+        const bool ok_x = flow_axis_deps(c->nx, PWOUT, n_wx, 4, [&](int a) {
+            const long long x = (long long)a * PWOUT;
+            const int w = int(std::min<long long>(PWOUT, c->nx - x));
+            const int last = (w - 1) / GWOUT * GWOUT;   // start of the last two-column unit
+            return x + std::max(PW - 4, last + 64 - 4);
+        }, xd);
+        const bool ok_y = flow_axis_deps(c->ny, seg, n_wy, LAG, [&](int a) {
+            return std::min<long long>(c->ny, (long long)(a + 1) * seg) + LAG;
+        }, yd);
+        off_xdep = (blob.size() + 15) / 16 * 16;
+        off_ydep = off_xdep + (xd.size() * 4 + 15) / 16 * 16;
+        off_ctr = off_ydep + (yd.size() * 4 + 15) / 16 * 16;
+        const size_t end = off_ctr + 16 + size_t(n_items) * 4;
+        // the wait flag sits in the last 16 bytes of the region
+        if (!ok_x || !ok_y || end + 16 > c->items_cap * sizeof(int4)) return cudaSuccess;
+        blob.resize(off_ctr, 0);
+        memcpy(blob.data() + off_xdep, xd.data(), xd.size() * 4);
+        memcpy(blob.data() + off_ydep, yd.data(), yd.size() * 4);
+    }
+    e = cudaMemcpyAsync(c->items, blob.data(), blob.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return e;
+    if (flow) {
+        u.flow = true;
+        u.n_wx = n_wx;
+        // odd steps start at the first unit of segment n_wy / 2
+        int shift = 0;
+        while (shift < int(list.size()) && list[shift].z < (n_wy / 2) * seg) ++shift;
+        u.shift = shift == int(list.size()) ? 0 : shift;
+        u.off_xdep = off_xdep;
+        u.off_ydep = off_ydep;
+        u.off_ctr = off_ctr;
+    }
     u.gen = c->medium_gen;
     u.seg = seg;
     u.n_items = n_items;
@@ -270,6 +388,105 @@ cudaError_t build_plateau_plan_ds(qla_ctx *c, int seg) {
     u.n_list = int(list.size());
     u.n_uniform = n_plateau;
     u.n_sets = n_recs;
+    return cudaSuccess;
+}
+
+// The dataflow launches' wait flag: the last 16 bytes of the unit region,
+// which no plan uses, so it survives plan rebuilds until the host reads it.
+int *flow_flag(qla_ctx *c) {
+    return reinterpret_cast<int *>(reinterpret_cast<char *>(c->items) + c->items_cap * 16 - 16);
+}
+
+// The plan of segments of `seg` rows (dataflow order and tables with
+// `flow`), built unless it is the current one.  A dataflow plan that does
+// not fit the workspace falls back to the per-step plan of the same
+// segments (and is not retried until the medium or the tuning changes).
+cudaError_t ensure_plateau_plan(qla_ctx *c, int seg, bool flow) {
+    auto &u = c->uplan;
+    if (u.gen == c->medium_gen && u.seg == seg && u.want_flow == flow) return cudaSuccess;
+    cudaError_t e = build_plateau_plan(c, seg, flow);
+    if (e == cudaSuccess && flow && u.gen != c->medium_gen) e = build_plateau_plan(c, seg, false);
+    if (e == cudaSuccess) u.want_flow = flow;
+    return e;
+}
+
+// Segment height of the dataflow plan of an FP32 E_z context, or 0 where its
+// steps run one launch each.  Dataflow steps need about three items per
+// resident warp slot: a unit's dependencies are then handed out about 1.5
+// waves before it (half a step, see k_step_march_flow) and have finished.
+// Taller segments recompute fewer halo rows but leave less of that slack:
+// without a tuning, the tallest segment of 64 to 256 rows (multiples of 32)
+// with at least 4.5 items per slot, else 64 rows with at least three
+// (measured on the 16384^2 vacuum bubble, per step: 1.375 ms at 192 rows
+// with 4.8 items per slot, 1.395 ms at 256 rows with 3.6, 1.401 ms at 128
+// rows with 7.2, against 1.415 ms for launches per step; 8192^2 ellipse:
+// 0.398 ms at 64 rows with 3.6, against 0.403 ms).
+// QLA_KERNEL_MARCH_FLOW takes dataflow steps on any lattice the plateau
+// split takes (32-row segments where none gives three items per slot).
+int flow_segment(const qla_ctx *c) {
+    if (c->prec != QLA_FP32 || c->P != 3 || march_lane_cols(c) != 2 || !c->items ||
+        c->nx % 4 != 0 || c->nx < PW)
+        return 0;
+    const int k = c->step_kernel;
+    if (k != QLA_KERNEL_AUTO && k != QLA_KERNEL_MARCH && k != QLA_KERNEL_MARCH_FLOW) return 0;
+    const long long n_wx = (c->nx + PWOUT - 1) / PWOUT;
+    const long long slots = 4LL * WARPS * c->num_sms;
+    // items x 2 >= slots x twice the target
+    auto items2 = [&](int seg) { return 2 * n_wx * ((c->ny + seg - 1) / seg); };
+    if (c->march_seg > 0) {
+        const int seg = std::max(16, (c->march_seg + 3) / 4 * 4);
+        return k == QLA_KERNEL_MARCH_FLOW || items2(seg) >= 6 * slots ? seg : 0;
+    }
+    for (int seg = 256; seg >= 64; seg -= 32)
+        if (items2(seg) >= 9 * slots) return seg;
+    if (items2(64) >= 6 * slots) return 64;
+    return k == QLA_KERNEL_MARCH_FLOW ? 32 : 0;
+}
+
+template <int VM>
+cudaError_t launch_flow(qla_ctx *c, const void *in, void *out, long long n_steps) {
+    auto kern = k_step_march_flow<VM>;
+    constexpr bool VIN = VM != V_NONE;
+    const size_t smem = plateau_ring_bytes<VM, VIN>() * WARPS;
+    struct Occ { cudaError_t err; int per_sm; };
+    static const Occ occ = [&] {
+        Occ o{cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+              1};
+        int b = 0;
+        if (o.err == cudaSuccess)
+            o.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * WARPS, smem);
+        o.per_sm = b > 0 ? b : 1;
+        return o;
+    }();
+    if (occ.err != cudaSuccess) return occ.err;
+    const auto &u = c->uplan;
+    char *base = reinterpret_cast<char *>(c->items);
+    unsigned *ctr = reinterpret_cast<unsigned *>(base + u.off_ctr);
+    int *err = flow_flag(c);
+    if (!c->flow_unchecked) {
+        const cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    // units x steps of one launch below 2^31, item counters below 2^32
+    const long long per = std::max(1LL, std::min<long long>((1LL << 31) / u.n_list, 1LL << 26));
+    float *a = static_cast<float *>(const_cast<void *>(in)), *b = static_cast<float *>(out);
+    for (long long left = n_steps; left > 0;) {
+        const long long k = std::min(per, left);
+        cudaError_t e = cudaMemsetAsync(ctr, 0, 16 + size_t(u.n_items) * 4, c->stream);
+        if (e != cudaSuccess) return e;
+        kern<<<occ.per_sm * c->num_sms, 32 * WARPS, smem, c->stream>>>(
+            a, b, c->midx, static_cast<const MedRec<float> *>(c->table), c->nx, c->ny, c->pitch,
+            c->plane_elems, reinterpret_cast<const int4 *>(c->items), u.n_list, u.seg, u.n_wx,
+            u.shift, reinterpret_cast<const int *>(base + u.off_xdep),
+            reinterpret_cast<const int *>(base + u.off_ydep), ctr, err, int(k), c->flow_budget,
+            c->flow_withhold);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        c->launches++;
+        c->flow_unchecked = true;
+        if (k & 1) std::swap(a, b);
+        left -= k;
+    }
     return cudaSuccess;
 }
 
@@ -345,7 +562,8 @@ cudaError_t launch_t(qla_ctx *c, const void *in, void *out, const void *table) {
             // per step: 16384^2 vacuum bubble 1.51 ms at 96-128 rows, 1.54 at
             // 256, 1.65 at 512; 8192^2 ellipse 0.430 ms at 64 rows, 0.453 at
             // 128, 0.467 at 256)
-            int pseg = c->march_seg;
+            const int fseg = flow_segment(c);
+            int pseg = fseg > 0 ? fseg : c->march_seg;
             if (pseg <= 0) {
                 const int n_pwx = (c->nx + PWOUT - 1) / PWOUT;
                 const long long slots = (long long)blocks_per_sm * WARPS * c->num_sms;
@@ -357,8 +575,8 @@ cudaError_t launch_t(qla_ctx *c, const void *in, void *out, const void *table) {
                 pseg = (pseg + 3) / 4 * 4;
             }
             const auto &u = c->uplan;
-            if (pseg >= 16 && (u.gen != c->medium_gen || u.seg != pseg)) {
-                const cudaError_t e = build_plateau_plan(c, pseg);
+            if (pseg >= 16) {
+                const cudaError_t e = ensure_plateau_plan(c, pseg, fseg > 0);
                 if (e != cudaSuccess) return e;
             }
             if (u.gen == c->medium_gen && u.seg == pseg && u.n_uniform > 0)
@@ -469,6 +687,49 @@ cudaError_t launch_step_march(qla_ctx *c, const void *in, void *out, bool vin) {
     case 4: return launch_vm<float, 3, 4>(c, in, out, vin);
     default: return launch_vm<float, 3, 2>(c, in, out, vin);
     }
+}
+
+cudaError_t launch_step_flow(qla_ctx *c, long long n_steps, bool *done) {
+    *done = false;
+    const int seg = flow_segment(c);
+    if (seg <= 0 || n_steps < 1) return cudaSuccess;
+    cudaError_t e = ensure_plateau_plan(c, seg, true);
+    if (e != cudaSuccess) return e;
+    const auto &u = c->uplan;
+    if (u.gen != c->medium_gen || u.seg != seg || !u.flow || u.n_uniform == 0) return cudaSuccess;
+    *done = true;
+    if (!c->pending_v && c->vmode != V_NONE) {
+        // the first step has no potential step to apply on entry: one
+        // per-step launch (the same plan), the rest with it pending
+        e = launch_step_march(c, c->state[c->cur], c->state[c->cur ^ 1], false);
+        if (e != cudaSuccess) return e;
+        c->launches++;
+        c->cur ^= 1;
+        c->pending_v = true;
+        if (--n_steps == 0) return cudaSuccess;
+    }
+    const void *in = c->state[c->cur];
+    void *out = c->state[c->cur ^ 1];
+    switch (c->vmode) {
+    case V_ROTATION: e = launch_flow<V_ROTATION>(c, in, out, n_steps); break;
+    case V_LITERAL: e = launch_flow<V_LITERAL>(c, in, out, n_steps); break;
+    default: e = launch_flow<V_NONE>(c, in, out, n_steps); break;
+    }
+    if (e != cudaSuccess) return e;
+    if (n_steps & 1) c->cur ^= 1;
+    c->pending_v = c->vmode != V_NONE;
+    return cudaSuccess;
+}
+
+cudaError_t flow_timed_out(qla_ctx *c, bool *timed_out) {
+    *timed_out = false;
+    if (!c->flow_unchecked) return cudaSuccess;
+    int v = 0;
+    const cudaError_t e = cudaMemcpy(&v, flow_flag(c), sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    c->flow_unchecked = false;
+    *timed_out = v != 0;
+    return cudaSuccess;
 }
 
 }  // namespace qla

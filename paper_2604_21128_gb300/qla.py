@@ -26,6 +26,7 @@ QLA_ANISOTROPIC = 8
 QLA_POTENTIAL_LCU = 16
 QLA_DOUBLE_SINGLE = 32
 QLA_KERNEL_AUTO, QLA_KERNEL_TILE, QLA_KERNEL_MARCH, QLA_KERNEL_MARCH_PLAIN = 0, 1, 2, 3
+QLA_KERNEL_MARCH_STEP, QLA_KERNEL_MARCH_FLOW = 4, 5
 
 STATUS = {0: "QLA_OK", 1: "QLA_EINVAL", 2: "QLA_ESTATE", 3: "QLA_ENOMEM",
           4: "QLA_ECUDA", 5: "QLA_ETIMEOUT", 6: "QLA_ENONFINITE"}
@@ -73,6 +74,8 @@ def load():
                            ("qla_set_step_kernel", [c_vp, c_int]),
                            ("qla_set_march_tuning", [c_vp, c_int, c_int]),
                            ("qla_march_plan", [c_vp, c_vp, c_vp, c_vp]),
+                           ("qla_flow_plan", [c_vp, c_vp]),
+                           ("qla_debug_flow", [c_vp, c_ll, c_ll]),
                            ("qla_set_packet_window", [c_vp, ctypes.POINTER(qla_packet), c_int,
                                                       c_int, c_int, c_int]),
                            ("qla_pack_box", [c_vp, c_int, c_int, c_int, c_int, c_vp]),
@@ -308,6 +311,17 @@ def qla_march_plan(ctx):
     return a.value, b.value, n.value
 
 
+def qla_flow_plan(ctx):
+    """Segment rows of the current dataflow plan (0: one launch per step)."""
+    v = ctypes.c_int(0)
+    _check(ctx, load().qla_flow_plan(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def qla_debug_flow(ctx, budget_cycles=0, withhold_unit=-1):
+    _check(ctx, load().qla_debug_flow(ctx, int(budget_cycles), int(withhold_unit)))
+
+
 def qla_last_error(ctx):
     return load().qla_last_error(ctx).decode()
 
@@ -410,9 +424,11 @@ class Grid:
             return qla_probe(self._ctx, i, j)
 
     def set_step_kernel(self, kernel):
-        """"auto", "tile", "march" or "march_plain" (see qla_set_step_kernel)."""
+        """"auto", "tile", "march", "march_plain", "march_step" or "march_flow"
+        (see qla_set_step_kernel)."""
         k = {"auto": QLA_KERNEL_AUTO, "tile": QLA_KERNEL_TILE, "march": QLA_KERNEL_MARCH,
-             "march_plain": QLA_KERNEL_MARCH_PLAIN}
+             "march_plain": QLA_KERNEL_MARCH_PLAIN, "march_step": QLA_KERNEL_MARCH_STEP,
+             "march_flow": QLA_KERNEL_MARCH_FLOW}
         qla_set_step_kernel(self._ctx, k.get(kernel, kernel))
 
     def set_march_tuning(self, lane_cols=0, rows=0):
@@ -465,6 +481,15 @@ class Grid:
     def march_plan(self):
         """(work items, plateau items, plateau records) of the last marching step."""
         return qla_march_plan(self._ctx)
+
+    @property
+    def flow_plan(self):
+        """Segment rows of the dataflow plan (0: one launch per step)."""
+        return qla_flow_plan(self._ctx)
+
+    def debug_flow(self, budget_cycles=0, withhold_unit=-1):
+        """Test hook for the dataflow waits (see qla_debug_flow)."""
+        qla_debug_flow(self._ctx, budget_cycles, withhold_unit)
 
     def close(self):
         if getattr(self, "_borrowed", False):

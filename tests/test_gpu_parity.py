@@ -20,8 +20,12 @@ pytestmark = pytest.mark.gpu
 
 # Full-size FP32 runs of 16-24 steps, sampled sites against the oracle: the
 # absolute error per amplitude (packet amplitude 1; q2 = n E_z up to 2 inside
-# the dielectric).  Each step rounds ~18 rotations at ~2^-24 relative.
-FP32_SITE_BOUND = 2e-5
+# the dielectric).  Each step rounds ~18 rotation outputs at 2^-24 relative;
+# as a random walk over 24 steps that is of order sqrt(432) * 2^-24 ~ 1.2e-6 per
+# unit amplitude, and the sampled sites show 3e-7 - 5e-7.  (A systematic
+# coefficient error, such as one-word cos/sin, stays under this rounding
+# noise at 24 steps; the 10^4-step budget test is the one that sees it.)
+FP32_SITE_BOUND = 2e-6
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -373,6 +377,8 @@ def test_full_size_8192_sampled_sites():
         g.step(steps)
         got = g.probe(ii, jj)
         e = g.energy()
+        # the default launch configuration: dataflow launches of the split
+        assert g.flow_plan > 0
     half = oracle.reach_per_step() * steps + 2
     worst = 0.0
     for k in range(len(ii)):
@@ -406,6 +412,7 @@ def test_full_size_16384_bubble_sampled_sites():
         g.set_packet(**pk)
         g.step(steps)
         got = g.probe(ii, jj)
+        assert g.flow_plan == 192
     half = oracle.reach_per_step() * steps + 2
     worst = 0.0
     for k in range(len(ii)):
