@@ -308,6 +308,21 @@ qla_status qla_set_step_kernel(qla_ctx *ctx, int kernel);
  * if the next steps run one launch each (or no plan is built yet). */
 qla_status qla_flow_plan(const qla_ctx *ctx, int *segment_rows);
 
+/* The items a work item of a dataflow plan waits for (host only: no
+ * context, no device).  Geometry of the plan: windows of 120 stored columns
+ * (nx >= 128, a multiple of 4), segments of segment_rows rows (>= 16, a
+ * multiple of 4); item = segment * ceil(nx / 120) + window.  A unit of item
+ * i at step s waits until every item listed here (i itself included) has
+ * finished step s - 1: those whose stored sites its reads meet and those
+ * whose reads meet its stored sites, per axis (a window reads 4 columns
+ * left of its stored ones and up to 124 or, for its last two-column unit,
+ * 60 columns past that unit's first stored column; a segment reads 4 rows
+ * either side), the product of the two axes' lists.  Writes
+ * min(count, capacity) item indices to deps and the full count to *count.
+ * QLA_EINVAL for a geometry outside those limits. */
+qla_status qla_flow_item_deps(int nx, int ny, int segment_rows, int item, int *deps,
+                              int capacity, int *count);
+
 /* Test hook for the dataflow waits (never needed in normal use):
  * budget_cycles > 0 sets each wait's limit in SM clock cycles (0 restores
  * the default 2^32, about two seconds); withhold_unit >= 0 makes the unit

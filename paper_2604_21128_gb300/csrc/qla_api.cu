@@ -9,6 +9,7 @@
 
 #include "qla_internal.h"
 #include "qla_limits.h"
+#include "qla_plateau.cuh"
 
 namespace qla {
 
@@ -677,6 +678,43 @@ qla_status qla_flow_plan(const qla_ctx *c, int *segment_rows) {
     if (!c || !segment_rows) return QLA_EINVAL;
     const auto &u = c->uplan;
     *segment_rows = u.gen == c->medium_gen && u.flow && u.n_uniform > 0 ? u.seg : 0;
+    return QLA_OK;
+}
+
+qla_status qla_flow_item_deps(int nx, int ny, int segment_rows, int item, int *deps,
+                              int capacity, int *count) {
+    using namespace qla::march;
+    if (!count || capacity < 0 || (capacity > 0 && !deps)) return QLA_EINVAL;
+    *count = 0;
+    if (nx < PW || nx % 4 != 0 || ny < 8 || segment_rows < 16 || segment_rows % 4 != 0)
+        return QLA_EINVAL;
+    const int seg = segment_rows;
+    const int n_wx = (nx + PWOUT - 1) / PWOUT, n_wy = (ny + seg - 1) / seg;
+    if (item < 0 || (long long)item >= (long long)n_wx * n_wy) return QLA_EINVAL;
+    // the reads of the plan's items, as the dataflow plan takes them: a
+    // window's 128 plateau columns from 4 left of its first stored column,
+    // or its last two-column unit's 64 (from 4 left of that unit's first
+    // stored column), whichever reaches further; a segment's rows and four
+    // either side
+    std::vector<int> xd, yd;
+    const bool ok_x = flow_axis_deps(nx, PWOUT, n_wx, 4, [&](int a) {
+        const long long x = (long long)a * PWOUT;
+        const int w = int(std::min<long long>(PWOUT, nx - x));
+        const int last = (w - 1) / GWOUT * GWOUT;
+        return x + std::max(PW - 4, last + 64 - 4);
+    }, xd);
+    const bool ok_y = flow_axis_deps(ny, seg, n_wy, LAG, [&](int a) {
+        return std::min<long long>(ny, (long long)(a + 1) * seg) + LAG;
+    }, yd);
+    if (!ok_x || !ok_y) return QLA_EINVAL;
+    const int wx = item % n_wx, wy = item / n_wx;
+    const int cx = xd[size_t(wx) * FLOW_DEPS], cy = yd[size_t(wy) * FLOW_DEPS];
+    for (int k = 0; k < cx * cy; ++k) {
+        const int d = yd[size_t(wy) * FLOW_DEPS + 1 + k / cx] * n_wx +
+                      xd[size_t(wx) * FLOW_DEPS + 1 + k % cx];
+        if (k < capacity) deps[k] = d;
+    }
+    *count = cx * cy;
     return QLA_OK;
 }
 

@@ -76,6 +76,8 @@ def load():
                            ("qla_march_plan", [c_vp, c_vp, c_vp, c_vp]),
                            ("qla_flow_plan", [c_vp, c_vp]),
                            ("qla_debug_flow", [c_vp, c_ll, c_ll]),
+                           ("qla_flow_item_deps", [c_int, c_int, c_int, c_int, c_vp, c_int,
+                                                   c_vp]),
                            ("qla_set_packet_window", [c_vp, ctypes.POINTER(qla_packet), c_int,
                                                       c_int, c_int, c_int]),
                            ("qla_pack_box", [c_vp, c_int, c_int, c_int, c_int, c_vp]),
@@ -316,6 +318,18 @@ def qla_flow_plan(ctx):
     v = ctypes.c_int(0)
     _check(ctx, load().qla_flow_plan(ctx, ctypes.byref(v)))
     return v.value
+
+
+def qla_flow_item_deps(nx, ny, segment_rows, item):
+    """Items that a unit of `item` waits for in a dataflow plan (see
+    qla_flow_item_deps); host only."""
+    buf = (ctypes.c_int * 64)()
+    n = ctypes.c_int(0)
+    st = load().qla_flow_item_deps(int(nx), int(ny), int(segment_rows), int(item), buf, 64,
+                                   ctypes.byref(n))
+    if st != 0:
+        raise QLAError(st, "qla_flow_item_deps(%d, %d, %d, %d)" % (nx, ny, segment_rows, item))
+    return [buf[k] for k in range(min(n.value, 64))]
 
 
 def qla_debug_flow(ctx, budget_cycles=0, withhold_unit=-1):
