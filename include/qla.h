@@ -171,7 +171,9 @@ qla_status qla_get_state(qla_ctx *ctx, double *q_host);
 
 /* Advance n_steps >= 0 steps of Eq. 2e14 on the context's stream (returns
  * without waiting).  n_steps == 0 is a no-op; otherwise QLA_ESTATE before
- * both a medium and a state are set. */
+ * both a medium and a state are set.  The steps run as one launch each, or
+ * (FP32 E_z contexts on large lattices, see qla_set_step_kernel) as one
+ * dataflow launch for the whole call; the results are the same bits. */
 qla_status qla_step(qla_ctx *ctx, long long n_steps);
 
 /* Total energy, Eq. A13 without the cell area: the sum over sites and
